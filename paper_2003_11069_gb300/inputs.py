@@ -1,0 +1,203 @@
+"""Seeded synthetic input fields for the colour-gradient NCI lattice Boltzmann runs.
+
+This module builds initial component-density fields (rho1, rho2) only. It holds none
+of the method's arithmetic (no equilibria, no streaming, no collision): the same arrays
+are handed to the CUDA library and to the CPU oracle, each of which builds its own
+populations from them.
+
+Fields are flat float64 arrays in site order idx = x + nx*(y + ny*z). The order
+parameter of the initial state is a tanh profile psi0 = tanh((R - r)/w) around each
+droplet (psi0 = +1 inside, -1 outside); rho1 = rho0 (1 + psi0)/2, rho2 = rho0 (1 - psi0)/2.
+Where droplets overlap, the larger psi0 wins.
+
+Workload shapes follow the paper's soft-flowing-crystal studies: packed droplets of
+the dispersed phase (component 1) in a channel or square duct bounded by walls,
+with thin films of the continuous phase between neighbours (arXiv:2003.11069,
+Results, Figs. 2-3; the geometry of the paper's device is not given, so these are
+synthetic stand-ins).
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+
+import numpy as np
+
+
+@dataclass
+class Fields:
+    nx: int
+    ny: int
+    nz: int
+    rho1: np.ndarray
+    rho2: np.ndarray
+    meta: dict = field(default_factory=dict)
+
+    @property
+    def n(self) -> int:
+        return self.nx * self.ny * self.nz
+
+
+def _to_rho(psi0: np.ndarray, rho0: float = 1.0):
+    psi0 = np.clip(psi0, -1.0, 1.0)
+    return (rho0 * 0.5 * (1.0 + psi0)).ravel().copy(), (rho0 * 0.5 * (1.0 - psi0)).ravel().copy()
+
+
+def _paint(psi: np.ndarray, centers, radii, width: float, periodic_axes, pad: float = 5.0):
+    """psi = max(psi, tanh((R - r)/w)) in a box around each droplet.
+
+    psi has shape (nz, ny, nx) (nz = 1 in 2D); centers are (x, y, z)."""
+    nz, ny, nx = psi.shape
+    dims = (nx, ny, nz)
+    for c, R in zip(centers, radii):
+        ext = R + pad * width
+        rng_ax = []
+        for a in range(3):
+            if dims[a] == 1:
+                rng_ax.append((np.zeros(1, dtype=np.int64), np.zeros(1)))
+                continue
+            lo = int(math.floor(c[a] - ext))
+            hi = int(math.ceil(c[a] + ext))
+            idx = np.arange(lo, hi + 1)
+            d = idx - c[a]
+            if periodic_axes[a]:
+                idx = np.mod(idx, dims[a])
+            else:
+                keep = (idx >= 0) & (idx < dims[a])
+                idx, d = idx[keep], d[keep]
+            rng_ax.append((idx, d))
+        (ix, dx), (iy, dy), (iz, dz) = rng_ax
+        r = np.sqrt(dz[:, None, None] ** 2 + dy[None, :, None] ** 2 + dx[None, None, :] ** 2)
+        val = np.tanh((R - r) / width)
+        sub = psi[np.ix_(iz, iy, ix)]
+        psi[np.ix_(iz, iy, ix)] = np.maximum(sub, val)
+    return psi
+
+
+def droplet(nx: int, ny: int, nz: int = 1, radius: float = 30.0, width: float = 2.0,
+            center=None, rho0: float = 1.0) -> Fields:
+    """One droplet of the dispersed phase in a periodic box (2D when nz == 1)."""
+    if center is None:
+        center = ((nx - 1) / 2.0, (ny - 1) / 2.0, (nz - 1) / 2.0 if nz > 1 else 0.0)
+    z, y, x = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    r = np.sqrt((x - center[0]) ** 2 + (y - center[1]) ** 2 + (z - center[2]) ** 2)
+    psi = np.tanh((radius - r) / width)
+    r1, r2 = _to_rho(psi, rho0)
+    return Fields(nx, ny, nz, r1, r2, {"kind": "droplet", "radius": radius, "width": width})
+
+
+def uniform(nx: int, ny: int, nz: int = 1, psi0: float = -1.0, rho0: float = 1.0) -> Fields:
+    """Uniform state (psi0 = -1: pure continuous phase, single-phase flow)."""
+    psi = np.full((nz, ny, nx), psi0)
+    r1, r2 = _to_rho(psi, rho0)
+    return Fields(nx, ny, nz, r1, r2, {"kind": "uniform", "psi0": psi0})
+
+
+def slabs(nx: int, ny: int, bands, width: float = 2.0, nz: int = 1, rho0: float = 1.0) -> Fields:
+    """Planar films of the dispersed phase: psi0 = +1 for y in each [y_lo, y_hi] band,
+    with tanh edges of the given width (y periodic)."""
+    y = np.arange(ny, dtype=np.float64)
+    prof = -np.ones(ny)
+    for lo, hi in bands:
+        mid, half = 0.5 * (lo + hi), 0.5 * (hi - lo)
+        for shift in (-ny, 0, ny):
+            d = np.abs(y - mid - shift)
+            prof = np.maximum(prof, np.tanh((half - d) / width))
+    psi = np.broadcast_to(prof[None, :, None], (nz, ny, nx)).copy()
+    r1, r2 = _to_rho(psi, rho0)
+    return Fields(nx, ny, nz, r1, r2, {"kind": "slabs", "bands": list(bands)})
+
+
+def _clip_radii(centers: np.ndarray, radii: np.ndarray, dims, periodic, film: float):
+    """Shrink radii so that neighbouring droplets keep a film of at least `film`."""
+    n = len(centers)
+    out = radii.copy()
+    for a in range(n):
+        d = centers - centers[a]
+        for ax in range(len(dims)):
+            if periodic[ax] and dims[ax] > 1:
+                d[:, ax] -= dims[ax] * np.round(d[:, ax] / dims[ax])
+        dist = np.sqrt((d ** 2).sum(axis=1))
+        dist[a] = np.inf
+        j = int(np.argmin(dist))
+        out[a] = min(out[a], 0.5 * (dist[j] - film))
+    return out
+
+
+def channel_emulsion_2d(nx: int, ny: int, seed: int, r_lo: float = 12.0, r_hi: float = 16.0,
+                        area_fraction: float = 0.8, jitter: float = 1.0, width: float = 2.0,
+                        film: float = 1.0, rho0: float = 1.0) -> Fields:
+    """Packed 2D emulsion in a channel with walls below y=0 and above y=ny-1, periodic in x.
+
+    Droplet radii are uniform in [r_lo, r_hi]; centres sit on a hexagonal lattice whose
+    spacing gives the requested area fraction at the mean radius, with uniform +-jitter.
+    Rows fill the channel height. Radii are clipped to keep a film >= `film` between
+    neighbours, so the near-contact force (not merging) separates them."""
+    rng = np.random.default_rng(seed)
+    rbar = 0.5 * (r_lo + r_hi)
+    a = rbar * math.sqrt(2.0 * math.pi / (math.sqrt(3.0) * area_fraction))
+    ncol = max(1, int(round(nx / a)))
+    ax = nx / ncol
+    dy = ax * math.sqrt(3.0) / 2.0
+    y0 = r_lo + 1.5
+    nrow = max(1, int(math.floor((ny - 2 * y0) / dy)) + 1)
+    ytop = y0 + (nrow - 1) * dy
+    yshift = 0.5 * ((ny - 1) - ytop - y0)
+    centers = []
+    for r in range(nrow):
+        for c in range(ncol):
+            centers.append([(c + 0.5 * (r % 2)) * ax, y0 + yshift + r * dy, 0.0])
+    centers = np.asarray(centers, dtype=np.float64)
+    centers[:, :2] += rng.uniform(-jitter, jitter, size=(len(centers), 2))
+    radii = rng.uniform(r_lo, r_hi, size=len(centers))
+    radii = _clip_radii(centers[:, :2], radii, (nx, ny), (True, False), film)
+    # keep each droplet at least one lattice unit from the walls
+    radii = np.minimum(radii, np.minimum(centers[:, 1] + 0.5, ny - 0.5 - centers[:, 1]) - 1.0)
+    psi = -np.ones((1, ny, nx))
+    _paint(psi, centers, radii, width, (True, False, True))
+    r1, r2 = _to_rho(psi, rho0)
+    frac = float(np.pi * (radii ** 2).sum() / (nx * ny))
+    return Fields(nx, ny, 1, r1, r2, {
+        "kind": "channel_emulsion_2d", "seed": seed, "droplets": len(radii), "rows": nrow,
+        "area_fraction": frac, "r_mean": float(radii.mean()), "spacing": ax})
+
+
+def duct_emulsion_3d(nx: int, ny: int, nz: int, seed: int, radius: float = 10.0,
+                     volume_fraction: float = 0.7, jitter: float = 1.0, width: float = 2.0,
+                     film: float = 1.0, rho0: float = 1.0) -> Fields:
+    """Packed 3D emulsion in a square duct (walls in y and z, periodic in x).
+
+    Centres sit on a jittered face-centred-cubic lattice sized for the requested volume
+    fraction at the given radius; radii are clipped to keep a film >= `film`."""
+    rng = np.random.default_rng(seed)
+    cell = (16.0 * math.pi * radius ** 3 / (3.0 * volume_fraction)) ** (1.0 / 3.0)
+    ncx = max(1, int(round(nx / cell)))
+    cx = nx / ncx
+    basis = np.array([[0, 0, 0], [0.5, 0.5, 0], [0.5, 0, 0.5], [0, 0.5, 0.5]])
+    lo = radius * 0.75
+    pts = []
+    nyc = int(math.ceil(ny / cell)) + 1
+    nzc = int(math.ceil(nz / cell)) + 1
+    for i in range(ncx):
+        for j in range(nyc):
+            for k in range(nzc):
+                for b in basis:
+                    x = (i + b[0]) * cx
+                    y = lo + (j + b[1]) * cell
+                    z = lo + (k + b[2]) * cell
+                    if y <= ny - 1 - lo and z <= nz - 1 - lo:
+                        pts.append([x, y, z])
+    centers = np.asarray(pts, dtype=np.float64)
+    centers += rng.uniform(-jitter, jitter, size=centers.shape)
+    radii = np.full(len(centers), float(radius))
+    radii = _clip_radii(centers, radii, (nx, ny, nz), (True, False, False), film)
+    wall_gap = np.minimum.reduce([centers[:, 1] + 0.5, ny - 0.5 - centers[:, 1],
+                                  centers[:, 2] + 0.5, nz - 0.5 - centers[:, 2]]) - 1.0
+    radii = np.minimum(radii, wall_gap)
+    psi = -np.ones((nz, ny, nx))
+    _paint(psi, centers, radii, width, (True, False, False))
+    r1, r2 = _to_rho(psi, rho0)
+    frac = float(4.0 / 3.0 * np.pi * (radii ** 3).sum() / (nx * ny * nz))
+    return Fields(nx, ny, nz, r1, r2, {
+        "kind": "duct_emulsion_3d", "seed": seed, "droplets": len(radii),
+        "volume_fraction": frac, "r_mean": float(radii.mean())})
