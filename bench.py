@@ -1,0 +1,377 @@
+"""Benchmark of the fused NCI colour-gradient lattice Boltzmann step on GB300.
+
+One "step" is one full lattice Boltzmann time step (stream, moments, gradient, NCI,
+collide, recolour) over the whole lattice. Default workload: the 2D soft-flowing-
+crystal channel, D2Q9, 2048 x 256 sites, walls at top and bottom, periodic in x,
+packed droplets (radius 12-16, hexagonal rows, area fraction 0.8 target), body force
+1e-5, A_h = 0.05, FP32 storage and arithmetic. Metric: MLUPS (million lattice-site
+updates per second), whole job. The 2048 x 256 lattice fits in L2, so L2 is flushed
+(a 512 MB write) before every timed step and each step is timed alone with CUDA
+events on the library's stream.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--workload channel2d|duct3d|droplet2d] [--precision fp32|fp64]
+
+--impl reference times the FP64 CPU oracle on the host cores (the deliberately slow
+correctness reference, not a tuned CPU code). Under torchrun every rank runs its own
+replica of the workload on its own GPU (the step does not shard here); rank 0 prints
+one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+from paper_2003_11069_gb300 import inputs  # noqa: E402
+
+HBM_FALLBACK_GBS = 6800.0
+L2_FLUSH_BYTES = 512 << 20
+
+WORKLOADS = {
+    # name: lattice, sizes, walls, physics, generator
+    "channel2d": dict(lattice=0, nx=2048, ny=256, nz=1, wall_y=1, wall_z=0, tau=1.0, A_s=0.01, beta=0.7,
+                      A_h=0.05, force=(1e-5, 0.0, 0.0),
+                      gen=lambda nx, ny, nz, seed: inputs.channel_emulsion_2d(nx, ny, seed=seed),
+                      desc="D2Q9 soft-flowing-crystal channel 2048x256, walls y, packed droplets R 12-16 "
+                           "af 0.8 target, G=1e-5, A_h=0.05"),
+    "duct3d": dict(lattice=1, nx=512, ny=128, nz=128, wall_y=1, wall_z=1, tau=1.0, A_s=0.01, beta=0.7,
+                   A_h=0.03, force=(2e-6, 0.0, 0.0),
+                   gen=lambda nx, ny, nz, seed: inputs.duct_emulsion_3d(nx, ny, nz, seed=seed),
+                   desc="D3Q27 packed-emulsion square duct 512x128x128, walls y,z, FCC droplets R 10 "
+                        "vf 0.7 target, G=2e-6, A_h=0.03"),
+    "droplet2d": dict(lattice=0, nx=128, ny=128, nz=1, wall_y=0, wall_z=0, tau=1.0, A_s=0.01, beta=0.7,
+                      A_h=0.05, force=(0.0, 0.0, 0.0),
+                      gen=lambda nx, ny, nz, seed: inputs.droplet(nx, ny, radius=30),
+                      desc="D2Q9 periodic 128x128, one droplet R 30, A_h=0.05"),
+}
+
+# Population bytes moved per site update: 2 components x Q x (1 read + 1 write).
+def alg_bytes_per_site(lattice: int, elem: int) -> int:
+    Q = 9 if lattice == 0 else 27
+    return 2 * Q * elem * 2
+
+
+def measured_hbm_peak():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            v = float(json.load(fh)["hbm_gbs"])
+        return v, "measured"
+    except Exception:
+        return HBM_FALLBACK_GBS, "fallback"
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    d = os.path.join(ROOT, "paper_2003_11069_gb300", "csrc")
+    for name in sorted(os.listdir(d)):
+        with open(os.path.join(d, name), "rb") as fh:
+            h.update(name.encode())
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(workload: str, precision: str):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken on the
+    current kernel sources (else None)."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as fh:
+            rec = json.load(fh)
+        ent = rec.get(f"{workload}/{precision}")
+        if ent and ent.get("kernel_sources") == kernel_source_hash():
+            return ent.get("dram_bytes_per_step")
+    except Exception:
+        pass
+    return None
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=self.fh, stderr=subprocess.DEVNULL)
+            time.sleep(0.3)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.fh.close()
+
+    def summary(self):
+        if self.proc is None or not self.path:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        rows = []
+        with open(self.path) as fh:
+            for line in fh:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        smax = max(float(r[2]) for r in rows if r[2].replace(".", "").isdigit())
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower() == "active"})
+        loaded = [v for v in sm if v > 0.5 * smax] or sm
+        return {"sm_mhz": statistics.median(loaded), "sm_max_mhz": smax, "reasons": reasons,
+                "samples": len(rows)}
+
+
+def cpu_oracle_run(w: dict, budget_s: float, nthreads: int, crop=None):
+    """Time the FP64 CPU oracle on (a crop of) the workload for about budget_s seconds."""
+    import oracle
+    nx, ny, nz = (crop or (w["nx"], w["ny"], w["nz"]))
+    fl = w["gen"](nx, ny, nz, 1234)
+    p = oracle.make_params(lattice=w["lattice"], nx=nx, ny=ny, nz=nz, wall_y=w["wall_y"], wall_z=w["wall_z"],
+                           tau=w["tau"], A_s=w["A_s"], beta=w["beta"], A_h=w["A_h"], force=w["force"])
+    f = oracle.init(p, fl.rho1, fl.rho2)
+    steps, t0 = 0, time.perf_counter()
+    chunk = 1
+    while True:
+        oracle.step_inplace(p, f, chunk, nthreads)
+        steps += chunk
+        el = time.perf_counter() - t0
+        if el >= budget_s:
+            break
+        chunk = max(1, min(chunk * 2, int(steps * (budget_s - el) / max(el, 1e-9)) or 1))
+    el = time.perf_counter() - t0
+    n = nx * ny * nz
+    return {"mlups": n * steps / el / 1e6, "steps": steps, "seconds": el, "sites": n,
+            "sample": f"{nx}x{ny}x{nz} crop of the same generator, {steps} steps, FP64 oracle"}
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def run_reference(args, w):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    cores = os.cpu_count() or 1
+    import oracle
+    nx, ny, nz = w["nx"], w["ny"], w["nz"]
+    sites = nx * ny * nz
+    # each step: one full oracle step on a bounded sample of the workload
+    budget_sites = 600_000 if w["lattice"] == 0 else 120_000
+    if sites > budget_sites:
+        if w["lattice"] == 0:
+            crop = (nx, max(16, budget_sites // nx), 1)
+        else:
+            crop = (max(32, budget_sites // (ny * nz) // 32 * 32) if budget_sites // (ny * nz) >= 32 else 32,
+                    min(ny, 48), min(nz, 48))
+    else:
+        crop = (nx, ny, nz)
+    fl = w["gen"](*crop, 1234)
+    p = oracle.make_params(lattice=w["lattice"], nx=crop[0], ny=crop[1], nz=crop[2], wall_y=w["wall_y"],
+                           wall_z=w["wall_z"], tau=w["tau"], A_s=w["A_s"], beta=w["beta"], A_h=w["A_h"],
+                           force=w["force"])
+    f = oracle.init(p, fl.rho1, fl.rho2)
+    for _ in range(args.warmup):
+        oracle.step_inplace(p, f, 1, cores)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.step_inplace(p, f, 1, cores)
+    el = time.perf_counter() - t0
+    n = crop[0] * crop[1] * crop[2]
+    mlups = n * args.steps / el / 1e6
+    sample = f"{crop[0]}x{crop[1]}x{crop[2]} sample of the workload per step"
+    line = {
+        "impl": "reference", "metric": "MLUPS", "value": round(mlups, 4), "unit": "MLUPS",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(el / args.steps * 1e3, 4), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": w["desc"], "sample": sample, "precision": "fp64 (CPU oracle)"},
+        "cpu_baseline": {"value": round(mlups, 4), "unit": "MLUPS", "cores": cores, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": round(mlups, 4), "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="channel2d", choices=sorted(WORKLOADS))
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--cpu-budget", type=float, default=12.0)
+    args = ap.parse_args(argv)
+    w = WORKLOADS[args.workload]
+    if args.warmup < 3:
+        raise SystemExit("--warmup must be >= 3")
+    if args.impl == "reference":
+        return run_reference(args, w)
+
+    import torch
+    from paper_2003_11069_gb300 import lbnci
+
+    ws, rank, local = dist_env()
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA GPU (the library has no CPU path)")
+    torch.cuda.set_device(local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    lbnci.load()
+    stream = torch.cuda.Stream()
+    prec = lbnci.LB_FP32 if args.precision == "fp32" else lbnci.LB_FP64
+    elem = 4 if prec == lbnci.LB_FP32 else 8
+    nx, ny, nz = w["nx"], w["ny"], w["nz"]
+    N = nx * ny * nz
+    cfg = lbnci.lb_config_make(lattice=w["lattice"], nx=nx, ny=ny, nz=nz, wall_y=w["wall_y"], wall_z=w["wall_z"],
+                               tau=w["tau"], A_s=w["A_s"], beta=w["beta"], A_h=w["A_h"], force=w["force"],
+                               precision=prec, stream=stream.cuda_stream)
+    fl = w["gen"](nx, ny, nz, 1234 + rank)
+    rho1 = torch.from_numpy(fl.rho1).cuda()
+    rho2 = torch.from_numpy(fl.rho2).cuda()
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+    torch.cuda.synchronize()
+
+    sim = lbnci.Sim(cfg, workspace="torch")
+    with torch.cuda.stream(stream):
+        sim.init_fields(rho1, rho2)
+        sim.step(args.warmup)
+        stream.synchronize()
+        starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+        ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        launches0 = sim.launches()
+        with ClockSampler(local) as clk:
+            for k in range(args.steps):
+                flush.fill_(k & 0xFF)  # evict the lattice from L2 before each timed step
+                starts[k].record(stream)
+                sim.step(1)
+                ends[k].record(stream)
+            torch.cuda.synchronize()
+        launches = sim.launches() - launches0
+        step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+        total_ms = float(sum(step_ms))
+        if dist:
+            t = torch.tensor([total_ms], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            total_ms = float(t.item())
+            dist.barrier()
+        obs = sim.observables(allow_numeric=True)
+    clocks = clk.summary()
+    ms_per_step = total_ms / args.steps
+    value = N * args.steps * ws / (total_ms * 1e-3) / 1e6
+
+    # end to end through the public API with host buffers
+    e2e = None
+    if not args.no_e2e:
+        h1 = torch.from_numpy(fl.rho1).pin_memory()
+        h2 = torch.from_numpy(fl.rho2).pin_memory()
+        psi_h = torch.empty(N, dtype=torch.float64).pin_memory()
+        u_h = torch.empty(3 * N, dtype=torch.float64).pin_memory()
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        sim.init_fields(h1.numpy(), h2.numpy())
+        sim.step(args.steps)
+        o2 = sim.observables(psi_h.numpy(), u_h.numpy(), allow_numeric=True)
+        torch.cuda.synchronize()
+        el = time.perf_counter() - t0
+        if dist:
+            t = torch.tensor([el], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            el = float(t.item())
+        e2e = {"value": round(N * args.steps * ws / el / 1e6, 3), "unit": "MLUPS",
+               "h2d_bytes_per_step": round(2 * 8 * N / args.steps, 1),
+               "d2h_bytes_per_step": round((4 * 8 * N + 80) / args.steps, 1),
+               "note": "lb_init_fields from pinned host rho1/rho2, lb_step(K), lb_observables with psi "
+                       "and u copied back to host; bytes per step = totals / K"}
+    sim.close()
+    if dist:
+        dist.destroy_process_group()
+    if rank != 0:
+        return 0
+
+    peak, peak_kind = measured_hbm_peak()
+    bpsite = alg_bytes_per_site(w["lattice"], elem)
+    achieved = bpsite * N / (ms_per_step * 1e-3) / 1e9
+    traffic = recorded_traffic(args.workload, args.precision)
+    cpu = None
+    if not args.no_cpu_baseline:
+        crop = (512, 64, 1) if w["lattice"] == 0 else (64, 32, 32)
+        if args.workload == "droplet2d":
+            crop = None
+        r = cpu_oracle_run(w, args.cpu_budget, os.cpu_count() or 1, crop)
+        cpu = {"value": round(r["mlups"], 4), "unit": "MLUPS", "cores": os.cpu_count() or 1, "kind": "oracle",
+               "sample": r["sample"]}
+    line = {
+        "metric": "MLUPS", "value": round(value, 2), "unit": "MLUPS", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(ms_per_step, 5), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32" if prec == lbnci.LB_FP32 else "f64", "data": "synthetic",
+        "config": {"workload": w["desc"], "sites": N, "precision": args.precision,
+                   "l2": "flushed (512 MB write) before every timed step; each step timed alone",
+                   "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU",
+                   "droplets": fl.meta.get("droplets"),
+                   "fraction": fl.meta.get("area_fraction", fl.meta.get("volume_fraction"))},
+        "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                     "frac": round(achieved / peak, 4), "traffic": traffic,
+                     "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured"
+                     else "fallback 6.8 TB/s",
+                     "kernel": "one lattice step (all step kernels)", "alg_bytes_per_site": bpsite},
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+        "gpu_launches": int(launches),
+        "clocks": clocks,
+        "observables": {"n_nci": obs["n_nci"], "n_interface": obs["n_interface"], "n_bad": obs["n_bad"]},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,151 @@
+/*
+ * lbnci.h -- C ABI of the GB300 (sm_103a) two-component colour-gradient lattice
+ * Boltzmann solver with near-contact interactions (NCI).
+ *
+ * Method: Montessori, Tiribocchi, Bonaccorso, Lauricella, Succi, "Lattice Boltzmann
+ * simulations capture the multiscale physics of soft flowing crystals",
+ * arXiv:2003.11069, section "Materials and Methods":
+ *   - two population sets f_i^k (k = 1, 2) evolving by Eq. (CGLBE), dt = 1;
+ *   - collision Omega = Omega^(3)[Omega^(1) + Omega^(2)]: BGK relaxation, the
+ *     surface-tension perturbation and recolouring with segregation beta;
+ *   - order parameter psi = (rho1 - rho2)/(rho1 + rho2), normal n = -grad psi/|grad psi|;
+ *   - NCI force F_rep = -A_h[h(x)] n delta_I, delta_I = |grad psi|/2, Eq. (near_c),
+ *     with A_h = A for h <= h_min, A (h_min/h)^3 for h_min < h <= h_max, 0 beyond.
+ * A uniform body force G drives the flow; G and F_rep enter through Guo forcing.
+ * Every entry point runs its arithmetic in this library's CUDA kernels; there is
+ * no CPU fallback. A missing or unusable GPU makes lb_create fail with LB_ECUDA.
+ *
+ * Conventions
+ *   Site index     idx = x + nx*(y + ny*z), x fastest; nz = 1 on D2Q9.
+ *   Boundaries     x is periodic. y (and z on D3Q27) is periodic, or bounded by
+ *                  halfway bounce-back walls just below index 0 and just above
+ *                  index n-1 when wall_y (wall_z) is set.
+ *   Velocities     direction i = 0..Q-1 has c_i given by the base-3 digits of i
+ *                  (x from the lowest digit, then y, then z), digit d mapping to
+ *                  {0, +1, -1}[d]. Weights: D2Q9 4/9, 1/9, 1/36; D3Q27 8/27, 2/27,
+ *                  1/54, 1/216 by |c_i|^2.
+ *   Populations    f[k][i][idx], k = 0 for component 1 (the dispersed phase,
+ *                  psi > 0) and 1 for component 2. The state between steps is the
+ *                  post-collision population at its own site; a step first pulls
+ *                  (streams), then collides.
+ *   Vectors        [3][N] arrays (component-major), z component 0 on D2Q9.
+ *   Host/device    arrays are host pointers when on_device == 0 and device pointers
+ *                  (on the sim's device) when on_device == 1. All host arrays are
+ *                  FP64 (int32 for hit maps) whatever the storage precision.
+ *
+ * Ownership: the sim owns the memory it allocates; a caller-provided workspace
+ * (lb_config.workspace) stays the caller's and must outlive the sim. Caller arrays
+ * are only read or written during the call (or, for on_device == 1, in stream order
+ * on lb_config.stream).
+ *
+ * Errors: every call returns an lb_status and never aborts or traps. lb_step
+ * reports launch failures at once; numerical blow-up (a non-finite or non-positive
+ * density) is reported by the next lb_observables / lb_fields as LB_ENUMERIC.
+ * lb_last_error() gives a one-line description of the last failure. A sim handle
+ * must not be used from two host threads at once.
+ */
+#ifndef LBNCI_H
+#define LBNCI_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  LB_OK = 0,
+  LB_EINVAL = 1,       /* bad argument or configuration */
+  LB_ENOMEM = 2,       /* device allocation failed or workspace too small */
+  LB_ECUDA = 3,        /* CUDA runtime error (no device, launch failure, ...) */
+  LB_ENUMERIC = 4,     /* non-finite or non-positive density detected */
+  LB_EUNSUPPORTED = 5  /* valid request this build does not implement */
+} lb_status;
+
+typedef enum { LB_D2Q9 = 0, LB_D3Q27 = 1 } lb_lattice;
+
+typedef enum {
+  LB_FP64 = 0,   /* populations stored and computed in FP64 (parity path) */
+  LB_FP32 = 1    /* populations stored and computed in FP32 */
+} lb_precision;
+
+typedef struct {
+  int lattice;          /* lb_lattice */
+  int nx, ny, nz;       /* lattice size; nz = 1 for D2Q9 */
+  int wall_y, wall_z;   /* 1 = halfway bounce-back walls on that axis, 0 = periodic */
+  double tau;           /* BGK relaxation time, nu = (tau - 1/2)/3; tau > 1/2 */
+  double A_s;           /* perturbation amplitude of each component; sigma = 4 A_s tau/9 */
+  double beta;          /* recolouring segregation parameter, 0 <= beta <= 1 */
+  double A_h;           /* NCI strength A (force per unit volume); 0 disables NCI */
+  double h_min, h_max;  /* NCI cut-offs in lattice units, 0 < h_min <= h_max < 5 */
+  double g_th;          /* interface threshold on |grad psi| for the NCI ray search */
+  double force[3];      /* uniform body-force density G */
+  int precision;        /* lb_precision */
+  void* stream;         /* cudaStream_t for all work; NULL = the legacy default stream */
+  void* workspace;      /* optional caller-owned device memory, 256-byte aligned */
+  size_t workspace_bytes;
+} lb_config;
+
+typedef struct lb_sim lb_sim;
+
+typedef struct {
+  double mass[2];        /* sum over sites of rho_1, rho_2 */
+  double momentum[3];    /* sum over sites of rho u = j + F/2 */
+  double flow_rate;      /* (1/nx) sum rho u_x: mean mass flux through a cross-section */
+  double flow_rate_disp; /* (1/nx) sum rho_1 u_x: the dispersed phase's share */
+  long long step;        /* steps taken since lb_init_fields / lb_set_populations */
+  long long n_interface; /* sites with |grad psi| > g_th */
+  long long n_nci;       /* sites where the NCI force acts (a facing interface was hit) */
+  long long n_bad;       /* sites with a non-finite or non-positive density */
+} lb_obs;
+
+/* Device bytes lb_create needs when it is given a workspace (cfg->workspace). */
+lb_status lb_workspace_size(const lb_config* cfg, size_t* bytes);
+
+/* Validate cfg, take the current CUDA device, allocate (or carve from the
+ * workspace) two population buffers and scratch. The populations start at zero:
+ * call lb_init_fields or lb_set_populations before lb_step. */
+lb_status lb_create(const lb_config* cfg, lb_sim** out);
+
+/* f^k_i = f_eq_i(rho_k, u) (second-order equilibrium, c_s^2 = 1/3) at every site:
+ * the state of a mixture at rest or moving with u, taken as post-collision at t = 0.
+ * rho1, rho2: [N]; u: [3][N] or NULL for u = 0. Resets the step counter. */
+lb_status lb_init_fields(lb_sim* sim, const double* rho1, const double* rho2,
+                         const double* u, int on_device);
+
+/* Advance nsteps >= 0 full steps (stream, moments, gradient, NCI, collide,
+ * recolour). Asynchronous on cfg->stream. */
+lb_status lb_step(lb_sim* sim, long long nsteps);
+
+/* Reductions of the current state (see lb_obs) and, optionally, psi [N] and
+ * u [3][N]. The macroscopic fields are those the next collision would see:
+ * densities of the streamed populations and u = (j + F/2)/rho with F = G + F_rep.
+ * Synchronises cfg->stream. Returns LB_ENUMERIC (with out filled) if n_bad > 0. */
+lb_status lb_observables(lb_sim* sim, lb_obs* out, double* psi_out, double* u_out,
+                         int on_device);
+
+/* Per-site fields of the current state, each optional (NULL = skip):
+ * rho1, rho2, psi [N]; grad psi, F_rep, u [3][N]; hit [N] = NCI distance h
+ * (0 where no facing interface was found). Synchronises cfg->stream. */
+lb_status lb_fields(lb_sim* sim, double* rho1, double* rho2, double* psi, double* grad,
+                    double* frep, int* hit, double* u, int on_device);
+
+/* Copy the populations out of / into the sim as FP64 [2][Q][N] (converted from / to
+ * the storage precision). lb_set_populations resets the step counter. */
+lb_status lb_get_populations(lb_sim* sim, double* f, int on_device);
+lb_status lb_set_populations(lb_sim* sim, const double* f, int on_device);
+
+/* Release everything the sim allocated. NULL is allowed. */
+void lb_destroy(lb_sim* sim);
+
+/* One-line description of the last failure on this sim (or, for sim == NULL, of
+ * the last failure of lb_create / lb_workspace_size on this thread). */
+const char* lb_last_error(const lb_sim* sim);
+
+/* Step kernels launched by this sim since lb_create (for launch accounting). */
+long long lb_kernel_launches(const lb_sim* sim);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

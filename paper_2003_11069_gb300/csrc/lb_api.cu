@@ -1,0 +1,425 @@
+// lb_api.cu -- C ABI of the NCI colour-gradient lattice Boltzmann library (lbnci.h).
+// Handles, validation, memory and the step loop; all arithmetic runs in the kernels
+// of lb_fp64.cu / lb_fp32.cu.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+#include "../../include/lbnci.h"
+#include "lb_launch.h"
+
+namespace lbnci {
+
+__global__ void __launch_bounds__(256) reduce_partials_kernel(const double* __restrict__ partials,
+                                                              long long nblocks, double* __restrict__ out) {
+  // One block: thread t sums blocks t, t+256, ... in order, then a fixed tree.
+  __shared__ double s[256];
+  for (int q = 0; q < kRedSlots; ++q) {
+    double v = 0.0;
+    for (long long b = threadIdx.x; b < nblocks; b += blockDim.x) v += partials[b * kRedSlots + q];
+    s[threadIdx.x] = v;
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+      if ((int)threadIdx.x < w) s[threadIdx.x] += s[threadIdx.x + w];
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) out[q] = s[0];
+    __syncthreads();
+  }
+}
+
+cudaError_t reduce_partials(const double* partials, long long nblocks, double* out, cudaStream_t s) {
+  reduce_partials_kernel<<<1, 256, 0, s>>>(partials, nblocks, out);
+  return cudaGetLastError();
+}
+
+long long tiled_blocks(int lattice, const StepParams& p) {
+  if (lattice == 0) {
+    return (long long)((p.nx + Tile<0>::X - 1) / Tile<0>::X) * ((p.ny + Tile<0>::Y - 1) / Tile<0>::Y) *
+           ((p.nz + Tile<0>::Z - 1) / Tile<0>::Z);
+  }
+  return (long long)((p.nx + Tile<1>::X - 1) / Tile<1>::X) * ((p.ny + Tile<1>::Y - 1) / Tile<1>::Y) *
+         ((p.nz + Tile<1>::Z - 1) / Tile<1>::Z);
+}
+
+}  // namespace lbnci
+
+using namespace lbnci;
+
+struct lb_sim {
+  lb_config cfg;
+  StepParams p;
+  const Launchers* L;
+  int Q;
+  int device;
+  cudaStream_t stream;
+  void* fa;        // current state
+  void* fb;        // back buffer (also staging between steps)
+  void* psi;       // order parameter of the streamed state
+  double* partials;
+  double* result;  // kRedSlots doubles
+  double* host_result;  // pinned
+  long long nblocks;
+  bool owns;       // memory from cudaMalloc (else carved from the workspace)
+  void* base;      // cudaMalloc'd block
+  long long step;
+  long long launches;
+  char err[256];
+};
+
+namespace {
+
+thread_local char g_err[256] = "";
+
+lb_status fail(lb_sim* s, lb_status st, const char* fmt, ...) {
+  char* dst = s ? s->err : g_err;
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(dst, 256, fmt, ap);
+  va_end(ap);
+  return st;
+}
+
+lb_status cuda_fail(lb_sim* s, cudaError_t e, const char* what) {
+  return fail(s, LB_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
+
+struct Layout {
+  size_t fa, fb, psi, partials, result, total;
+};
+
+lb_status validate(const lb_config* c, StepParams* p, Layout* lay, long long* nblocks) {
+  if (!c) return fail(nullptr, LB_EINVAL, "config is NULL");
+  if (c->lattice != LB_D2Q9 && c->lattice != LB_D3Q27)
+    return fail(nullptr, LB_EINVAL, "unknown lattice %d", c->lattice);
+  if (c->precision != LB_FP64 && c->precision != LB_FP32)
+    return fail(nullptr, LB_EUNSUPPORTED, "precision %d is not implemented", c->precision);
+  if (c->nx < 1 || c->ny < 1 || c->nz < 1)
+    return fail(nullptr, LB_EINVAL, "lattice sizes must be >= 1 (got %d x %d x %d)", c->nx, c->ny, c->nz);
+  if (c->lattice == LB_D2Q9 && c->nz != 1) return fail(nullptr, LB_EINVAL, "D2Q9 needs nz == 1");
+  if (c->lattice == LB_D2Q9 && c->wall_z) return fail(nullptr, LB_EINVAL, "D2Q9 has no z walls");
+  if (!(c->tau > 0.5) || !std::isfinite(c->tau)) return fail(nullptr, LB_EINVAL, "tau must be > 1/2");
+  if (!(c->beta >= 0.0 && c->beta <= 1.0)) return fail(nullptr, LB_EINVAL, "beta must be in [0, 1]");
+  if (!(c->A_s >= 0.0) || !std::isfinite(c->A_s)) return fail(nullptr, LB_EINVAL, "A_s must be >= 0");
+  if (!(c->A_h >= 0.0) || !std::isfinite(c->A_h)) return fail(nullptr, LB_EINVAL, "A_h must be >= 0");
+  if (!(c->g_th >= 0.0) || !std::isfinite(c->g_th)) return fail(nullptr, LB_EINVAL, "g_th must be >= 0");
+  for (int a = 0; a < 3; ++a)
+    if (!std::isfinite(c->force[a])) return fail(nullptr, LB_EINVAL, "force must be finite");
+  int smax = 0;
+  if (c->A_h > 0.0) {
+    if (!(c->h_min > 0.0 && c->h_min <= c->h_max && c->h_max < 5.0))
+      return fail(nullptr, LB_EINVAL, "NCI needs 0 < h_min <= h_max < 5 (got %g, %g)", c->h_min, c->h_max);
+    smax = (int)std::floor(c->h_max);
+  }
+  const long long N = (long long)c->nx * c->ny * c->nz;
+  if (N > (1LL << 40)) return fail(nullptr, LB_EINVAL, "lattice too large");
+  p->nx = c->nx; p->ny = c->ny; p->nz = c->nz;
+  p->wall_y = c->wall_y ? 1 : 0;
+  p->wall_z = c->wall_z ? 1 : 0;
+  p->N = N;
+  p->tau = c->tau; p->A_s = c->A_s; p->beta = c->beta; p->A_h = c->A_h;
+  p->h_min = c->h_min; p->h_max = c->h_max; p->g_th = c->g_th;
+  for (int a = 0; a < 3; ++a) p->G[a] = c->force[a];
+  if (c->lattice == LB_D2Q9) p->G[2] = 0.0;
+  p->smax = smax;
+  const int Q = c->lattice == LB_D2Q9 ? 9 : 27;
+  const size_t elem = c->precision == LB_FP64 ? 8 : 4;
+  *nblocks = tiled_blocks(c->lattice, *p);
+  size_t off = 0;
+  lay->fa = off; off = align256(off + 2 * (size_t)Q * (size_t)N * elem);
+  lay->fb = off; off = align256(off + 2 * (size_t)Q * (size_t)N * elem);
+  lay->psi = off; off = align256(off + (size_t)N * elem);
+  lay->partials = off; off = align256(off + (size_t)(*nblocks) * kRedSlots * sizeof(double));
+  lay->result = off; off = align256(off + 16 * sizeof(double));
+  lay->total = off;
+  return LB_OK;
+}
+
+// Bytes of FP64 staging the back buffer can hold.
+size_t staging_doubles(const lb_sim* s) {
+  return 2 * (size_t)s->Q * (size_t)s->p.N * s->L->elem / sizeof(double);
+}
+
+// Run the fields kernel on the current state with the given device outputs and
+// fill s->host_result with the reduced observables (synchronises the stream).
+lb_status run_fields(lb_sim* s, const FieldOut& outs) {
+  cudaError_t e = s->L->moments(s->fa, s->psi, s->p, s->stream);
+  if (e != cudaSuccess) return cuda_fail(s, e, "moments launch");
+  FieldOut fo = outs;
+  fo.partials = s->partials;
+  e = s->L->fields(s->fa, s->psi, s->p, fo, s->stream);
+  if (e != cudaSuccess) return cuda_fail(s, e, "fields launch");
+  e = reduce_partials(s->partials, s->nblocks, s->result, s->stream);
+  if (e != cudaSuccess) return cuda_fail(s, e, "reduce launch");
+  e = cudaMemcpyAsync(s->host_result, s->result, kRedSlots * sizeof(double), cudaMemcpyDeviceToHost, s->stream);
+  if (e != cudaSuccess) return cuda_fail(s, e, "result copy");
+  e = cudaStreamSynchronize(s->stream);
+  if (e != cudaSuccess) return cuda_fail(s, e, "stream synchronize");
+  return LB_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+lb_status lb_workspace_size(const lb_config* cfg, size_t* bytes) {
+  if (!bytes) return fail(nullptr, LB_EINVAL, "bytes is NULL");
+  StepParams p;
+  Layout lay;
+  long long nb;
+  lb_status st = validate(cfg, &p, &lay, &nb);
+  if (st != LB_OK) return st;
+  *bytes = lay.total;
+  return LB_OK;
+}
+
+lb_status lb_create(const lb_config* cfg, lb_sim** out) {
+  if (!out) return fail(nullptr, LB_EINVAL, "out is NULL");
+  *out = nullptr;
+  StepParams p;
+  Layout lay;
+  long long nblocks;
+  lb_status st = validate(cfg, &p, &lay, &nblocks);
+  if (st != LB_OK) return st;
+  int dev = -1;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return fail(nullptr, LB_ECUDA, "no CUDA device: %s", cudaGetErrorString(e));
+  const Launchers* L = cfg->precision == LB_FP64 ? launchers_fp64(cfg->lattice) : launchers_fp32(cfg->lattice);
+  lb_sim* s = new (std::nothrow) lb_sim();
+  if (!s) return fail(nullptr, LB_ENOMEM, "host allocation failed");
+  s->cfg = *cfg;
+  s->p = p;
+  s->L = L;
+  s->Q = cfg->lattice == LB_D2Q9 ? 9 : 27;
+  s->device = dev;
+  s->stream = (cudaStream_t)cfg->stream;
+  s->nblocks = nblocks;
+  unsigned char* base = nullptr;
+  if (cfg->workspace) {
+    if (((uintptr_t)cfg->workspace & 255u) != 0) {
+      delete s;
+      return fail(nullptr, LB_EINVAL, "workspace must be 256-byte aligned");
+    }
+    if (cfg->workspace_bytes < lay.total) {
+      delete s;
+      return fail(nullptr, LB_ENOMEM, "workspace has %zu bytes, %zu needed", cfg->workspace_bytes, lay.total);
+    }
+    base = (unsigned char*)cfg->workspace;
+    s->owns = false;
+  } else {
+    e = cudaMalloc((void**)&base, lay.total);
+    if (e != cudaSuccess) {
+      delete s;
+      cudaGetLastError();
+      return fail(nullptr, e == cudaErrorMemoryAllocation ? LB_ENOMEM : LB_ECUDA,
+                  "cudaMalloc of %zu bytes failed: %s", lay.total, cudaGetErrorString(e));
+    }
+    s->owns = true;
+    s->base = base;
+  }
+  s->fa = base + lay.fa;
+  s->fb = base + lay.fb;
+  s->psi = base + lay.psi;
+  s->partials = (double*)(base + lay.partials);
+  s->result = (double*)(base + lay.result);
+  e = cudaMallocHost((void**)&s->host_result, 16 * sizeof(double));
+  if (e != cudaSuccess) {
+    if (s->owns) cudaFree(s->base);
+    delete s;
+    return fail(nullptr, LB_ECUDA, "pinned allocation failed: %s", cudaGetErrorString(e));
+  }
+  e = cudaMemsetAsync(s->fa, 0, lay.psi, s->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+  if (e != cudaSuccess) {
+    lb_destroy(s);
+    return fail(nullptr, LB_ECUDA, "initial clear failed: %s", cudaGetErrorString(e));
+  }
+  *out = s;
+  return LB_OK;
+}
+
+lb_status lb_init_fields(lb_sim* s, const double* rho1, const double* rho2, const double* u, int on_device) {
+  if (!s) return fail(nullptr, LB_EINVAL, "sim is NULL");
+  if (!rho1 || !rho2) return fail(s, LB_EINVAL, "rho1 and rho2 are required");
+  const long long N = s->p.N;
+  const double *d1 = rho1, *d2 = rho2, *du = u;
+  cudaError_t e;
+  if (!on_device) {
+    // Stage the host fields in the back buffer (it holds at least 4.5 N doubles).
+    double* st = (double*)s->fb;
+    const size_t need = (size_t)N * (u ? 5 : 2);
+    if (need > staging_doubles(s)) return fail(s, LB_EUNSUPPORTED, "staging too small");
+    e = cudaMemcpyAsync(st, rho1, N * sizeof(double), cudaMemcpyHostToDevice, s->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(st + N, rho2, N * sizeof(double), cudaMemcpyHostToDevice, s->stream);
+    if (e == cudaSuccess && u) e = cudaMemcpyAsync(st + 2 * N, u, 3 * N * sizeof(double), cudaMemcpyHostToDevice, s->stream);
+    if (e != cudaSuccess) return cuda_fail(s, e, "field upload");
+    d1 = st; d2 = st + N; du = u ? st + 2 * N : nullptr;
+  }
+  e = s->L->init(s->fa, d1, d2, du, N, s->stream);
+  ++s->launches;
+  if (e != cudaSuccess) return cuda_fail(s, e, "init launch");
+  if (!on_device) {
+    e = cudaStreamSynchronize(s->stream);
+    if (e != cudaSuccess) return cuda_fail(s, e, "stream synchronize");
+  }
+  s->step = 0;
+  return LB_OK;
+}
+
+lb_status lb_step(lb_sim* s, long long nsteps) {
+  if (!s) return fail(nullptr, LB_EINVAL, "sim is NULL");
+  if (nsteps < 0) return fail(s, LB_EINVAL, "nsteps must be >= 0");
+  for (long long t = 0; t < nsteps; ++t) {
+    cudaError_t e = s->L->moments(s->fa, s->psi, s->p, s->stream);
+    if (e != cudaSuccess) return cuda_fail(s, e, "moments launch");
+    e = s->L->collide(s->fa, s->fb, s->psi, s->p, s->stream);
+    if (e != cudaSuccess) return cuda_fail(s, e, "collide launch");
+    s->launches += 2;
+    std::swap(s->fa, s->fb);
+    ++s->step;
+  }
+  return LB_OK;
+}
+
+lb_status lb_fields(lb_sim* s, double* rho1, double* rho2, double* psi, double* grad, double* frep,
+                    int* hit, double* u, int on_device) {
+  if (!s) return fail(nullptr, LB_EINVAL, "sim is NULL");
+  const long long N = s->p.N;
+  if (on_device) {
+    FieldOut fo{rho1, rho2, psi, grad, frep, hit, u, nullptr};
+    lb_status st = run_fields(s, fo);
+    s->launches += 3;
+    if (st != LB_OK) return st;
+    return s->host_result[9] > 0 ? fail(s, LB_ENUMERIC, "non-finite or non-positive density at %.0f sites", s->host_result[9]) : LB_OK;
+  }
+  // Host outputs: one pass per requested field, staged in the back buffer.
+  struct Req { void* host; int slot; size_t bytes; };
+  Req reqs[7] = {{rho1, 0, N * sizeof(double)}, {rho2, 1, N * sizeof(double)}, {psi, 2, N * sizeof(double)},
+                 {grad, 3, 3 * N * sizeof(double)}, {frep, 4, 3 * N * sizeof(double)}, {hit, 5, N * sizeof(int)},
+                 {u, 6, 3 * N * sizeof(double)}};
+  bool any = false;
+  for (const Req& r : reqs) {
+    if (!r.host) continue;
+    any = true;
+    FieldOut fo{};
+    double* st = (double*)s->fb;
+    switch (r.slot) {
+      case 0: fo.rho1 = st; break;
+      case 1: fo.rho2 = st; break;
+      case 2: fo.psi = st; break;
+      case 3: fo.grad = st; break;
+      case 4: fo.frep = st; break;
+      case 5: fo.hit = (int*)st; break;
+      case 6: fo.u = st; break;
+    }
+    lb_status stt = run_fields(s, fo);
+    s->launches += 3;
+    if (stt != LB_OK) return stt;
+    cudaError_t e = cudaMemcpy(r.host, st, r.bytes, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(s, e, "field download");
+  }
+  if (!any) {
+    FieldOut fo{};
+    lb_status st = run_fields(s, fo);
+    s->launches += 3;
+    if (st != LB_OK) return st;
+  }
+  return s->host_result[9] > 0 ? fail(s, LB_ENUMERIC, "non-finite or non-positive density at %.0f sites", s->host_result[9]) : LB_OK;
+}
+
+lb_status lb_observables(lb_sim* s, lb_obs* out, double* psi_out, double* u_out, int on_device) {
+  if (!s) return fail(nullptr, LB_EINVAL, "sim is NULL");
+  if (!out) return fail(s, LB_EINVAL, "out is NULL");
+  lb_status st = lb_fields(s, nullptr, nullptr, psi_out, nullptr, nullptr, nullptr, u_out, on_device);
+  if (st != LB_OK && st != LB_ENUMERIC) return st;
+  const double* r = s->host_result;
+  out->mass[0] = r[0];
+  out->mass[1] = r[1];
+  out->momentum[0] = r[2];
+  out->momentum[1] = r[3];
+  out->momentum[2] = r[4];
+  out->flow_rate = r[5] / (double)s->p.nx;
+  out->flow_rate_disp = r[6] / (double)s->p.nx;
+  out->step = s->step;
+  out->n_interface = (long long)r[7];
+  out->n_nci = (long long)r[8];
+  out->n_bad = (long long)r[9];
+  return st;
+}
+
+lb_status lb_get_populations(lb_sim* s, double* f, int on_device) {
+  if (!s) return fail(nullptr, LB_EINVAL, "sim is NULL");
+  if (!f) return fail(s, LB_EINVAL, "f is NULL");
+  const size_t n = 2 * (size_t)s->Q * (size_t)s->p.N;
+  cudaError_t e;
+  if (s->L->elem == sizeof(double)) {
+    e = cudaMemcpyAsync(f, s->fa, n * sizeof(double), on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+    return e == cudaSuccess ? LB_OK : cuda_fail(s, e, "population copy");
+  }
+  if (on_device) {
+    e = s->L->to_f64(s->fa, f, (long long)n, s->stream);
+    ++s->launches;
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+    return e == cudaSuccess ? LB_OK : cuda_fail(s, e, "population convert");
+  }
+  // One (k, i) plane at a time through the back buffer.
+  const size_t plane = (size_t)s->p.N;
+  for (size_t q = 0; q < 2 * (size_t)s->Q; ++q) {
+    e = s->L->to_f64((const char*)s->fa + q * plane * s->L->elem, (double*)s->fb, (long long)plane, s->stream);
+    ++s->launches;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(f + q * plane, s->fb, plane * sizeof(double), cudaMemcpyDeviceToHost, s->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+    if (e != cudaSuccess) return cuda_fail(s, e, "population download");
+  }
+  return LB_OK;
+}
+
+lb_status lb_set_populations(lb_sim* s, const double* f, int on_device) {
+  if (!s) return fail(nullptr, LB_EINVAL, "sim is NULL");
+  if (!f) return fail(s, LB_EINVAL, "f is NULL");
+  const size_t n = 2 * (size_t)s->Q * (size_t)s->p.N;
+  cudaError_t e;
+  if (s->L->elem == sizeof(double)) {
+    e = cudaMemcpyAsync(s->fa, f, n * sizeof(double), on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+    if (e != cudaSuccess) return cuda_fail(s, e, "population copy");
+  } else if (on_device) {
+    e = s->L->from_f64(f, s->fa, (long long)n, s->stream);
+    ++s->launches;
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+    if (e != cudaSuccess) return cuda_fail(s, e, "population convert");
+  } else {
+    const size_t plane = (size_t)s->p.N;
+    for (size_t q = 0; q < 2 * (size_t)s->Q; ++q) {
+      e = cudaMemcpyAsync(s->fb, f + q * plane, plane * sizeof(double), cudaMemcpyHostToDevice, s->stream);
+      if (e == cudaSuccess) e = s->L->from_f64((const double*)s->fb, (char*)s->fa + q * plane * s->L->elem, (long long)plane, s->stream);
+      ++s->launches;
+      if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+      if (e != cudaSuccess) return cuda_fail(s, e, "population upload");
+    }
+  }
+  s->step = 0;
+  return LB_OK;
+}
+
+void lb_destroy(lb_sim* s) {
+  if (!s) return;
+  cudaStreamSynchronize(s->stream);
+  if (s->owns && s->base) cudaFree(s->base);
+  if (s->host_result) cudaFreeHost(s->host_result);
+  delete s;
+}
+
+const char* lb_last_error(const lb_sim* s) { return s ? s->err : g_err; }
+
+long long lb_kernel_launches(const lb_sim* s) { return s ? s->launches : 0; }
+
+}  // extern "C"

