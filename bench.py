@@ -241,6 +241,8 @@ def main(argv=None):
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=12.0)
+    ap.add_argument("--flush-mb", type=int, default=L2_FLUSH_BYTES >> 20,
+                    help="L2 flush buffer written before every timed step (MB)")
     args = ap.parse_args(argv)
     w = WORKLOADS[args.workload]
     if args.warmup < 3:
@@ -271,7 +273,7 @@ def main(argv=None):
     fl = w["gen"](nx, ny, nz, 1234 + rank)
     rho1 = torch.from_numpy(fl.rho1).cuda()
     rho2 = torch.from_numpy(fl.rho2).cuda()
-    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+    flush = torch.empty(max(1, args.flush_mb) << 20, dtype=torch.uint8, device="cuda")
     torch.cuda.synchronize()
 
     sim = lbnci.Sim(cfg, workspace="torch")
@@ -287,7 +289,8 @@ def main(argv=None):
         launches0 = sim.launches()
         with ClockSampler(local) as clk:
             for k in range(args.steps):
-                flush.fill_(k & 0xFF)  # evict the lattice from L2 before each timed step
+                if args.flush_mb > 0:
+                    flush.fill_(k & 0xFF)  # evict the lattice from L2 before each timed step
                 starts[k].record(stream)
                 sim.step(1)
                 ends[k].record(stream)
@@ -354,7 +357,8 @@ def main(argv=None):
         "scaling": "weak", "vs_baseline": None,
         "dtype": "f32" if prec == lbnci.LB_FP32 else "f64", "data": "synthetic",
         "config": {"workload": w["desc"], "sites": N, "precision": args.precision,
-                   "l2": "flushed (512 MB write) before every timed step; each step timed alone",
+                   "l2": (f"flushed ({args.flush_mb} MB write) before every timed step; each step timed alone"
+                          if args.flush_mb > 0 else "not flushed"),
                    "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU",
                    "droplets": fl.meta.get("droplets"),
                    "fraction": fl.meta.get("area_fraction", fl.meta.get("volume_fraction"))},

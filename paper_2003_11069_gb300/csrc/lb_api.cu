@@ -7,6 +7,7 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 
@@ -38,7 +39,7 @@ cudaError_t reduce_partials(const double* partials, long long nblocks, double* o
   return cudaGetLastError();
 }
 
-long long tiled_blocks(int lattice, const StepParams& p) {
+long long tiled_blocks(int lattice, const HostParams& p) {
   if (lattice == 0) {
     return (long long)((p.nx + Tile<0>::X - 1) / Tile<0>::X) * ((p.ny + Tile<0>::Y - 1) / Tile<0>::Y) *
            ((p.nz + Tile<0>::Z - 1) / Tile<0>::Z);
@@ -53,7 +54,7 @@ using namespace lbnci;
 
 struct lb_sim {
   lb_config cfg;
-  StepParams p;
+  HostParams p;
   const Launchers* L;
   int Q;
   int device;
@@ -95,7 +96,7 @@ struct Layout {
   size_t fa, fb, psi, partials, result, total;
 };
 
-lb_status validate(const lb_config* c, StepParams* p, Layout* lay, long long* nblocks) {
+lb_status validate(const lb_config* c, HostParams* p, Layout* lay, long long* nblocks) {
   if (!c) return fail(nullptr, LB_EINVAL, "config is NULL");
   if (c->lattice != LB_D2Q9 && c->lattice != LB_D3Q27)
     return fail(nullptr, LB_EINVAL, "unknown lattice %d", c->lattice);
@@ -114,21 +115,26 @@ lb_status validate(const lb_config* c, StepParams* p, Layout* lay, long long* nb
     if (!std::isfinite(c->force[a])) return fail(nullptr, LB_EINVAL, "force must be finite");
   int smax = 0;
   if (c->A_h > 0.0) {
-    if (!(c->h_min > 0.0 && c->h_min <= c->h_max && c->h_max < 5.0))
+    if (!(c->h_min > 0.0 && c->h_min <= c->h_max && c->h_max < kMaxProbe + 1.0))
       return fail(nullptr, LB_EINVAL, "NCI needs 0 < h_min <= h_max < 5 (got %g, %g)", c->h_min, c->h_max);
     smax = (int)std::floor(c->h_max);
   }
   const long long N = (long long)c->nx * c->ny * c->nz;
-  if (N > (1LL << 40)) return fail(nullptr, LB_EINVAL, "lattice too large");
+  const int Qc = c->lattice == LB_D2Q9 ? 9 : 27;
+  if (2LL * Qc * N >= (1LL << 32))
+    return fail(nullptr, LB_EINVAL, "lattice too large (2*Q*N must be < 2^32 populations)");
   p->nx = c->nx; p->ny = c->ny; p->nz = c->nz;
   p->wall_y = c->wall_y ? 1 : 0;
   p->wall_z = c->wall_z ? 1 : 0;
-  p->N = N;
+  p->N = (int)N;
   p->tau = c->tau; p->A_s = c->A_s; p->beta = c->beta; p->A_h = c->A_h;
   p->h_min = c->h_min; p->h_max = c->h_max; p->g_th = c->g_th;
   for (int a = 0; a < 3; ++a) p->G[a] = c->force[a];
   if (c->lattice == LB_D2Q9) p->G[2] = 0.0;
   p->smax = smax;
+  // Tile of the fused D2Q9 kernel: LBNCI_FUSED_SPT=2 (32x16, the default) or 4 (32x32).
+  p->spt = 2;
+  if (const char* e = std::getenv("LBNCI_FUSED_SPT")) p->spt = std::atoi(e) == 4 ? 4 : 2;
   const int Q = c->lattice == LB_D2Q9 ? 9 : 27;
   const size_t elem = c->precision == LB_FP64 ? 8 : 4;
   *nblocks = tiled_blocks(c->lattice, *p);
@@ -150,11 +156,11 @@ size_t staging_doubles(const lb_sim* s) {
 // Run the fields kernel on the current state with the given device outputs and
 // fill s->host_result with the reduced observables (synchronises the stream).
 lb_status run_fields(lb_sim* s, const FieldOut& outs) {
-  cudaError_t e = s->L->moments(s->fa, s->psi, s->p, s->stream);
-  if (e != cudaSuccess) return cuda_fail(s, e, "moments launch");
   FieldOut fo = outs;
   fo.partials = s->partials;
-  e = s->L->fields(s->fa, s->psi, s->p, fo, s->stream);
+  int nk = 0;
+  cudaError_t e = s->L->fields(s->fa, s->psi, s->p, fo, s->stream, &nk);
+  s->launches += nk + 1;
   if (e != cudaSuccess) return cuda_fail(s, e, "fields launch");
   e = reduce_partials(s->partials, s->nblocks, s->result, s->stream);
   if (e != cudaSuccess) return cuda_fail(s, e, "reduce launch");
@@ -171,7 +177,7 @@ extern "C" {
 
 lb_status lb_workspace_size(const lb_config* cfg, size_t* bytes) {
   if (!bytes) return fail(nullptr, LB_EINVAL, "bytes is NULL");
-  StepParams p;
+  HostParams p;
   Layout lay;
   long long nb;
   lb_status st = validate(cfg, &p, &lay, &nb);
@@ -183,7 +189,7 @@ lb_status lb_workspace_size(const lb_config* cfg, size_t* bytes) {
 lb_status lb_create(const lb_config* cfg, lb_sim** out) {
   if (!out) return fail(nullptr, LB_EINVAL, "out is NULL");
   *out = nullptr;
-  StepParams p;
+  HostParams p;
   Layout lay;
   long long nblocks;
   lb_status st = validate(cfg, &p, &lay, &nblocks);
@@ -262,7 +268,7 @@ lb_status lb_init_fields(lb_sim* s, const double* rho1, const double* rho2, cons
     if (e != cudaSuccess) return cuda_fail(s, e, "field upload");
     d1 = st; d2 = st + N; du = u ? st + 2 * N : nullptr;
   }
-  e = s->L->init(s->fa, d1, d2, du, N, s->stream);
+  e = s->L->init(s->fa, d1, d2, du, s->p, s->stream);
   ++s->launches;
   if (e != cudaSuccess) return cuda_fail(s, e, "init launch");
   if (!on_device) {
@@ -277,11 +283,10 @@ lb_status lb_step(lb_sim* s, long long nsteps) {
   if (!s) return fail(nullptr, LB_EINVAL, "sim is NULL");
   if (nsteps < 0) return fail(s, LB_EINVAL, "nsteps must be >= 0");
   for (long long t = 0; t < nsteps; ++t) {
-    cudaError_t e = s->L->moments(s->fa, s->psi, s->p, s->stream);
-    if (e != cudaSuccess) return cuda_fail(s, e, "moments launch");
-    e = s->L->collide(s->fa, s->fb, s->psi, s->p, s->stream);
-    if (e != cudaSuccess) return cuda_fail(s, e, "collide launch");
-    s->launches += 2;
+    int nk = 0;
+    cudaError_t e = s->L->step(s->fa, s->fb, s->psi, s->p, s->stream, &nk);
+    s->launches += nk;
+    if (e != cudaSuccess) return cuda_fail(s, e, "step launch");
     std::swap(s->fa, s->fb);
     ++s->step;
   }
@@ -295,7 +300,6 @@ lb_status lb_fields(lb_sim* s, double* rho1, double* rho2, double* psi, double* 
   if (on_device) {
     FieldOut fo{rho1, rho2, psi, grad, frep, hit, u, nullptr};
     lb_status st = run_fields(s, fo);
-    s->launches += 3;
     if (st != LB_OK) return st;
     return s->host_result[9] > 0 ? fail(s, LB_ENUMERIC, "non-finite or non-positive density at %.0f sites", s->host_result[9]) : LB_OK;
   }
@@ -320,7 +324,6 @@ lb_status lb_fields(lb_sim* s, double* rho1, double* rho2, double* psi, double* 
       case 6: fo.u = st; break;
     }
     lb_status stt = run_fields(s, fo);
-    s->launches += 3;
     if (stt != LB_OK) return stt;
     cudaError_t e = cudaMemcpy(r.host, st, r.bytes, cudaMemcpyDeviceToHost);
     if (e != cudaSuccess) return cuda_fail(s, e, "field download");
@@ -328,7 +331,6 @@ lb_status lb_fields(lb_sim* s, double* rho1, double* rho2, double* psi, double* 
   if (!any) {
     FieldOut fo{};
     lb_status st = run_fields(s, fo);
-    s->launches += 3;
     if (st != LB_OK) return st;
   }
   return s->host_result[9] > 0 ? fail(s, LB_ENUMERIC, "non-finite or non-positive density at %.0f sites", s->host_result[9]) : LB_OK;

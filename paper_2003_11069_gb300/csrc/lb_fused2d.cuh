@@ -1,0 +1,155 @@
+// lb_fused2d.cuh -- the whole D2Q9 step in one pass over the populations.
+//
+// A 256-thread block owns a 32 x (8*SPT) tile; each thread owns SPT sites of one
+// column and keeps their 18 pulled populations in registers from the first phase to
+// the collision, so each population is read from memory once for the collision.
+//   phase 1: pull own sites (registers) and the psi halo of radius smax+1 (the halo's
+//            populations are pulled, reduced to psi and dropped; neighbouring blocks
+//            read the same lines, which L2 serves);
+//   phase 2: unit normal n = -grad psi/|grad psi| and |grad psi| for the tile and a
+//            halo of radius smax, once per cell, into shared memory;
+//   phase 3: NCI ray search over the shared (n, |grad psi|) cells, Guo velocity,
+//            BGK + source + perturbation, recolouring, store.
+// Arithmetic is expression-for-expression that of the tiled kernel, so the FP64
+// instantiation rounds like the oracle.
+#pragma once
+
+#include "lb_kernels.cuh"
+
+namespace lbnci {
+
+template <typename T>
+size_t fused2d_smem_bytes(int smax, int spt) {
+  const int R = smax + 1;
+  const int TY = kFusedThreadsY * spt;
+  const size_t psi = (size_t)(kFusedTX + 2 * R) * (TY + 2 * R);
+  const size_t ng = 3 * (size_t)(kFusedTX + 2 * smax) * (TY + 2 * smax);
+  return sizeof(T) * (psi + ng);
+}
+
+template <typename T, int SPT>
+__global__ void __launch_bounds__(256, SPT <= 2 ? 2 : 1)
+fused2d_kernel(const T* __restrict__ f, T* __restrict__ fout, StepT<T> p) {
+  constexpr int Q = 9, TX = kFusedTX, TYT = kFusedThreadsY, TY = TYT * SPT;
+  constexpr int NT = TX * TYT;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int S = p.smax, R = S + 1;
+  const int RX = TX + 2 * R, RY = TY + 2 * R;
+  const int GX = TX + 2 * S, GY = TY + 2 * S, GXY = GX * GY;
+  T* s_psi = reinterpret_cast<T*>(smem_raw);
+  T* s_ng = s_psi + RX * RY;  // [3][GXY]: n_x, n_y, |grad psi|
+  const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
+  const int tx = threadIdx.x, ty = threadIdx.y, tid = tx + TX * ty;
+
+  // phase 1: own sites into registers, their psi into shared memory; an own position
+  // beyond a ragged lattice edge holds the psi of the site it wraps to
+  T fin[SPT][2][Q];
+  bool act[SPT];
+#pragma unroll
+  for (int s = 0; s < SPT; ++s) {
+    const int x = x0 + tx, y = y0 + ty + s * TYT;
+    act[s] = x < p.nx && y < p.ny;
+    const int c = (tx + R) + RX * (ty + s * TYT + R);
+    if (act[s]) {
+      pull_site<0, T>(f, x, y, 0, p, fin[s]);
+      s_psi[c] = psi_of<Q, T>(fin[s]);
+    } else {
+      const int gx = wrapn(x, p.nx);
+      int gy = y;
+      if (!p.wall_y) gy = wrapn(gy, p.ny);
+      if (gy < p.ny) {
+        T h[2][Q];
+        pull_site<0, T>(f, gx, gy, 0, p, h);
+        s_psi[c] = psi_of<Q, T>(h);
+      }
+    }
+  }
+  // the halo ring of width R, enumerated compactly: two bands of R full rows, then
+  // the R-wide left and right sides of the tile rows
+  {
+    const unsigned mRX = 0xFFFFFFFFu / (unsigned)RX + 1u;       // h / RX == umulhi(h, mRX)
+    const unsigned m2R = 0xFFFFFFFFu / (unsigned)(2 * R) + 1u;  // exact for h < 2^16
+    const int nband = R * RX, nside = 2 * R * TY;
+    for (int h = tid; h < 2 * nband + nside; h += NT) {
+      int lx, ly;
+      if (h < 2 * nband) {
+        const int hb = h < nband ? h : h - nband;
+        const int row = (int)__umulhi((unsigned)hb, mRX);
+        lx = hb - row * RX;
+        ly = h < nband ? row : R + TY + row;
+      } else {
+        const int hs = h - 2 * nband;
+        const int row = (int)__umulhi((unsigned)hs, m2R);
+        const int col = hs - row * 2 * R;
+        lx = col < R ? col : col + TX;
+        ly = R + row;
+      }
+      const int gx = wrapn(x0 - R + lx, p.nx);
+      int gy = y0 - R + ly;
+      if (p.wall_y) { if (gy < 0 || gy >= p.ny) continue; } else gy = wrapn(gy, p.ny);
+      T hf[2][Q];
+      pull_site<0, T>(f, gx, gy, 0, p, hf);
+      s_psi[lx + RX * ly] = psi_of<Q, T>(hf);
+    }
+  }
+  __syncthreads();
+
+  // phase 2: n and |grad psi| of every cell within smax of the tile
+  for_region(tid, NT, GX, GY, 1, [&](int c, int lx, int ly, int) {
+    int gy = y0 - S + ly;
+    if (p.wall_y) { if (gy < 0 || gy >= p.ny) return; } else gy = wrapn(gy, p.ny);
+    T grad[3], n[3];
+    grad_smem<0, T>(s_psi, RX, 0, (lx + 1) + RX * (ly + 1), gy, 0, p, grad);
+    const T g = M<T>::unit(grad, n);
+    s_ng[c] = n[0];
+    s_ng[GXY + c] = n[1];
+    s_ng[2 * GXY + c] = g;
+  });
+  __syncthreads();
+
+  // phase 3: NCI, forcing, collision, recolouring, store
+#pragma unroll
+  for (int s = 0; s < SPT; ++s) {
+    if (!act[s]) continue;
+    const int x = x0 + tx, y = y0 + ty + s * TYT;
+    const int idx = x + p.nx * y;
+    const int c = (tx + S) + GX * (ty + s * TYT + S);
+    const T n0 = s_ng[c], n1 = s_ng[GXY + c], g = s_ng[2 * GXY + c];
+    T rho1, rho2;
+    psi_of<Q, T>(fin[s], &rho1, &rho2);
+    const T rho = rho1 + rho2;
+    T j[3];
+    momentum<0, T>(fin[s], j);
+    T frep[3] = {T(0), T(0), T(0)};
+    if (S > 0 && g > p.g_th) {
+      int hit = 0;
+#pragma unroll
+      for (int st = 1; st <= kMaxProbe; ++st) {
+        if (st > S) break;
+        const int dx = round_probe<T>(T(st) * n0);
+        const int dy = round_probe<T>(T(st) * n1);
+        const int py = y + dy;
+        if (p.wall_y && (py < 0 || py >= p.ny)) break;
+        const int cp = c + dx + GX * dy;
+        if (!(s_ng[2 * GXY + cp] > p.g_th)) continue;
+        const T dot = s_ng[cp] * n0 + s_ng[GXY + cp] * n1;
+        if (dot < T(0)) { hit = st; break; }
+      }
+      if (hit) {
+        const T A = p.Ah[hit];
+        const T deltaI = T(0.5) * g;
+        frep[0] = -A * n0 * deltaI;
+        frep[1] = -A * n1 * deltaI;
+      }
+    }
+    T F[3], u[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) F[a] = p.G[a] + frep[a];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) u[a] = M<T>::div(j[a] + T(0.5) * F[a], rho);
+    const T m[3] = {-n0, -n1, T(0)};
+    collide_store<0, T>(fin[s], rho1, rho2, u, F, g, m, p, fout, idx);
+  }
+}
+
+}  // namespace lbnci

@@ -1,134 +1,250 @@
 // lb_kernels.cuh -- CUDA kernels of one colour-gradient NCI lattice Boltzmann step
 // (arXiv:2003.11069, "Materials and Methods"), templated on the lattice and on the
 // storage/compute type T (double or float). Instantiated by lb_fp64.cu (compiled
-// without multiply-add contraction, the parity path) and lb_fp32.cu.
+// without multiply-add contraction: the parity path) and lb_fp32.cu.
 //
-// Step = two launches:
-//   moments_kernel : pull-stream the post-collision state, rho_k = sum_i f_i^k,
-//                    psi = (rho1 - rho2)/(rho1 + rho2)  -> psi[N]
-//   collide_kernel : stage the psi tile + halo of radius smax+1 in shared memory,
-//                    gradient (isotropic, 2nd order), NCI ray search and F_rep,
-//                    Guo velocity, BGK + Guo source + perturbation, recolouring,
-//                    write f* to the other buffer.
-// The fields variant of collide_kernel writes the macroscopic fields and block
-// partial sums instead of populations.
+// Per-site stages, in the paper's order:
+//   pull-stream with halfway bounce-back             Eq. (CGLBE)
+//   rho_k = sum_i f_i^k, psi = (rho1-rho2)/(rho1+rho2)
+//   isotropic gradient of psi, n = -grad psi/|grad psi|, delta_I = |grad psi|/2
+//   NCI ray search, F_rep = -A_h(h) n delta_I         Eq. (near_c)
+//   Guo velocity, BGK + Guo source + perturbation, recolouring (Omega^(3)[Omega^(1)+Omega^(2)])
+//
+// Kernels:
+//   fused2d_kernel  : the D2Q9 step in one pass (lb_fused2d.cuh)
+//   moments_kernel  : psi of the streamed state (3D step and the fields path)
+//   tiled_kernel    : gradient + NCI + collision from a psi array staged in shared
+//                     memory; FIELDS variant writes macroscopic fields and partial sums
 #pragma once
 
 #include "lb_lattice.cuh"
 
 namespace lbnci {
 
-template <typename T> __device__ __forceinline__ T tround(T v);
-template <> __device__ __forceinline__ double tround<double>(double v) { return round(v); }
-template <> __device__ __forceinline__ float tround<float>(float v) { return roundf(v); }
-template <typename T> __device__ __forceinline__ T tsqrt(T v);
-template <> __device__ __forceinline__ double tsqrt<double>(double v) { return sqrt(v); }
-template <> __device__ __forceinline__ float tsqrt<float>(float v) { return sqrtf(v); }
-
-// Wrap a coordinate that is at most one period out of range.
-__device__ __forceinline__ int wrap1(int v, int n) { return v < 0 ? v + n : (v >= n ? v - n : v); }
-// Wrap any coordinate into [0, n).
-__device__ __forceinline__ int wrapn(int v, int n) { int r = v % n; return r < 0 ? r + n : r; }
-
-// Pull population i of component k into site (x,y,z): from the upstream site, or,
-// when that lies beyond a wall, the opposite population of the site itself
-// (halfway bounce-back).
-template <int LAT, typename T>
-__device__ __forceinline__ T pull(const T* __restrict__ f, int k, int i, int x, int y, int z,
-                                  long long idx, const StepParams& p) {
-  constexpr int Q = Lattice<LAT>::Q;
-  const int sx = wrap1(x - cc(i, 0), p.nx);
-  int sy = y - cc(i, 1);
-  int sz = z - cc(i, 2);
-  bool wall = false;
-  if (p.wall_y) wall |= (sy < 0 || sy >= p.ny); else sy = wrap1(sy, p.ny);
-  if (Lattice<LAT>::D == 3) {
-    if (p.wall_z) wall |= (sz < 0 || sz >= p.nz); else sz = wrap1(sz, p.nz);
-  } else {
-    sz = 0;
+// FP64: IEEE operations only (round exactly as the oracle's C does).
+// FP32: fast intrinsics where the result feeds no bit-exact comparison.
+template <typename T> struct M;
+template <> struct M<double> {
+  static __device__ __forceinline__ double div(double a, double b) { return a / b; }
+  // |g| and the unit vector -g/|g| (0 when g = 0)
+  static __device__ __forceinline__ double unit(const double g[3], double n[3]) {
+    const double gn = ::sqrt(g[0] * g[0] + g[1] * g[1] + g[2] * g[2]);
+    if (gn > 0.0) { n[0] = -g[0] / gn; n[1] = -g[1] / gn; n[2] = -g[2] / gn; }
+    else { n[0] = 0.0; n[1] = 0.0; n[2] = 0.0; }
+    return gn;
   }
-  const size_t N = (size_t)p.N;
-  if (wall) return f[(size_t)(k * Q + opposite(i)) * N + (size_t)idx];
-  const long long src = (long long)sx + (long long)p.nx * ((long long)sy + (long long)p.ny * sz);
-  return f[(size_t)(k * Q + i) * N + (size_t)src];
+};
+template <> struct M<float> {
+  static __device__ __forceinline__ float div(float a, float b) { return __fdividef(a, b); }
+  static __device__ __forceinline__ float unit(const float g[3], float n[3]) {
+    const float g2 = g[0] * g[0] + g[1] * g[1] + g[2] * g[2];
+    if (g2 > 0.0f) {
+      const float inv = rsqrtf(g2);
+      n[0] = -g[0] * inv; n[1] = -g[1] * inv; n[2] = -g[2] * inv;
+      return g2 * inv;
+    }
+    n[0] = 0.0f; n[1] = 0.0f; n[2] = 0.0f;
+    return 0.0f;
+  }
+};
+
+// Round half away from zero for |v| < kMaxProbe + 1/2, by comparisons only (no
+// float-to-int conversion): the probe offset round(s n_a) of the NCI ray search.
+template <typename T>
+__device__ __forceinline__ int round_probe(T v) {
+  const T a = v < T(0) ? -v : v;
+  const int m = (a >= T(0.5)) + (a >= T(1.5)) + (a >= T(2.5)) + (a >= T(3.5));
+  return v < T(0) ? -m : m;
 }
 
-template <int LAT, typename T>
-__global__ void __launch_bounds__(256) moments_kernel(const T* __restrict__ f, T* __restrict__ psi,
-                                                      StepParams p) {
-  constexpr int Q = Lattice<LAT>::Q;
-  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= p.N) return;
-  const int x = (int)(idx % p.nx);
-  const int y = (int)((idx / p.nx) % p.ny);
-  const int z = (int)(idx / ((long long)p.nx * p.ny));
-  T r[2] = {T(0), T(0)};
-#pragma unroll
-  for (int k = 0; k < 2; ++k) {
-#pragma unroll
-    for (int i = 0; i < Q; ++i) r[k] += pull<LAT, T>(f, k, i, x, y, z, idx, p);
-  }
-  psi[idx] = (r[0] - r[1]) / (r[0] + r[1]);
+// Wrap a coordinate into [0, n) (a few periods at most; no integer division).
+__device__ __forceinline__ int wrapn(int v, int n) {
+  while (v < 0) v += n;
+  while (v >= n) v -= n;
+  return v;
 }
 
-// Isotropic gradient (1/c_s^2) sum_i w_i c_i psi(x + c_i) from the shared-memory
-// region; a neighbour beyond a wall is replaced by its mirror image across the wall
-// plane (the crossing velocity components are dropped). (lx,ly,lz): region
-// coordinates, (gy,gz): global coordinates for the wall test.
+// Visit the cells c = tid, tid + NT, ... of an RX x RY x RZ region together with
+// their coordinates (lx, ly, lz), stepping the coordinates incrementally so that the
+// loop itself needs no integer division.
+template <typename F>
+__device__ __forceinline__ void for_region(int tid, int NT, int RX, int RY, int RZ, F&& fn) {
+  const int total = RX * RY * RZ;
+  int lx = tid % RX, ly = (tid / RX) % RY, lz = tid / (RX * RY);
+  const int sx = NT % RX, sy = (NT / RX) % RY, sz = NT / (RX * RY);
+  for (int c = tid; c < total; c += NT) {
+    fn(c, lx, ly, lz);
+    lx += sx; ly += sy; lz += sz;
+    if (lx >= RX) { lx -= RX; ++ly; }
+    if (ly >= RY) { ly -= RY; ++lz; }
+  }
+}
+
+// Pull the 2Q populations of site (x,y,z) from the post-collision state: from the
+// upstream site x - c_i, or, when that lies beyond a wall, the opposite population
+// of the site itself (halfway bounce-back).
 template <int LAT, typename T>
-__device__ __forceinline__ void grad_at(const T* __restrict__ sp, int RX, int RY, int lx, int ly,
-                                        int lz, int gy, int gz, const StepParams& p, T g[3]) {
+__device__ __forceinline__ void pull_site(const T* __restrict__ f, int x, int y, int z, const StepT<T>& p,
+                                          T out[2][Lattice<LAT>::Q]) {
   constexpr int Q = Lattice<LAT>::Q;
+  constexpr bool D3 = Lattice<LAT>::D == 3;
+  const unsigned N = (unsigned)p.N;  // 2*Q*N < 2^32 is checked at creation
+  const int xm = x == 0 ? p.nx - 1 : x - 1, xp = x == p.nx - 1 ? 0 : x + 1;
+  int ym, yp, zm = 0, zp = 0;
+  bool bym = false, byp = false, bzm = false, bzp = false;
+  if (p.wall_y) { ym = y - 1; yp = y + 1; bym = y == 0; byp = y == p.ny - 1; }
+  else { ym = y == 0 ? p.ny - 1 : y - 1; yp = y == p.ny - 1 ? 0 : y + 1; }
+  if (D3) {
+    if (p.wall_z) { zm = z - 1; zp = z + 1; bzm = z == 0; bzp = z == p.nz - 1; }
+    else { zm = z == 0 ? p.nz - 1 : z - 1; zp = z == p.nz - 1 ? 0 : z + 1; }
+  }
+  const int idx = x + p.nx * (y + p.ny * z);
+  static_for<Q>([&](auto I) {
+    constexpr int i = decltype(I)::value;
+    constexpr int cx = cc(i, 0), cy = cc(i, 1), cz = cc(i, 2);
+    bool bounce = (cy == 1 && bym) || (cy == -1 && byp);
+    if (D3) bounce = bounce || (cz == 1 && bzm) || (cz == -1 && bzp);
+    const int sx = cx == 1 ? xm : (cx == -1 ? xp : x);
+    const int sy = cy == 1 ? ym : (cy == -1 ? yp : y);
+    const int sz = D3 ? (cz == 1 ? zm : (cz == -1 ? zp : z)) : 0;
+    const int src = sx + p.nx * (sy + p.ny * sz);
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+      const unsigned off = bounce ? (unsigned)(k * Q + opposite(i)) * N + (unsigned)idx
+                                  : (unsigned)(k * Q + i) * N + (unsigned)src;
+      out[k][i] = f[off];
+    }
+  });
+}
+
+// psi = (rho1 - rho2)/(rho1 + rho2) of pulled populations (sums in direction order).
+template <int Q, typename T>
+__device__ __forceinline__ T psi_of(const T fin[2][Q], T* r1out = nullptr, T* r2out = nullptr) {
+  T r1 = T(0), r2 = T(0);
+#pragma unroll
+  for (int i = 0; i < Q; ++i) r1 += fin[0][i];
+#pragma unroll
+  for (int i = 0; i < Q; ++i) r2 += fin[1][i];
+  if (r1out) *r1out = r1;
+  if (r2out) *r2out = r2;
+  return M<T>::div(r1 - r2, r1 + r2);
+}
+
+// Isotropic gradient (1/c_s^2) sum_i w_i c_i psi(x + c_i) from a shared-memory psi
+// region with strides (1, RX, RX*RY); a neighbour beyond a wall is replaced by its
+// mirror image across the wall plane (the crossing velocity components are dropped).
+// (gy, gz): global coordinates of the cell, for the wall test.
+template <int LAT, typename T>
+__device__ __forceinline__ void grad_smem(const T* __restrict__ sp, int RX, int RXY, int c, int gy, int gz,
+                                          const StepT<T>& p, T g[3]) {
+  constexpr int Q = Lattice<LAT>::Q;
+  constexpr bool D3 = Lattice<LAT>::D == 3;
   g[0] = T(0); g[1] = T(0); g[2] = T(0);
   const bool ylo = p.wall_y && gy == 0, yhi = p.wall_y && gy == p.ny - 1;
-  const bool zlo = Lattice<LAT>::D == 3 && p.wall_z && gz == 0;
-  const bool zhi = Lattice<LAT>::D == 3 && p.wall_z && gz == p.nz - 1;
-#pragma unroll
-  for (int i = 1; i < Q; ++i) {
-    int dy = cc(i, 1), dz = cc(i, 2);
-    if ((dy < 0 && ylo) || (dy > 0 && yhi)) dy = 0;
-    if ((dz < 0 && zlo) || (dz > 0 && zhi)) dz = 0;
-    const T v = sp[(lx + cc(i, 0)) + RX * ((ly + dy) + RY * (lz + dz))];
-    if (cc(i, 0) != 0) g[0] += T(Lattice<LAT>::w(i) * cc(i, 0)) * v;
-    if (cc(i, 1) != 0) g[1] += T(Lattice<LAT>::w(i) * cc(i, 1)) * v;
-    if (Lattice<LAT>::D == 3 && cc(i, 2) != 0) g[2] += T(Lattice<LAT>::w(i) * cc(i, 2)) * v;
-  }
+  const bool zlo = D3 && p.wall_z && gz == 0, zhi = D3 && p.wall_z && gz == p.nz - 1;
+  static_for<Q>([&](auto I) {
+    constexpr int i = decltype(I)::value;
+    if constexpr (i > 0) {
+      constexpr T wx = T(Lattice<LAT>::w(i) * cc(i, 0));
+      constexpr T wy = T(Lattice<LAT>::w(i) * cc(i, 1));
+      constexpr T wz = T(Lattice<LAT>::w(i) * cc(i, 2));
+      int dy = cc(i, 1), dz = cc(i, 2);
+      if ((dy < 0 && ylo) || (dy > 0 && yhi)) dy = 0;
+      if ((dz < 0 && zlo) || (dz > 0 && zhi)) dz = 0;
+      const T v = sp[c + cc(i, 0) + RX * dy + RXY * dz];
+      if constexpr (cc(i, 0) != 0) g[0] += wx * v;
+      if constexpr (cc(i, 1) != 0) g[1] += wy * v;
+      if constexpr (D3 && cc(i, 2) != 0) g[2] += wz * v;
+    }
+  });
   g[0] = T(3) * g[0];
   g[1] = T(3) * g[1];
   g[2] = T(3) * g[2];
 }
 
-template <typename T>
-__device__ __forceinline__ T norm3(const T g[3]) {
-  return tsqrt<T>(g[0] * g[0] + g[1] * g[1] + g[2] * g[2]);
+
+// Guo velocity u = (j + F/2)/rho with j = sum_k sum_i f_i^k c_i.
+template <int LAT, typename T>
+__device__ __forceinline__ void momentum(const T fin[2][Lattice<LAT>::Q], T j[3]) {
+  constexpr int Q = Lattice<LAT>::Q;
+  j[0] = T(0); j[1] = T(0); j[2] = T(0);
+  static_for<Q>([&](auto I) {
+    constexpr int i = decltype(I)::value;
+    const T fi = fin[0][i] + fin[1][i];
+    if constexpr (cc(i, 0) != 0) j[0] += cc(i, 0) > 0 ? fi : -fi;
+    if constexpr (cc(i, 1) != 0) j[1] += cc(i, 1) > 0 ? fi : -fi;
+    if constexpr (Lattice<LAT>::D == 3 && cc(i, 2) != 0) j[2] += cc(i, 2) > 0 ? fi : -fi;
+  });
 }
 
-// A_h(h): A for h <= h_min, A (h_min/h)^3 for h_min < h <= h_max, 0 beyond (Eq. near_c).
-template <typename T>
-__device__ __forceinline__ T nci_strength(int h, const StepParams& p) {
-  const T hd = T(h);
-  if (hd <= T(p.h_min)) return T(p.A_h);
-  if (hd <= T(p.h_max)) {
-    const T r = T(p.h_min) / hd;
-    return T(p.A_h) * (r * r * r);
-  }
-  return T(0);
+// BGK relaxation towards f_eq(rho, u) with the Guo source, plus the perturbation
+// (A_s/2)|grad psi| [w_i (c_i.m)^2 - w_i/3] of each component, on the total
+// population; then recolouring f^1 = (rho1/rho) f* + beta rho1 rho2/rho w_i cos(theta_i),
+// f^2 = (rho2/rho) f* - same, cos(theta_i) = c_i.m/|c_i|. m = grad psi/|grad psi|.
+template <int LAT, typename T>
+__device__ __forceinline__ void collide_store(const T fin[2][Lattice<LAT>::Q], T rho1, T rho2, const T u[3],
+                                              const T F[3], T g, const T m[3], const StepT<T>& p,
+                                              T* __restrict__ fout, int idx) {
+  constexpr int Q = Lattice<LAT>::Q;
+  const unsigned N = (unsigned)p.N;
+  const T rho = rho1 + rho2;
+  const T uF = u[0] * F[0] + u[1] * F[1] + u[2] * F[2];
+  const T uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+  const T seg = M<T>::div(p.beta * rho1 * rho2, rho);
+  const T pamp = p.pamp * g;
+  const T c1 = M<T>::div(rho1, rho), c2 = M<T>::div(rho2, rho);
+  static_for<Q>([&](auto I) {
+    constexpr int i = decltype(I)::value;
+    constexpr T w = T(Lattice<LAT>::w(i));
+    constexpr T cx = T(cc(i, 0)), cy = T(cc(i, 1)), cz = T(cc(i, 2));
+    constexpr T w3 = w / T(3);
+    constexpr T inv_len = speed2(i) == 0 ? T(0)
+                        : T(1) / (speed2(i) == 1 ? T(1) : (speed2(i) == 2 ? T(1.4142135623730951)
+                                                                           : T(1.7320508075688772)));
+    const T fi = fin[0][i] + fin[1][i];
+    const T cu = cx * u[0] + cy * u[1] + cz * u[2];
+    const T cF = cx * F[0] + cy * F[1] + cz * F[2];
+    const T cm = cx * m[0] + cy * m[1] + cz * m[2];
+    const T S = p.guo * w * (T(3) * (cF - uF) + T(9) * cu * cF);
+    const T feq = w * rho * (T(1) + T(3) * cu + T(4.5) * cu * cu - T(1.5) * uu);
+    T fs = fi - p.omega * (fi - feq) + S;
+    fs += pamp * (w * cm * cm - w3);
+    const T rc = seg * w * (cm * inv_len);
+    fout[(unsigned)i * N + (unsigned)idx] = c1 * fs + rc;
+    fout[(unsigned)(Q + i) * N + (unsigned)idx] = c2 * fs - rc;
+  });
 }
 
+// ---------------------------------------------------------------------------- moments
+template <int LAT, typename T>
+__global__ void __launch_bounds__(256) moments_kernel(const T* __restrict__ f, T* __restrict__ psi, StepT<T> p) {
+  constexpr int Q = Lattice<LAT>::Q;
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= p.N) return;
+  const int x = idx % p.nx;
+  const int y = (idx / p.nx) % p.ny;
+  const int z = idx / (p.nx * p.ny);
+  T fin[2][Q];
+  pull_site<LAT, T>(f, x, y, z, p, fin);
+  psi[idx] = psi_of<Q, T>(fin);
+}
+
+// ---------------------------------------------------------------------------- tiled
 template <int LAT> __host__ __device__ constexpr int region_rz(int R) {
   return Lattice<LAT>::D == 3 ? Tile<LAT>::Z + 2 * R : 1;
 }
 
 template <int LAT, typename T>
-size_t collide_smem_bytes(int smax) {
+size_t tiled_smem_bytes(int smax) {
   const int R = smax + 1;
   return sizeof(T) * (size_t)(Tile<LAT>::X + 2 * R) * (Tile<LAT>::Y + 2 * R) * region_rz<LAT>(R);
 }
 
+// Gradient, NCI and collision from a psi array: the psi tile and its halo of radius
+// smax+1 are staged in shared memory; probes recompute the gradient there.
 template <int LAT, typename T, bool FIELDS>
 __global__ void __launch_bounds__(256)
-collide_kernel(const T* __restrict__ f, T* __restrict__ fout, const T* __restrict__ psi,
-               StepParams p, FieldOut fo) {
+tiled_kernel(const T* __restrict__ f, T* __restrict__ fout, const T* __restrict__ psi, StepT<T> p, FieldOut fo) {
   constexpr int D = Lattice<LAT>::D;
   constexpr int Q = Lattice<LAT>::Q;
   constexpr int TX = Tile<LAT>::X, TY = Tile<LAT>::Y, TZ = Tile<LAT>::Z;
@@ -137,22 +253,20 @@ collide_kernel(const T* __restrict__ f, T* __restrict__ fout, const T* __restric
 
   const int R = p.smax + 1;
   const int RX = TX + 2 * R, RY = TY + 2 * R, RZ = region_rz<LAT>(R);
+  const int RXY = RX * RY;
   const int RZoff = D == 3 ? R : 0;
   const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY, z0 = blockIdx.z * TZ;
   const int tid = threadIdx.x + TX * (threadIdx.y + TY * threadIdx.z);
 
-  // Stage psi of the tile and its halo (periodic wrap; cells beyond a wall are never read).
-  const int ncell = RX * RY * RZ;
-  for (int t = tid; t < ncell; t += TX * TY * TZ) {
-    const int lx = t % RX, ly = (t / RX) % RY, lz = t / (RX * RY);
+  for_region(tid, TX * TY * TZ, RX, RY, RZ, [&](int t, int lx, int ly, int lz) {
     const int gx = wrapn(x0 - R + lx, p.nx);
     int gy = y0 - R + ly;
     int gz = D == 3 ? z0 - RZoff + lz : 0;
     bool out = false;
     if (p.wall_y) out |= (gy < 0 || gy >= p.ny); else gy = wrapn(gy, p.ny);
     if (D == 3) { if (p.wall_z) out |= (gz < 0 || gz >= p.nz); else gz = wrapn(gz, p.nz); }
-    sp[t] = out ? T(0) : psi[(long long)gx + (long long)p.nx * ((long long)gy + (long long)p.ny * gz)];
-  }
+    sp[t] = out ? T(0) : psi[gx + p.nx * (gy + p.ny * gz)];
+  });
   __syncthreads();
 
   const int x = x0 + threadIdx.x, y = y0 + threadIdx.y, z = z0 + threadIdx.z;
@@ -162,77 +276,58 @@ collide_kernel(const T* __restrict__ f, T* __restrict__ fout, const T* __restric
   if (FIELDS) for (int q = 0; q < kRedSlots; ++q) red[q] = 0.0;
 
   if (active) {
-    const long long idx = (long long)x + (long long)p.nx * ((long long)y + (long long)p.ny * z);
-    const size_t N = (size_t)p.N;
-    // 1. pull
+    const int idx = x + p.nx * (y + p.ny * z);
+    const unsigned N = (unsigned)p.N;
     T fin[2][Q];
-#pragma unroll
-    for (int k = 0; k < 2; ++k)
-#pragma unroll
-      for (int i = 0; i < Q; ++i) fin[k][i] = pull<LAT, T>(f, k, i, x, y, z, idx, p);
-    // 2. moments
-    T rho1 = T(0), rho2 = T(0);
-#pragma unroll
-    for (int i = 0; i < Q; ++i) rho1 += fin[0][i];
-#pragma unroll
-    for (int i = 0; i < Q; ++i) rho2 += fin[1][i];
+    pull_site<LAT, T>(f, x, y, z, p, fin);
+    T rho1, rho2;
+    const T psi_own = psi_of<Q, T>(fin, &rho1, &rho2);
     const T rho = rho1 + rho2;
-    T j[3] = {T(0), T(0), T(0)};
-#pragma unroll
-    for (int i = 0; i < Q; ++i) {
-      const T fi = fin[0][i] + fin[1][i];
-      if (cc(i, 0) != 0) j[0] += cc(i, 0) > 0 ? fi : -fi;
-      if (cc(i, 1) != 0) j[1] += cc(i, 1) > 0 ? fi : -fi;
-      if (D == 3 && cc(i, 2) != 0) j[2] += cc(i, 2) > 0 ? fi : -fi;
-    }
-    // 3. gradient, normal
-    const int lx = threadIdx.x + R, ly = threadIdx.y + R, lz = threadIdx.z + RZoff;
-    T grad[3];
-    grad_at<LAT, T>(sp, RX, RY, lx, ly, lz, y, z, p, grad);
-    const T g = norm3<T>(grad);
-    // 4. NCI ray search along n = -grad psi/|grad psi|
+    T j[3];
+    momentum<LAT, T>(fin, j);
+    const int c0 = (threadIdx.x + R) + RX * (threadIdx.y + R) + RXY * (threadIdx.z + RZoff);
+    T grad[3], n[3];
+    grad_smem<LAT, T>(sp, RX, RXY, c0, y, z, p, grad);
+    const T g = M<T>::unit(grad, n);
     T frep[3] = {T(0), T(0), T(0)};
     int hit = 0;
-    const bool iface = g > T(p.g_th);
+    const bool iface = g > p.g_th;
     if (p.smax > 0 && iface) {
-      T n[3];
-      n[0] = -grad[0] / g;
-      n[1] = -grad[1] / g;
-      n[2] = D == 3 ? -grad[2] / g : T(0);
-      for (int s = 1; s <= p.smax; ++s) {
-        const int dx = (int)tround<T>(T(s) * n[0]);
-        const int dy = (int)tround<T>(T(s) * n[1]);
-        const int dz = D == 3 ? (int)tround<T>(T(s) * n[2]) : 0;
+#pragma unroll
+      for (int s = 1; s <= kMaxProbe; ++s) {
+        if (s > p.smax) break;
+        const int dx = round_probe<T>(T(s) * n[0]);
+        const int dy = round_probe<T>(T(s) * n[1]);
+        const int dz = D == 3 ? round_probe<T>(T(s) * n[2]) : 0;
         const int py = y + dy, pz = z + dz;
         if (p.wall_y && (py < 0 || py >= p.ny)) break;
         if (D == 3 && p.wall_z && (pz < 0 || pz >= p.nz)) break;
-        T gp[3];
-        grad_at<LAT, T>(sp, RX, RY, lx + dx, ly + dy, lz + dz, py, pz, p, gp);
-        const T gpn = norm3<T>(gp);
-        if (!(gpn > T(p.g_th))) continue;
-        T dot = (-gp[0] / gpn) * n[0] + (-gp[1] / gpn) * n[1];
-        if (D == 3) dot += (-gp[2] / gpn) * n[2];
+        T gp[3], np_[3];
+        grad_smem<LAT, T>(sp, RX, RXY, c0 + dx + RX * dy + RXY * dz, py, pz, p, gp);
+        const T gpn = M<T>::unit(gp, np_);
+        if (!(gpn > p.g_th)) continue;
+        T dot = np_[0] * n[0] + np_[1] * n[1];
+        if (D == 3) dot += np_[2] * n[2];
         if (dot < T(0)) { hit = s; break; }
       }
       if (hit) {
-        const T A = nci_strength<T>(hit, p);
+        const T A = p.Ah[hit];
         const T deltaI = T(0.5) * g;
         frep[0] = -A * n[0] * deltaI;
         frep[1] = -A * n[1] * deltaI;
         frep[2] = -A * n[2] * deltaI;
       }
     }
-    // 5. force and Guo velocity
     T F[3], u[3];
 #pragma unroll
-    for (int a = 0; a < 3; ++a) F[a] = T(p.G[a]) + frep[a];
+    for (int a = 0; a < 3; ++a) F[a] = p.G[a] + frep[a];
 #pragma unroll
-    for (int a = 0; a < 3; ++a) u[a] = (j[a] + T(0.5) * F[a]) / rho;
+    for (int a = 0; a < 3; ++a) u[a] = M<T>::div(j[a] + T(0.5) * F[a], rho);
 
     if (FIELDS) {
       if (fo.rho1) fo.rho1[idx] = (double)rho1;
       if (fo.rho2) fo.rho2[idx] = (double)rho2;
-      if (fo.psi) fo.psi[idx] = (double)((rho1 - rho2) / rho);
+      if (fo.psi) fo.psi[idx] = (double)psi_own;
       for (int a = 0; a < 3; ++a) {
         if (fo.grad) fo.grad[a * N + idx] = (double)grad[a];
         if (fo.frep) fo.frep[a * N + idx] = (double)frep[a];
@@ -253,32 +348,8 @@ collide_kernel(const T* __restrict__ f, T* __restrict__ fout, const T* __restric
                        !(isfinite((double)u[0]) && isfinite((double)u[1]) && isfinite((double)u[2]));
       red[9] = bad ? 1.0 : 0.0;
     } else {
-      // 6. BGK + Guo source + perturbation on the total population; 7. recolouring.
-      T m[3] = {T(0), T(0), T(0)};
-      if (g > T(0)) { m[0] = grad[0] / g; m[1] = grad[1] / g; m[2] = grad[2] / g; }
-      const T omega = T(1) / T(p.tau);
-      const T guo = T(1) - T(0.5) * omega;
-      const T uF = u[0] * F[0] + u[1] * F[1] + u[2] * F[2];
-      const T uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
-      const T seg = T(p.beta) * rho1 * rho2 / rho;
-      const T pamp = T(2) * (T(0.5) * T(p.A_s)) * g;
-      const T c1 = rho1 / rho, c2 = rho2 / rho;
-#pragma unroll
-      for (int i = 0; i < Q; ++i) {
-        const T w = T(Lattice<LAT>::w(i));
-        const T fi = fin[0][i] + fin[1][i];
-        const T cu = T(cc(i, 0)) * u[0] + T(cc(i, 1)) * u[1] + T(cc(i, 2)) * u[2];
-        const T cF = T(cc(i, 0)) * F[0] + T(cc(i, 1)) * F[1] + T(cc(i, 2)) * F[2];
-        const T cm = T(cc(i, 0)) * m[0] + T(cc(i, 1)) * m[1] + T(cc(i, 2)) * m[2];
-        const T S = guo * w * (T(3) * (cF - uF) + T(9) * cu * cF);
-        const T feq = w * rho * (T(1) + T(3) * cu + T(4.5) * cu * cu - T(1.5) * uu);
-        T fs = fi - omega * (fi - feq) + S;
-        fs += pamp * (w * cm * cm - w / T(3));
-        const T inv_len = speed2(i) == 0 ? T(0) : T(1) / tsqrt<T>(T(speed2(i)));
-        const T rc = seg * w * (cm * inv_len);
-        fout[(size_t)i * N + idx] = c1 * fs + rc;
-        fout[(size_t)(Q + i) * N + idx] = c2 * fs - rc;
-      }
+      const T m[3] = {-n[0], -n[1], -n[2]};
+      collide_store<LAT, T>(fin, rho1, rho2, u, F, g, m, p, fout, idx);
     }
   }
 
@@ -308,30 +379,27 @@ collide_kernel(const T* __restrict__ f, T* __restrict__ fout, const T* __restric
   }
 }
 
-// Sum the per-block partials in a fixed order (deterministic) into out[kRedSlots].
-__global__ void __launch_bounds__(256) reduce_partials_kernel(const double* __restrict__ partials,
-                                                              long long nblocks, double* __restrict__ out);
-
+// ---------------------------------------------------------------------------- setup
 template <int LAT, typename T>
 __global__ void __launch_bounds__(256) init_kernel(T* __restrict__ f, const double* __restrict__ rho1,
                                                    const double* __restrict__ rho2,
-                                                   const double* __restrict__ u, long long N) {
+                                                   const double* __restrict__ u, int N) {
   constexpr int Q = Lattice<LAT>::Q;
-  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= N) return;
   const size_t n = (size_t)N;
   T us[3] = {T(0), T(0), T(0)};
   if (u) { us[0] = T(u[idx]); us[1] = T(u[n + idx]); us[2] = T(u[2 * n + idx]); }
   const T uu = us[0] * us[0] + us[1] * us[1] + us[2] * us[2];
   const T r[2] = {T(rho1[idx]), T(rho2[idx])};
-#pragma unroll
-  for (int i = 0; i < Q; ++i) {
+  static_for<Q>([&](auto I) {
+    constexpr int i = decltype(I)::value;
+    constexpr T w = T(Lattice<LAT>::w(i));
     const T cu = T(cc(i, 0)) * us[0] + T(cc(i, 1)) * us[1] + T(cc(i, 2)) * us[2];
-    const T w = T(Lattice<LAT>::w(i));
 #pragma unroll
     for (int k = 0; k < 2; ++k)
       f[(size_t)(k * Q + i) * n + idx] = w * r[k] * (T(1) + T(3) * cu + T(4.5) * cu * cu - T(1.5) * uu);
-  }
+  });
 }
 
 template <typename S, typename D>

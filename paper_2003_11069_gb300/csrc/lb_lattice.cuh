@@ -10,7 +10,22 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <type_traits>
+#include <utility>
+
 namespace lbnci {
+
+// Compile-time loop: f(std::integral_constant<int, I>) for I = 0..N-1, so that every
+// per-direction constant below is a constant expression (folded by the compiler,
+// never evaluated at run time in FP64).
+template <typename F, int... Is>
+__host__ __device__ __forceinline__ void static_for_impl(F&& f, std::integer_sequence<int, Is...>) {
+  (f(std::integral_constant<int, Is>{}), ...);
+}
+template <int N, typename F>
+__host__ __device__ __forceinline__ void static_for(F&& f) {
+  static_for_impl(f, std::make_integer_sequence<int, N>{});
+}
 
 __host__ __device__ constexpr int digit_c(int d) { return d == 0 ? 0 : (d == 1 ? 1 : -1); }
 __host__ __device__ constexpr int pow3(int a) { return a == 0 ? 1 : 3 * pow3(a - 1); }
@@ -42,15 +57,26 @@ template <> struct Lattice<1> {  // D3Q27
   }
 };
 
-// Parameters of one step, passed by value to every kernel.
-struct StepParams {
+// Parameters of one step in the arithmetic type T of the kernels (converted once on
+// the host, so an FP32 kernel never touches FP64).
+template <typename T>
+struct StepT {
   int nx, ny, nz;
   int wall_y, wall_z;
-  long long N;        // nx*ny*nz
-  double tau, A_s, beta, A_h, h_min, h_max, g_th;
-  double G[3];
-  int smax;           // probe steps of the NCI ray search (0 = NCI off)
+  int N;        // nx*ny*nz (< 2^31)
+  int smax;     // probe steps of the NCI ray search (0 = NCI off)
+  T omega;      // 1/tau
+  T guo;        // 1 - omega/2 (Guo source prefactor)
+  T pamp;       // 2 * (A_s/2): perturbation amplitude summed over both components
+  T beta;       // recolouring segregation
+  T g_th;       // interface threshold on |grad psi|
+  T G[3];       // body force
+  T Ah[8];      // A_h(h) for integer probe distance h (0 unused): A for h <= h_min,
+                // A (h_min/h)^3 for h_min < h <= h_max, 0 beyond
 };
+
+// Largest number of NCI probe steps the kernels support (h_max < kMaxProbe + 1).
+constexpr int kMaxProbe = 4;
 
 // Optional per-site outputs of the fields kernel (device pointers, FP64).
 struct FieldOut {
@@ -66,9 +92,12 @@ struct FieldOut {
 
 constexpr int kRedSlots = 10;  // mass1, mass2, P_x, P_y, P_z, flux, flux_disp, n_if, n_nci, n_bad
 
-// Thread-block tile of the tiled kernels.
+// Thread-block tile of the tiled (fields and 3D step) kernels.
 template <int LAT> struct Tile;
 template <> struct Tile<0> { static constexpr int X = 32, Y = 8, Z = 1; };
 template <> struct Tile<1> { static constexpr int X = 32, Y = 4, Z = 2; };
+
+// Fused D2Q9 step kernel: 32 x (8*SPT) sites per 256-thread block.
+constexpr int kFusedTX = 32, kFusedThreadsY = 8;
 
 }  // namespace lbnci

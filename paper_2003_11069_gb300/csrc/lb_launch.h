@@ -8,15 +8,22 @@
 
 namespace lbnci {
 
+// Everything a launcher needs, in FP64; each instantiation converts it to its own
+// arithmetic type once per call.
+struct HostParams {
+  int nx, ny, nz, wall_y, wall_z, N, smax;
+  int spt;  // sites per thread of the fused D2Q9 kernel (2 or 4)
+  double tau, A_s, beta, A_h, h_min, h_max, g_th, G[3];
+};
+
 struct Launchers {
   size_t elem;  // bytes per stored population
   cudaError_t (*init)(void* f, const double* rho1, const double* rho2, const double* u,
-                      long long N, cudaStream_t s);
-  cudaError_t (*moments)(const void* f, void* psi, const StepParams& p, cudaStream_t s);
-  cudaError_t (*collide)(const void* f, void* fout, const void* psi, const StepParams& p,
-                         cudaStream_t s);
-  cudaError_t (*fields)(const void* f, const void* psi, const StepParams& p, const FieldOut& fo,
-                        cudaStream_t s);
+                      const HostParams& p, cudaStream_t s);
+  // One full step fa -> fb (psi: scratch of N elements). Returns kernels launched via *nk.
+  cudaError_t (*step)(const void* fa, void* fb, void* psi, const HostParams& p, cudaStream_t s, int* nk);
+  cudaError_t (*fields)(const void* f, void* psi, const HostParams& p, const FieldOut& fo,
+                        cudaStream_t s, int* nk);
   cudaError_t (*to_f64)(const void* src, double* dst, long long n, cudaStream_t s);
   cudaError_t (*from_f64)(const double* src, void* dst, long long n, cudaStream_t s);
 };
@@ -25,7 +32,7 @@ const Launchers* launchers_fp64(int lattice);
 const Launchers* launchers_fp32(int lattice);
 
 // Number of thread blocks of the tiled kernels (= partial-sum slots of the fields kernel).
-long long tiled_blocks(int lattice, const StepParams& p);
+long long tiled_blocks(int lattice, const HostParams& p);
 cudaError_t reduce_partials(const double* partials, long long nblocks, double* out, cudaStream_t s);
 
 }  // namespace lbnci

@@ -73,8 +73,11 @@ CASES = {
 }
 
 
+@pytest.mark.parametrize("spt", ["4", "2"])
 @pytest.mark.parametrize("name", list(CASES))
-def test_fp64_d2q9_parity(name):
+def test_fp64_d2q9_parity(name, spt, monkeypatch):
+    """Both tilings of the fused D2Q9 kernel (32x32 and 32x16 sites per block)."""
+    monkeypatch.setenv("LBNCI_FUSED_SPT", spt)
     case = CASES[name]
     p = oracle.make_params(lattice=oracle.D2Q9, **case["p"])
     fl = case["gen"]()
@@ -191,22 +194,32 @@ def test_set_get_populations_roundtrip_and_workspace():
 
 
 # ----------------------------------------------------------------------------- FP32
-def _near_tie_sites(p, f):
-    """Sites whose NCI decision or probe rounding is within 1e-4 of a tie (from the oracle)."""
+FP32_TOL = 2e-6  # per-step error bound on the population scale (see the design notes)
+
+
+def _near_tie_sites(p, f, margin=1e-5):
+    """Sites whose NCI decision is within `margin` of a floating-point tie, judged on the
+    oracle's FP64 fields: |grad psi| near g_th at the site or a probe, a probe offset
+    s*n near a half-integer, or a facing test n(y).n(x) near 0."""
     of = oracle.fields(p, f)
+    N = oracle.N_of(p)
     g = np.sqrt((of["grad"] ** 2).sum(axis=0))
-    near = np.abs(g - p.g_th) < 1e-4
-    n = np.where(g > 0, -of["grad"] / np.where(g > 0, g, 1), 0)
+    near = np.abs(g - p.g_th) < margin
+    # a site next to a near-threshold cell can see its probe decision flip
+    n = np.where(g > 0, -of["grad"] / np.where(g > 0, g, 1), 0.0)
+    iface = g > p.g_th
     for s in range(1, int(np.floor(p.h_max)) + 1):
-        frac = np.abs(np.abs(s * n) - np.floor(np.abs(s * n)) - 0.5)
-        near |= (frac < 1e-4).any(axis=0) & (g > p.g_th)
+        v = np.abs(s * n)
+        near |= iface & (np.abs(v - np.floor(v) - 0.5) < margin).any(axis=0)
     return near, of
 
 
 @pytest.mark.parametrize("lat", [oracle.D2Q9, oracle.D3Q27])
 def test_fp32_one_step_tolerance(lat):
-    """FP32 storage and arithmetic: one step from the same (FP32-representable) state is
-    within 2e-6 of the FP64 oracle on the population scale, away from NCI ties."""
+    """FP32 storage and arithmetic: one step from the same (FP32-representable) state.
+    NCI decisions (hit distances) agree with the FP64 oracle's except at near-tie sites;
+    where they agree, every population is within FP32_TOL of the oracle on the
+    population scale max(|f|, w_i)."""
     if lat == oracle.D2Q9:
         p = oracle.make_params(lattice=lat, nx=160, ny=64, wall_y=1, tau=1.0, A_s=0.01, beta=0.7, A_h=0.05,
                                force=(1e-5, 0, 0))
@@ -225,10 +238,24 @@ def test_fp32_one_step_tolerance(lat):
     ref = oracle.step(p, f0, 1)
     near, of = _near_tie_sites(p, f0)
     Q, N = oracle.Q_of(p), oracle.N_of(p)
+    differ = fields["hit"] != of["hit"]
+    assert not (differ & ~near).any(), f"{int((differ & ~near).sum())} NCI decisions differ away from ties"
+    assert differ.sum() <= max(3, near.sum())
     rel = (np.abs(got - ref) / _scale(p, ref)).reshape(2 * Q, N)
-    # a differing NCI decision changes the sites within one step of it; exclude those
-    # neighbourhoods only if a tie exists (none expected for these inputs)
-    assert near.sum() <= 2, f"{near.sum()} near-tie sites"
-    ok = ~near
-    assert rel[:, ok].max() <= 2e-6, rel[:, ok].max()
-    assert np.array_equal(fields["hit"][ok], of["hit"][ok])
+    ok = ~differ
+    assert (of["hit"][ok] > 0).sum() > 0
+    assert rel[:, ok].max() <= FP32_TOL, rel[:, ok].max()
+
+
+def test_fp32_mass_conservation():
+    """FP32: each component's mass drifts by no more than rounding over 2000 steps."""
+    fl = inputs.channel_emulsion_2d(256, 64, seed=2, r_lo=10, r_hi=13)
+    cfg = lbnci.lb_config_make(nx=256, ny=64, wall_y=1, tau=1.0, A_s=0.01, beta=0.7, A_h=0.05,
+                               force=(1e-5, 0, 0), precision=lbnci.LB_FP32)
+    with lbnci.Sim(cfg) as sim:
+        sim.init_fields(fl.rho1, fl.rho2)
+        m0 = sim.observables()["mass"]
+        sim.step(2000)
+        o = sim.observables()
+    assert np.all(np.abs(o["mass"] - m0) / m0 < 2e-5), (o["mass"], m0)
+    assert o["n_nci"] > 0 and o["n_bad"] == 0
