@@ -145,6 +145,25 @@ const char* lb_last_error(const lb_sim* sim);
 /* Step kernels launched by this sim since lb_create (for launch accounting). */
 long long lb_kernel_launches(const lb_sim* sim);
 
+/* Observables with no allocation at all. The paper has no counterpart: this is a
+ * convenience for callers that cannot let a library allocate device memory (work
+ * recorded into a CUDA graph, where cudaMalloc is not allowed during capture; an
+ * application whose device memory is fully reserved by its own pool; a loop that
+ * must not risk the device synchronisation a cudaMalloc can cause).
+ * Computes exactly what lb_observables reports (step is set to 0) for the caller's
+ * populations f: a device array [2][Q][N] in the storage type of cfg->precision
+ * (double for LB_FP64, float for LB_FP32), laid out as lb_get_populations describes.
+ * cfg->workspace is ignored; work runs on cfg->stream and the call synchronises it.
+ * Scratch comes from a fixed 8 MiB static device array inside the library (held by
+ * every GPU that loads it until the process exits), so lattices are limited to about
+ * 2 million sites in FP32 and 1 million in FP64; larger ones return LB_EINVAL with
+ * the sizes in lb_last_error(NULL). The first call on a device looks up the array's
+ * device address (and may load the library's device code): make that first call
+ * before any stream capture. All calls share the array: calls that overlap on the
+ * GPU (other streams, other host threads on the same device) race and must not be
+ * issued. Returns LB_ENUMERIC (with out filled) if n_bad > 0. */
+lb_status lb_observables_noalloc(const lb_config* cfg, const void* f, lb_obs* out);
+
 #ifdef __cplusplus
 }
 #endif

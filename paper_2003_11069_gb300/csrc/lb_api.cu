@@ -9,6 +9,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <mutex>
 #include <new>
 
 #include "../../include/lbnci.h"
@@ -425,3 +426,102 @@ const char* lb_last_error(const lb_sim* s) { return s ? s->err : g_err; }
 long long lb_kernel_launches(const lb_sim* s) { return s ? s->launches : 0; }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------------
+// Observables without any allocation (lb_observables_noalloc).
+//
+// Some callers cannot let a library allocate device memory: code that records work
+// into a CUDA graph (cudaMalloc is not allowed while a stream is being captured),
+// applications whose device memory is fully reserved by their own pool allocator (a
+// raw cudaMalloc would fail or fragment it), and latency-critical loops in which a
+// cudaMalloc, which may synchronise the device, is not acceptable. For them this
+// entry point computes the same reductions as lb_observables from a population array
+// they already own, using only the fixed scratch array below.
+//
+// The scratch lives in this translation unit for the whole life of the process: every
+// GPU that loads the library holds kNoAllocScratchBytes of it. All calls share it and
+// it keeps the previous call's contents; every call overwrites all it reads (psi, the
+// block partials and the result), so nothing needs clearing, but two calls that
+// overlap on the GPU (different streams, or different host threads on one device)
+// race on it and must not be issued.
+namespace {
+
+constexpr size_t kNoAllocScratchBytes = size_t(8) << 20;  // 8 MiB per device
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mu;
+void* g_noalloc_ptr[kMaxDevices] = {};
+
+// Device address of the scratch array on the current device. In host code the
+// array's name is only a host-side stand-in, so its device address is looked up once
+// per device (with that device current) and cached.
+lb_status noalloc_scratch(void** out) {
+  int dev = -1;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return fail(nullptr, LB_ECUDA, "no CUDA device: %s", cudaGetErrorString(e));
+  if (dev < 0 || dev >= kMaxDevices) return fail(nullptr, LB_EUNSUPPORTED, "device ordinal %d out of range", dev);
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (!g_noalloc_ptr[dev]) {
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || !p)
+      return fail(nullptr, LB_ECUDA, "cudaGetSymbolAddress of the scratch array failed: %s", cudaGetErrorString(e));
+    g_noalloc_ptr[dev] = p;
+  }
+  *out = g_noalloc_ptr[dev];
+  return LB_OK;
+}
+
+}  // namespace
+
+extern "C" lb_status lb_observables_noalloc(const lb_config* cfg, const void* f, lb_obs* out) {
+  if (!out) return fail(nullptr, LB_EINVAL, "out is NULL");
+  if (!f) return fail(nullptr, LB_EINVAL, "f is NULL");
+  HostParams p;
+  Layout lay;
+  long long nblocks;
+  lb_status st = validate(cfg, &p, &lay, &nblocks);
+  if (st != LB_OK) return st;
+  const size_t elem = cfg->precision == LB_FP64 ? sizeof(double) : sizeof(float);
+  const size_t psi_off = 0;
+  const size_t part_off = align256(psi_off + (size_t)p.N * elem);
+  const size_t res_off = align256(part_off + (size_t)nblocks * kRedSlots * sizeof(double));
+  const size_t need = res_off + 16 * sizeof(double);
+  if (need > kNoAllocScratchBytes)
+    return fail(nullptr, LB_EINVAL,
+                "lb_observables_noalloc: a %d-site lattice needs %zu bytes of scratch, more than the "
+                "%zu-byte static array (about %zu sites at this precision)",
+                p.N, need, kNoAllocScratchBytes, kNoAllocScratchBytes / (elem + 1) - 1024);
+  void* scratch = nullptr;
+  st = noalloc_scratch(&scratch);
+  if (st != LB_OK) return st;
+  unsigned char* base = (unsigned char*)scratch;
+  cudaStream_t stream = (cudaStream_t)cfg->stream;
+  const Launchers* L = cfg->precision == LB_FP64 ? launchers_fp64(cfg->lattice) : launchers_fp32(cfg->lattice);
+  FieldOut fo{};
+  fo.partials = (double*)(base + part_off);
+  int nk = 0;
+  cudaError_t e = L->fields(f, base + psi_off, p, fo, stream, &nk);
+  if (e != cudaSuccess) return fail(nullptr, LB_ECUDA, "fields launch: %s", cudaGetErrorString(e));
+  double* result = (double*)(base + res_off);
+  e = reduce_partials(fo.partials, nblocks, result, stream);
+  if (e != cudaSuccess) return fail(nullptr, LB_ECUDA, "reduce launch: %s", cudaGetErrorString(e));
+  double r[kRedSlots];
+  e = cudaMemcpyAsync(r, result, sizeof(r), cudaMemcpyDeviceToHost, stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+  if (e != cudaSuccess) return fail(nullptr, LB_ECUDA, "result copy: %s", cudaGetErrorString(e));
+  out->mass[0] = r[0];
+  out->mass[1] = r[1];
+  out->momentum[0] = r[2];
+  out->momentum[1] = r[3];
+  out->momentum[2] = r[4];
+  out->flow_rate = r[5] / (double)p.nx;
+  out->flow_rate_disp = r[6] / (double)p.nx;
+  out->step = 0;
+  out->n_interface = (long long)r[7];
+  out->n_nci = (long long)r[8];
+  out->n_bad = (long long)r[9];
+  return out->n_bad > 0 ? fail(nullptr, LB_ENUMERIC, "non-finite or non-positive density at %lld sites", out->n_bad)
+                        : LB_OK;
+}

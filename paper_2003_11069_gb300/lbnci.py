@@ -23,7 +23,7 @@ STATUS = {0: "LB_OK", 1: "LB_EINVAL", 2: "LB_ENOMEM", 3: "LB_ECUDA", 4: "LB_ENUM
 # Every symbol include/lbnci.h declares.
 EXPORTS = ("lb_workspace_size", "lb_create", "lb_init_fields", "lb_step", "lb_observables",
            "lb_fields", "lb_get_populations", "lb_set_populations", "lb_destroy",
-           "lb_last_error", "lb_kernel_launches")
+           "lb_last_error", "lb_kernel_launches", "lb_observables_noalloc")
 
 
 class lb_config(ctypes.Structure):
@@ -96,6 +96,7 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
     lib.lb_last_error.restype = ctypes.c_char_p
     lib.lb_kernel_launches.argtypes = [simp]
     lib.lb_kernel_launches.restype = ctypes.c_longlong
+    lib.lb_observables_noalloc.argtypes = [cfgp, vp, ctypes.POINTER(lb_obs)]
     for name in EXPORTS:
         fn = getattr(lib, name)
         if fn.restype is ctypes.c_int or name not in ("lb_destroy", "lb_last_error", "lb_kernel_launches"):
@@ -224,6 +225,18 @@ def lb_last_error(sim=None) -> str:
 
 def lb_kernel_launches(sim) -> int:
     return int(load().lb_kernel_launches(sim))
+
+
+def lb_observables_noalloc(cfg: lb_config, f, allow_numeric=False) -> dict:
+    """Observables of device populations f (a CUDA tensor of the storage dtype) with no
+    allocation inside the library; see include/lbnci.h for its limits."""
+    if not _is_torch(f) or not f.is_cuda or not f.is_contiguous():
+        raise ValueError("f must be a contiguous CUDA tensor")
+    o = lb_obs()
+    st = load().lb_observables_noalloc(ctypes.byref(cfg), ctypes.c_void_p(f.data_ptr()), ctypes.byref(o))
+    if not (allow_numeric and st == LB_ENUMERIC):
+        _check(st, None)
+    return o.as_dict()
 
 
 class Sim:
