@@ -177,6 +177,22 @@ def cpu_oracle_run(w: dict, budget_s: float, nthreads: int, crop=None):
             "sample": f"{nx}x{ny}x{nz} crop of the same generator, {steps} steps, FP64 oracle"}
 
 
+def max_over_ranks(value: float, dist=None, device=None) -> float:
+    """Largest value over all ranks (the slowest rank sets the whole job's time)."""
+    if dist is None:
+        return float(value)
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_mlups(sites_per_rank: int, steps: int, world_size: int, seconds: float) -> float:
+    """Million site updates per second of all ranks together (weak scaling: every rank
+    advances its own replica of the workload)."""
+    return sites_per_rank * steps * world_size / seconds / 1e6
+
+
 def dist_env():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -297,16 +313,13 @@ def main(argv=None):
             torch.cuda.synchronize()
         launches = sim.launches() - launches0
         step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
-        total_ms = float(sum(step_ms))
+        total_ms = max_over_ranks(float(sum(step_ms)), dist, "cuda")
         if dist:
-            t = torch.tensor([total_ms], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            total_ms = float(t.item())
             dist.barrier()
         obs = sim.observables(allow_numeric=True)
     clocks = clk.summary()
     ms_per_step = total_ms / args.steps
-    value = N * args.steps * ws / (total_ms * 1e-3) / 1e6
+    value = whole_job_mlups(N, args.steps, ws, total_ms * 1e-3)
 
     # end to end through the public API with host buffers
     e2e = None
@@ -323,12 +336,8 @@ def main(argv=None):
         sim.step(args.steps)
         o2 = sim.observables(psi_h.numpy(), u_h.numpy(), allow_numeric=True)
         torch.cuda.synchronize()
-        el = time.perf_counter() - t0
-        if dist:
-            t = torch.tensor([el], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            el = float(t.item())
-        e2e = {"value": round(N * args.steps * ws / el / 1e6, 3), "unit": "MLUPS",
+        el = max_over_ranks(time.perf_counter() - t0, dist, "cuda")
+        e2e = {"value": round(whole_job_mlups(N, args.steps, ws, el), 3), "unit": "MLUPS",
                "h2d_bytes_per_step": round(2 * 8 * N / args.steps, 1),
                "d2h_bytes_per_step": round((4 * 8 * N + 80) / args.steps, 1),
                "note": "lb_init_fields from pinned host rho1/rho2, lb_step(K), lb_observables with psi "

@@ -28,7 +28,7 @@ size_t fused2d_smem_bytes(int smax, int spt) {
 }
 
 template <typename T, int SPT>
-__global__ void __launch_bounds__(256, SPT <= 2 ? 2 : 1)
+__global__ void __launch_bounds__(256, SPT <= 2 ? (sizeof(T) == 4 ? 3 : 2) : 1)
 fused2d_kernel(const T* __restrict__ f, T* __restrict__ fout, StepT<T> p) {
   constexpr int Q = 9, TX = kFusedTX, TYT = kFusedThreadsY, TY = TYT * SPT;
   constexpr int NT = TX * TYT;
@@ -51,17 +51,14 @@ fused2d_kernel(const T* __restrict__ f, T* __restrict__ fout, StepT<T> p) {
     act[s] = x < p.nx && y < p.ny;
     const int c = (tx + R) + RX * (ty + s * TYT + R);
     if (act[s]) {
-      pull_site<0, T>(f, x, y, 0, p, fin[s]);
+      pull_any<0, T>(f, x, y, 0, p, fin[s]);
       s_psi[c] = psi_of<Q, T>(fin[s]);
     } else {
       const int gx = wrapn(x, p.nx);
-      int gy = y;
-      if (!p.wall_y) gy = wrapn(gy, p.ny);
-      if (gy < p.ny) {
-        T h[2][Q];
-        pull_site<0, T>(f, gx, gy, 0, p, h);
-        s_psi[c] = psi_of<Q, T>(h);
-      }
+      const int gy = p.wall_y ? clampc(y, p.ny) : wrapn(y, p.ny);
+      T h[2][Q];
+      pull_site<0, T>(f, gx, gy, 0, p, h);
+      s_psi[c] = psi_of<Q, T>(h);
     }
   }
   // the halo ring of width R, enumerated compactly: two bands of R full rows, then
@@ -84,11 +81,13 @@ fused2d_kernel(const T* __restrict__ f, T* __restrict__ fout, StepT<T> p) {
         lx = col < R ? col : col + TX;
         ly = R + row;
       }
-      const int gx = wrapn(x0 - R + lx, p.nx);
+      // beyond a wall only the first row is read (as the mirror of the wall row)
       int gy = y0 - R + ly;
-      if (p.wall_y) { if (gy < 0 || gy >= p.ny) continue; } else gy = wrapn(gy, p.ny);
+      if (p.wall_y && (gy < -1 || gy > p.ny)) continue;
+      const int gx = wrapn(x0 - R + lx, p.nx);
+      gy = p.wall_y ? clampc(gy, p.ny) : wrapn(gy, p.ny);
       T hf[2][Q];
-      pull_site<0, T>(f, gx, gy, 0, p, hf);
+      pull_any<0, T>(f, gx, gy, 0, p, hf);
       s_psi[lx + RX * ly] = psi_of<Q, T>(hf);
     }
   }
@@ -99,7 +98,7 @@ fused2d_kernel(const T* __restrict__ f, T* __restrict__ fout, StepT<T> p) {
     int gy = y0 - S + ly;
     if (p.wall_y) { if (gy < 0 || gy >= p.ny) return; } else gy = wrapn(gy, p.ny);
     T grad[3], n[3];
-    grad_smem<0, T>(s_psi, RX, 0, (lx + 1) + RX * (ly + 1), gy, 0, p, grad);
+    grad_smem<0, T>(s_psi, RX, 0, (lx + 1) + RX * (ly + 1), grad);
     const T g = M<T>::unit(grad, n);
     s_ng[c] = n[0];
     s_ng[GXY + c] = n[1];
@@ -123,18 +122,19 @@ fused2d_kernel(const T* __restrict__ f, T* __restrict__ fout, StepT<T> p) {
     T frep[3] = {T(0), T(0), T(0)};
     if (S > 0 && g > p.g_th) {
       int hit = 0;
-#pragma unroll
-      for (int st = 1; st <= kMaxProbe; ++st) {
-        if (st > S) break;
-        const int dx = round_probe<T>(T(st) * n0);
-        const int dy = round_probe<T>(T(st) * n1);
+      static_for<kMaxProbe>([&](auto I) {
+        constexpr int st = decltype(I)::value + 1;
+        if (hit != 0 || st > S) return;  // found, stopped at a wall, or past h_max
+        const int dx = round_probe<st, T>(T(st) * n0);
+        const int dy = round_probe<st, T>(T(st) * n1);
         const int py = y + dy;
-        if (p.wall_y && (py < 0 || py >= p.ny)) break;
+        if (p.wall_y && (py < 0 || py >= p.ny)) { hit = -1; return; }
         const int cp = c + dx + GX * dy;
-        if (!(s_ng[2 * GXY + cp] > p.g_th)) continue;
+        if (!(s_ng[2 * GXY + cp] > p.g_th)) return;
         const T dot = s_ng[cp] * n0 + s_ng[GXY + cp] * n1;
-        if (dot < T(0)) { hit = st; break; }
-      }
+        if (dot < T(0)) hit = st;
+      });
+      if (hit < 0) hit = 0;
       if (hit) {
         const T A = p.Ah[hit];
         const T deltaI = T(0.5) * g;

@@ -48,12 +48,16 @@ template <> struct M<float> {
   }
 };
 
-// Round half away from zero for |v| < kMaxProbe + 1/2, by comparisons only (no
-// float-to-int conversion): the probe offset round(s n_a) of the NCI ray search.
-template <typename T>
+// Round half away from zero by comparisons only (no float-to-int conversion): the
+// probe offset round(s n_a) of the NCI ray search at step s. |n_a| <= 1 bounds
+// |s n_a| by s, so only the half-integers below s need testing.
+template <int S, typename T>
 __device__ __forceinline__ int round_probe(T v) {
   const T a = v < T(0) ? -v : v;
-  const int m = (a >= T(0.5)) + (a >= T(1.5)) + (a >= T(2.5)) + (a >= T(3.5));
+  int m = a >= T(0.5);
+  if constexpr (S >= 2) m += a >= T(1.5);
+  if constexpr (S >= 3) m += a >= T(2.5);
+  if constexpr (S >= 4) m += a >= T(3.5);
   return v < T(0) ? -m : m;
 }
 
@@ -117,6 +121,37 @@ __device__ __forceinline__ void pull_site(const T* __restrict__ f, int x, int y,
   });
 }
 
+// pull_site for a site whose upstream neighbours are all interior (no wrap, no wall):
+// every population comes from a fixed offset idx - c_i.(1, nx, nx ny).
+template <int LAT, typename T>
+__device__ __forceinline__ void pull_interior(const T* __restrict__ f, int idx, const StepT<T>& p,
+                                              T out[2][Lattice<LAT>::Q]) {
+  constexpr int Q = Lattice<LAT>::Q;
+  const unsigned N = (unsigned)p.N;
+  const int sy = p.nx, sz = p.nx * p.ny;
+  static_for<Q>([&](auto I) {
+    constexpr int i = decltype(I)::value;
+    const int src = idx - cc(i, 0) - sy * cc(i, 1) - sz * cc(i, 2);
+    out[0][i] = f[(unsigned)i * N + (unsigned)src];
+    out[1][i] = f[(unsigned)(Q + i) * N + (unsigned)src];
+  });
+}
+
+// True when site (x,y,z) can use pull_interior.
+template <int LAT, typename T>
+__device__ __forceinline__ bool is_interior(int x, int y, int z, const StepT<T>& p) {
+  bool in = x > 0 && x < p.nx - 1 && y > 0 && y < p.ny - 1;
+  if (Lattice<LAT>::D == 3) in = in && z > 0 && z < p.nz - 1;
+  return in;
+}
+
+template <int LAT, typename T>
+__device__ __forceinline__ void pull_any(const T* __restrict__ f, int x, int y, int z, const StepT<T>& p,
+                                         T out[2][Lattice<LAT>::Q]) {
+  if (is_interior<LAT, T>(x, y, z, p)) pull_interior<LAT, T>(f, x + p.nx * (y + p.ny * z), p, out);
+  else pull_site<LAT, T>(f, x, y, z, p, out);
+}
+
 // psi = (rho1 - rho2)/(rho1 + rho2) of pulled populations (sums in direction order).
 template <int Q, typename T>
 __device__ __forceinline__ T psi_of(const T fin[2][Q], T* r1out = nullptr, T* r2out = nullptr) {
@@ -131,27 +166,21 @@ __device__ __forceinline__ T psi_of(const T fin[2][Q], T* r1out = nullptr, T* r2
 }
 
 // Isotropic gradient (1/c_s^2) sum_i w_i c_i psi(x + c_i) from a shared-memory psi
-// region with strides (1, RX, RX*RY); a neighbour beyond a wall is replaced by its
-// mirror image across the wall plane (the crossing velocity components are dropped).
-// (gy, gz): global coordinates of the cell, for the wall test.
+// region with strides (1, RX, RXY). Cells beyond a wall hold the psi of their mirror
+// image across the wall plane (the clamped coordinate), which is what the stencil of a
+// site next to a wall reads: neutral wetting.
 template <int LAT, typename T>
-__device__ __forceinline__ void grad_smem(const T* __restrict__ sp, int RX, int RXY, int c, int gy, int gz,
-                                          const StepT<T>& p, T g[3]) {
+__device__ __forceinline__ void grad_smem(const T* __restrict__ sp, int RX, int RXY, int c, T g[3]) {
   constexpr int Q = Lattice<LAT>::Q;
   constexpr bool D3 = Lattice<LAT>::D == 3;
   g[0] = T(0); g[1] = T(0); g[2] = T(0);
-  const bool ylo = p.wall_y && gy == 0, yhi = p.wall_y && gy == p.ny - 1;
-  const bool zlo = D3 && p.wall_z && gz == 0, zhi = D3 && p.wall_z && gz == p.nz - 1;
   static_for<Q>([&](auto I) {
     constexpr int i = decltype(I)::value;
     if constexpr (i > 0) {
       constexpr T wx = T(Lattice<LAT>::w(i) * cc(i, 0));
       constexpr T wy = T(Lattice<LAT>::w(i) * cc(i, 1));
       constexpr T wz = T(Lattice<LAT>::w(i) * cc(i, 2));
-      int dy = cc(i, 1), dz = cc(i, 2);
-      if ((dy < 0 && ylo) || (dy > 0 && yhi)) dy = 0;
-      if ((dz < 0 && zlo) || (dz > 0 && zhi)) dz = 0;
-      const T v = sp[c + cc(i, 0) + RX * dy + RXY * dz];
+      const T v = sp[c + cc(i, 0) + RX * cc(i, 1) + RXY * cc(i, 2)];
       if constexpr (cc(i, 0) != 0) g[0] += wx * v;
       if constexpr (cc(i, 1) != 0) g[1] += wy * v;
       if constexpr (D3 && cc(i, 2) != 0) g[2] += wz * v;
@@ -162,6 +191,8 @@ __device__ __forceinline__ void grad_smem(const T* __restrict__ sp, int RX, int 
   g[2] = T(3) * g[2];
 }
 
+// Clamp a coordinate into [0, n): the mirror image of the first cell beyond a wall.
+__device__ __forceinline__ int clampc(int v, int n) { return v < 0 ? 0 : (v >= n ? n - 1 : v); }
 
 // Guo velocity u = (j + F/2)/rho with j = sum_k sum_i f_i^k c_i.
 template <int LAT, typename T>
@@ -193,26 +224,71 @@ __device__ __forceinline__ void collide_store(const T fin[2][Lattice<LAT>::Q], T
   const T seg = M<T>::div(p.beta * rho1 * rho2, rho);
   const T pamp = p.pamp * g;
   const T c1 = M<T>::div(rho1, rho), c2 = M<T>::div(rho2, rho);
-  static_for<Q>([&](auto I) {
-    constexpr int i = decltype(I)::value;
-    constexpr T w = T(Lattice<LAT>::w(i));
-    constexpr T cx = T(cc(i, 0)), cy = T(cc(i, 1)), cz = T(cc(i, 2));
-    constexpr T w3 = w / T(3);
-    constexpr T inv_len = speed2(i) == 0 ? T(0)
-                        : T(1) / (speed2(i) == 1 ? T(1) : (speed2(i) == 2 ? T(1.4142135623730951)
-                                                                           : T(1.7320508075688772)));
-    const T fi = fin[0][i] + fin[1][i];
-    const T cu = cx * u[0] + cy * u[1] + cz * u[2];
-    const T cF = cx * F[0] + cy * F[1] + cz * F[2];
-    const T cm = cx * m[0] + cy * m[1] + cz * m[2];
-    const T S = p.guo * w * (T(3) * (cF - uF) + T(9) * cu * cF);
-    const T feq = w * rho * (T(1) + T(3) * cu + T(4.5) * cu * cu - T(1.5) * uu);
-    T fs = fi - p.omega * (fi - feq) + S;
-    fs += pamp * (w * cm * cm - w3);
-    const T rc = seg * w * (cm * inv_len);
-    fout[(unsigned)i * N + (unsigned)idx] = c1 * fs + rc;
-    fout[(unsigned)(Q + i) * N + (unsigned)idx] = c2 * fs - rc;
-  });
+  if constexpr (std::is_same<T, double>::value) {
+    // FP64: the expressions exactly as written above, in the oracle's order.
+    static_for<Q>([&](auto I) {
+      constexpr int i = decltype(I)::value;
+      constexpr T w = T(Lattice<LAT>::w(i));
+      constexpr T cx = T(cc(i, 0)), cy = T(cc(i, 1)), cz = T(cc(i, 2));
+      constexpr T w3 = w / T(3);
+      constexpr T inv_len = speed2(i) == 0 ? T(0)
+                          : T(1) / (speed2(i) == 1 ? T(1) : (speed2(i) == 2 ? T(1.4142135623730951)
+                                                                             : T(1.7320508075688772)));
+      const T fi = fin[0][i] + fin[1][i];
+      const T cu = cx * u[0] + cy * u[1] + cz * u[2];
+      const T cF = cx * F[0] + cy * F[1] + cz * F[2];
+      const T cm = cx * m[0] + cy * m[1] + cz * m[2];
+      const T S = p.guo * w * (T(3) * (cF - uF) + T(9) * cu * cF);
+      const T feq = w * rho * (T(1) + T(3) * cu + T(4.5) * cu * cu - T(1.5) * uu);
+      T fs = fi - p.omega * (fi - feq) + S;
+      fs += pamp * (w * cm * cm - w3);
+      const T rc = seg * w * (cm * inv_len);
+      fout[(unsigned)i * N + (unsigned)idx] = c1 * fs + rc;
+      fout[(unsigned)(Q + i) * N + (unsigned)idx] = c2 * fs - rc;
+    });
+  } else {
+    // FP32: the same operator regrouped per site,
+    //   f*_i = (1 - omega) f_i + w_i [K0 + c.u (omega rho (3 + 4.5 c.u) + 9 guo c.F) + 3 guo c.F + pamp (c.m)^2]
+    //   K0 = omega rho (1 - 1.5 u.u) - 3 guo u.F - pamp/3,
+    // so that each direction costs a short chain of multiply-adds. The rest population
+    // of each component is set to rho_k minus the others (its exact value), so per-site
+    // mass is kept to the rounding of one sum instead of drifting with the coherent
+    // rounding of K0.
+    (void)c2;
+    const T orho = p.omega * rho;
+    const T K0 = orho * (T(1) - T(1.5) * uu) - T(3) * p.guo * uF - pamp * T(1.0 / 3.0);
+    const T a3 = T(3) * orho, a45 = T(4.5) * orho, g3 = T(3) * p.guo, g9 = T(9) * p.guo;
+    const T om1 = T(1) - p.omega;
+    T s1 = T(0), s2 = T(0);
+    static_for<Q>([&](auto I) {
+      constexpr int i = decltype(I)::value;
+      if constexpr (i > 0) {
+        constexpr T w = T(Lattice<LAT>::w(i));
+        constexpr int ix = cc(i, 0), iy = cc(i, 1), iz = cc(i, 2);
+        constexpr T wl = T(Lattice<LAT>::w(i) / (speed2(i) == 1 ? 1.0 : (speed2(i) == 2 ? 1.4142135623730951
+                                                                                         : 1.7320508075688772)));
+        auto dotc = [&](const T v[3]) {
+          T r = T(0);
+          if constexpr (ix == 1) r += v[0]; else if constexpr (ix == -1) r -= v[0];
+          if constexpr (iy == 1) r += v[1]; else if constexpr (iy == -1) r -= v[1];
+          if constexpr (iz == 1) r += v[2]; else if constexpr (iz == -1) r -= v[2];
+          return r;
+        };
+        const T fi = fin[0][i] + fin[1][i];
+        const T cu = dotc(u), cF = dotc(F), cm = dotc(m);
+        const T B = K0 + cu * (a3 + a45 * cu + g9 * cF) + g3 * cF + pamp * (cm * cm);
+        const T fs = om1 * fi + w * B;
+        const T o1 = c1 * fs + seg * wl * cm;
+        const T o2 = fs - o1;
+        s1 += o1;
+        s2 += o2;
+        fout[(unsigned)i * N + (unsigned)idx] = o1;
+        fout[(unsigned)(Q + i) * N + (unsigned)idx] = o2;
+      }
+    });
+    fout[(unsigned)idx] = rho1 - s1;
+    fout[(unsigned)Q * N + (unsigned)idx] = rho2 - s2;
+  }
 }
 
 // ---------------------------------------------------------------------------- moments
@@ -225,7 +301,7 @@ __global__ void __launch_bounds__(256) moments_kernel(const T* __restrict__ f, T
   const int y = (idx / p.nx) % p.ny;
   const int z = idx / (p.nx * p.ny);
   T fin[2][Q];
-  pull_site<LAT, T>(f, x, y, z, p, fin);
+  pull_any<LAT, T>(f, x, y, z, p, fin);
   psi[idx] = psi_of<Q, T>(fin);
 }
 
@@ -262,10 +338,9 @@ tiled_kernel(const T* __restrict__ f, T* __restrict__ fout, const T* __restrict_
     const int gx = wrapn(x0 - R + lx, p.nx);
     int gy = y0 - R + ly;
     int gz = D == 3 ? z0 - RZoff + lz : 0;
-    bool out = false;
-    if (p.wall_y) out |= (gy < 0 || gy >= p.ny); else gy = wrapn(gy, p.ny);
-    if (D == 3) { if (p.wall_z) out |= (gz < 0 || gz >= p.nz); else gz = wrapn(gz, p.nz); }
-    sp[t] = out ? T(0) : psi[gx + p.nx * (gy + p.ny * gz)];
+    gy = p.wall_y ? clampc(gy, p.ny) : wrapn(gy, p.ny);
+    if (D == 3) gz = p.wall_z ? clampc(gz, p.nz) : wrapn(gz, p.nz);
+    sp[t] = psi[gx + p.nx * (gy + p.ny * gz)];
   });
   __syncthreads();
 
@@ -279,7 +354,7 @@ tiled_kernel(const T* __restrict__ f, T* __restrict__ fout, const T* __restrict_
     const int idx = x + p.nx * (y + p.ny * z);
     const unsigned N = (unsigned)p.N;
     T fin[2][Q];
-    pull_site<LAT, T>(f, x, y, z, p, fin);
+    pull_any<LAT, T>(f, x, y, z, p, fin);
     T rho1, rho2;
     const T psi_own = psi_of<Q, T>(fin, &rho1, &rho2);
     const T rho = rho1 + rho2;
@@ -287,29 +362,32 @@ tiled_kernel(const T* __restrict__ f, T* __restrict__ fout, const T* __restrict_
     momentum<LAT, T>(fin, j);
     const int c0 = (threadIdx.x + R) + RX * (threadIdx.y + R) + RXY * (threadIdx.z + RZoff);
     T grad[3], n[3];
-    grad_smem<LAT, T>(sp, RX, RXY, c0, y, z, p, grad);
+    grad_smem<LAT, T>(sp, RX, RXY, c0, grad);
     const T g = M<T>::unit(grad, n);
     T frep[3] = {T(0), T(0), T(0)};
     int hit = 0;
     const bool iface = g > p.g_th;
     if (p.smax > 0 && iface) {
-#pragma unroll
-      for (int s = 1; s <= kMaxProbe; ++s) {
-        if (s > p.smax) break;
-        const int dx = round_probe<T>(T(s) * n[0]);
-        const int dy = round_probe<T>(T(s) * n[1]);
-        const int dz = D == 3 ? round_probe<T>(T(s) * n[2]) : 0;
+      static_for<kMaxProbe>([&](auto I) {
+        constexpr int s = decltype(I)::value + 1;
+        if (hit < 0 || hit > 0 || s > p.smax) return;  // stopped, found, or past h_max
+        const int dx = round_probe<s, T>(T(s) * n[0]);
+        const int dy = round_probe<s, T>(T(s) * n[1]);
+        const int dz = D == 3 ? round_probe<s, T>(T(s) * n[2]) : 0;
         const int py = y + dy, pz = z + dz;
-        if (p.wall_y && (py < 0 || py >= p.ny)) break;
-        if (D == 3 && p.wall_z && (pz < 0 || pz >= p.nz)) break;
+        if ((p.wall_y && (py < 0 || py >= p.ny)) || (D == 3 && p.wall_z && (pz < 0 || pz >= p.nz))) {
+          hit = -1;  // the ray left the fluid through a wall: no facing interface
+          return;
+        }
         T gp[3], np_[3];
-        grad_smem<LAT, T>(sp, RX, RXY, c0 + dx + RX * dy + RXY * dz, py, pz, p, gp);
+        grad_smem<LAT, T>(sp, RX, RXY, c0 + dx + RX * dy + RXY * dz, gp);
         const T gpn = M<T>::unit(gp, np_);
-        if (!(gpn > p.g_th)) continue;
+        if (!(gpn > p.g_th)) return;
         T dot = np_[0] * n[0] + np_[1] * n[1];
         if (D == 3) dot += np_[2] * n[2];
-        if (dot < T(0)) { hit = s; break; }
-      }
+        if (dot < T(0)) hit = s;
+      });
+      if (hit < 0) hit = 0;
       if (hit) {
         const T A = p.Ah[hit];
         const T deltaI = T(0.5) * g;
