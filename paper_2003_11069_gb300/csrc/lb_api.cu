@@ -12,7 +12,7 @@
 #include <mutex>
 #include <new>
 
-#include "../../include/lbnci.h"
+#include "lbnci.h"
 #include "lb_launch.h"
 
 namespace lbnci {
