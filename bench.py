@@ -58,10 +58,13 @@ WORKLOADS = {
                       desc="D2Q9 periodic 128x128, one droplet R 30, A_h=0.05"),
 }
 
-# Population bytes moved per site update: 2 components x Q x (1 read + 1 write).
-def alg_bytes_per_site(lattice: int, elem: int) -> int:
+# Bytes of state moved per site update (1 read + 1 write): FP64/FP32 populations are
+# 2 components x Q values; FP16-dev stores Q half2 deviations plus a float2 of
+# reference densities per site.
+def alg_bytes_per_site(lattice: int, precision: str) -> int:
     Q = 9 if lattice == 0 else 27
-    return 2 * Q * elem * 2
+    per_site = {"fp64": 2 * Q * 8, "fp32": 2 * Q * 4, "fp16dev": Q * 4 + 8}[precision]
+    return 2 * per_site
 
 
 def measured_hbm_peak():
@@ -253,7 +256,7 @@ def main(argv=None):
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="channel2d", choices=sorted(WORKLOADS))
-    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64", "fp16dev"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=12.0)
@@ -279,8 +282,7 @@ def main(argv=None):
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     lbnci.load()
     stream = torch.cuda.Stream()
-    prec = lbnci.LB_FP32 if args.precision == "fp32" else lbnci.LB_FP64
-    elem = 4 if prec == lbnci.LB_FP32 else 8
+    prec = {"fp32": lbnci.LB_FP32, "fp64": lbnci.LB_FP64, "fp16dev": lbnci.LB_FP16DEV}[args.precision]
     nx, ny, nz = w["nx"], w["ny"], w["nz"]
     N = nx * ny * nz
     cfg = lbnci.lb_config_make(lattice=w["lattice"], nx=nx, ny=ny, nz=nz, wall_y=w["wall_y"], wall_z=w["wall_z"],
@@ -349,7 +351,7 @@ def main(argv=None):
         return 0
 
     peak, peak_kind = measured_hbm_peak()
-    bpsite = alg_bytes_per_site(w["lattice"], elem)
+    bpsite = alg_bytes_per_site(w["lattice"], args.precision)
     achieved = bpsite * N / (ms_per_step * 1e-3) / 1e9
     traffic = recorded_traffic(args.workload, args.precision)
     cpu = None
@@ -364,7 +366,8 @@ def main(argv=None):
         "metric": "MLUPS", "value": round(value, 2), "unit": "MLUPS", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(ms_per_step, 5), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None,
-        "dtype": "f32" if prec == lbnci.LB_FP32 else "f64", "data": "synthetic",
+        "dtype": {"fp32": "f32", "fp64": "f64", "fp16dev": "f16 storage / f32 compute"}[args.precision],
+        "data": "synthetic",
         "config": {"workload": w["desc"], "sites": N, "precision": args.precision,
                    "l2": (f"flushed ({args.flush_mb} MB write) before every timed step; each step timed alone"
                           if args.flush_mb > 0 else "not flushed"),

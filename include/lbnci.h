@@ -65,8 +65,11 @@ typedef enum {
 typedef enum { LB_D2Q9 = 0, LB_D3Q27 = 1 } lb_lattice;
 
 typedef enum {
-  LB_FP64 = 0,   /* populations stored and computed in FP64 (parity path) */
-  LB_FP32 = 1    /* populations stored and computed in FP32 */
+  LB_FP64 = 0,    /* populations stored and computed in FP64 (parity path) */
+  LB_FP32 = 1,    /* populations stored and computed in FP32 */
+  LB_FP16DEV = 2  /* populations stored as FP16 deviations f_i - w_i rho_k from the
+                     lattice-weight equilibrium at rest, with FP32 reference densities
+                     rho_k per site; arithmetic in FP32 */
 } lb_precision;
 
 typedef struct {
@@ -130,8 +133,9 @@ lb_status lb_observables(lb_sim* sim, lb_obs* out, double* psi_out, double* u_ou
 lb_status lb_fields(lb_sim* sim, double* rho1, double* rho2, double* psi, double* grad,
                     double* frep, int* hit, double* u, int on_device);
 
-/* Copy the populations out of / into the sim as FP64 [2][Q][N] (converted from / to
- * the storage precision). lb_set_populations resets the step counter. */
+/* Copy the populations out of / into the sim as FP64 [2][Q][N] (decoded from / encoded
+ * to the storage precision; LB_FP16DEV takes each site's reference densities as the
+ * sums of the given populations). lb_set_populations resets the step counter. */
 lb_status lb_get_populations(lb_sim* sim, double* f, int on_device);
 lb_status lb_set_populations(lb_sim* sim, const double* f, int on_device);
 

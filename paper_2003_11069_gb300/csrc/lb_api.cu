@@ -88,6 +88,7 @@ lb_status fail(lb_sim* s, lb_status st, const char* fmt, ...) {
 }
 
 lb_status cuda_fail(lb_sim* s, cudaError_t e, const char* what) {
+  cudaGetLastError();  // clear the error so the next launch check does not report it again
   return fail(s, LB_ECUDA, "%s: %s", what, cudaGetErrorString(e));
 }
 
@@ -97,11 +98,17 @@ struct Layout {
   size_t fa, fb, psi, partials, result, total;
 };
 
+const Launchers* launchers_for(const lb_config* c) {
+  if (c->precision == LB_FP64) return launchers_fp64(c->lattice);
+  if (c->precision == LB_FP16DEV) return launchers_fp16dev(c->lattice);
+  return launchers_fp32(c->lattice);
+}
+
 lb_status validate(const lb_config* c, HostParams* p, Layout* lay, long long* nblocks) {
   if (!c) return fail(nullptr, LB_EINVAL, "config is NULL");
   if (c->lattice != LB_D2Q9 && c->lattice != LB_D3Q27)
     return fail(nullptr, LB_EINVAL, "unknown lattice %d", c->lattice);
-  if (c->precision != LB_FP64 && c->precision != LB_FP32)
+  if (c->precision != LB_FP64 && c->precision != LB_FP32 && c->precision != LB_FP16DEV)
     return fail(nullptr, LB_EUNSUPPORTED, "precision %d is not implemented", c->precision);
   if (c->nx < 1 || c->ny < 1 || c->nz < 1)
     return fail(nullptr, LB_EINVAL, "lattice sizes must be >= 1 (got %d x %d x %d)", c->nx, c->ny, c->nz);
@@ -137,21 +144,28 @@ lb_status validate(const lb_config* c, HostParams* p, Layout* lay, long long* nb
   p->spt = 2;
   if (const char* e = std::getenv("LBNCI_FUSED_SPT")) p->spt = std::atoi(e) == 4 ? 4 : 2;
   const int Q = c->lattice == LB_D2Q9 ? 9 : 27;
-  const size_t elem = c->precision == LB_FP64 ? 8 : 4;
+  (void)Q;
+  const Launchers* L = launchers_for(c);
+  const size_t state = L->state_bytes((size_t)N);
   *nblocks = tiled_blocks(c->lattice, *p);
   size_t off = 0;
-  lay->fa = off; off = align256(off + 2 * (size_t)Q * (size_t)N * elem);
-  lay->fb = off; off = align256(off + 2 * (size_t)Q * (size_t)N * elem);
-  lay->psi = off; off = align256(off + (size_t)N * elem);
+  lay->fa = off; off = align256(off + state);
+  lay->fb = off; off = align256(off + state);
+  lay->psi = off; off = align256(off + (size_t)N * L->compute_elem);
   lay->partials = off; off = align256(off + (size_t)(*nblocks) * kRedSlots * sizeof(double));
   lay->result = off; off = align256(off + 16 * sizeof(double));
   lay->total = off;
   return LB_OK;
 }
 
-// Bytes of FP64 staging the back buffer can hold.
-size_t staging_doubles(const lb_sim* s) {
-  return 2 * (size_t)s->Q * (size_t)s->p.N * s->L->elem / sizeof(double);
+// Doubles of staging the back buffer can hold.
+size_t staging_doubles(const lb_sim* s) { return s->L->state_bytes((size_t)s->p.N) / sizeof(double); }
+
+// Sites per host transfer of a [2Q][N] FP64 array through the back buffer (one copy
+// per population row of the chunk).
+long long staging_chunk(const lb_sim* s) {
+  const long long fit = (long long)(staging_doubles(s) / (size_t)(2 * s->Q));
+  return fit >= s->p.N ? s->p.N : fit;
 }
 
 // Run the fields kernel on the current state with the given device outputs and
@@ -198,7 +212,7 @@ lb_status lb_create(const lb_config* cfg, lb_sim** out) {
   int dev = -1;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return fail(nullptr, LB_ECUDA, "no CUDA device: %s", cudaGetErrorString(e));
-  const Launchers* L = cfg->precision == LB_FP64 ? launchers_fp64(cfg->lattice) : launchers_fp32(cfg->lattice);
+  const Launchers* L = launchers_for(cfg);
   lb_sim* s = new (std::nothrow) lb_sim();
   if (!s) return fail(nullptr, LB_ENOMEM, "host allocation failed");
   s->cfg = *cfg;
@@ -360,27 +374,28 @@ lb_status lb_observables(lb_sim* s, lb_obs* out, double* psi_out, double* u_out,
 lb_status lb_get_populations(lb_sim* s, double* f, int on_device) {
   if (!s) return fail(nullptr, LB_EINVAL, "sim is NULL");
   if (!f) return fail(s, LB_EINVAL, "f is NULL");
-  const size_t n = 2 * (size_t)s->Q * (size_t)s->p.N;
+  const int N = s->p.N, Q2 = 2 * s->Q;
   cudaError_t e;
-  if (s->L->elem == sizeof(double)) {
-    e = cudaMemcpyAsync(f, s->fa, n * sizeof(double), on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s->stream);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
-    return e == cudaSuccess ? LB_OK : cuda_fail(s, e, "population copy");
-  }
   if (on_device) {
-    e = s->L->to_f64(s->fa, f, (long long)n, s->stream);
+    e = s->L->decode(s->fa, f, 0, N, N, N, s->stream);
     ++s->launches;
     if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
-    return e == cudaSuccess ? LB_OK : cuda_fail(s, e, "population convert");
+    return e == cudaSuccess ? LB_OK : cuda_fail(s, e, "population decode");
   }
-  // One (k, i) plane at a time through the back buffer.
-  const size_t plane = (size_t)s->p.N;
-  for (size_t q = 0; q < 2 * (size_t)s->Q; ++q) {
-    e = s->L->to_f64((const char*)s->fa + q * plane * s->L->elem, (double*)s->fb, (long long)plane, s->stream);
+  // Host: decode a range of sites at a time into the back buffer, then a strided copy.
+  const long long chunk = staging_chunk(s);
+  if (chunk < 1) return fail(s, LB_EUNSUPPORTED, "staging too small");
+  for (long long s0 = 0; s0 < N; s0 += chunk) {
+    const int cnt = (int)(N - s0 < chunk ? N - s0 : chunk);
+    e = s->L->decode(s->fa, (double*)s->fb, (int)s0, cnt, cnt, N, s->stream);
     ++s->launches;
-    if (e == cudaSuccess) e = cudaMemcpyAsync(f + q * plane, s->fb, plane * sizeof(double), cudaMemcpyDeviceToHost, s->stream);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
-    if (e != cudaSuccess) return cuda_fail(s, e, "population download");
+    if (e != cudaSuccess) return cuda_fail(s, e, "population download (decode launch)");
+    for (int q = 0; q < Q2 && e == cudaSuccess; ++q)
+      e = cudaMemcpyAsync(f + (size_t)q * N + s0, (const double*)s->fb + (size_t)q * cnt,
+                          (size_t)cnt * sizeof(double), cudaMemcpyDeviceToHost, s->stream);
+    if (e != cudaSuccess) return cuda_fail(s, e, "population download (copy)");
+    e = cudaStreamSynchronize(s->stream);
+    if (e != cudaSuccess) return cuda_fail(s, e, "population download (synchronize)");
   }
   return LB_OK;
 }
@@ -388,25 +403,28 @@ lb_status lb_get_populations(lb_sim* s, double* f, int on_device) {
 lb_status lb_set_populations(lb_sim* s, const double* f, int on_device) {
   if (!s) return fail(nullptr, LB_EINVAL, "sim is NULL");
   if (!f) return fail(s, LB_EINVAL, "f is NULL");
-  const size_t n = 2 * (size_t)s->Q * (size_t)s->p.N;
+  const int N = s->p.N, Q2 = 2 * s->Q;
   cudaError_t e;
-  if (s->L->elem == sizeof(double)) {
-    e = cudaMemcpyAsync(s->fa, f, n * sizeof(double), on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s->stream);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
-    if (e != cudaSuccess) return cuda_fail(s, e, "population copy");
-  } else if (on_device) {
-    e = s->L->from_f64(f, s->fa, (long long)n, s->stream);
+  if (on_device) {
+    e = s->L->encode(f, s->fa, 0, N, N, N, s->stream);
     ++s->launches;
     if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
-    if (e != cudaSuccess) return cuda_fail(s, e, "population convert");
+    if (e != cudaSuccess) return cuda_fail(s, e, "population encode");
   } else {
-    const size_t plane = (size_t)s->p.N;
-    for (size_t q = 0; q < 2 * (size_t)s->Q; ++q) {
-      e = cudaMemcpyAsync(s->fb, f + q * plane, plane * sizeof(double), cudaMemcpyHostToDevice, s->stream);
-      if (e == cudaSuccess) e = s->L->from_f64((const double*)s->fb, (char*)s->fa + q * plane * s->L->elem, (long long)plane, s->stream);
+    const long long chunk = staging_chunk(s);
+    if (chunk < 1) return fail(s, LB_EUNSUPPORTED, "staging too small");
+    for (long long s0 = 0; s0 < N; s0 += chunk) {
+      const int cnt = (int)(N - s0 < chunk ? N - s0 : chunk);
+      e = cudaSuccess;
+      for (int q = 0; q < Q2 && e == cudaSuccess; ++q)
+        e = cudaMemcpyAsync((double*)s->fb + (size_t)q * cnt, f + (size_t)q * N + s0,
+                            (size_t)cnt * sizeof(double), cudaMemcpyHostToDevice, s->stream);
+      if (e != cudaSuccess) return cuda_fail(s, e, "population upload (copy)");
+      e = s->L->encode((const double*)s->fb, s->fa, (int)s0, cnt, cnt, N, s->stream);
       ++s->launches;
-      if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
-      if (e != cudaSuccess) return cuda_fail(s, e, "population upload");
+      if (e != cudaSuccess) return cuda_fail(s, e, "population upload (encode launch)");
+      e = cudaStreamSynchronize(s->stream);
+      if (e != cudaSuccess) return cuda_fail(s, e, "population upload (synchronize)");
     }
   }
   s->step = 0;
@@ -483,6 +501,8 @@ extern "C" lb_status lb_observables_noalloc(const lb_config* cfg, const void* f,
   long long nblocks;
   lb_status st = validate(cfg, &p, &lay, &nblocks);
   if (st != LB_OK) return st;
+  if (cfg->precision == LB_FP16DEV)
+    return fail(nullptr, LB_EUNSUPPORTED, "lb_observables_noalloc takes plain FP64 or FP32 populations");
   const size_t elem = cfg->precision == LB_FP64 ? sizeof(double) : sizeof(float);
   const size_t psi_off = 0;
   const size_t part_off = align256(psi_off + (size_t)p.N * elem);
@@ -498,7 +518,7 @@ extern "C" lb_status lb_observables_noalloc(const lb_config* cfg, const void* f,
   if (st != LB_OK) return st;
   unsigned char* base = (unsigned char*)scratch;
   cudaStream_t stream = (cudaStream_t)cfg->stream;
-  const Launchers* L = cfg->precision == LB_FP64 ? launchers_fp64(cfg->lattice) : launchers_fp32(cfg->lattice);
+  const Launchers* L = launchers_for(cfg);
   FieldOut fo{};
   fo.partials = (double*)(base + part_off);
   int nk = 0;

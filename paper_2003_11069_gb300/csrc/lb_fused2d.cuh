@@ -27,9 +27,10 @@ size_t fused2d_smem_bytes(int smax, int spt) {
   return sizeof(T) * (psi + ng);
 }
 
-template <typename T, int SPT>
-__global__ void __launch_bounds__(256, SPT <= 2 ? (sizeof(T) == 4 ? 3 : 2) : 1)
-fused2d_kernel(const T* __restrict__ f, T* __restrict__ fout, StepT<T> p) {
+template <typename ST, int SPT>
+__global__ void __launch_bounds__(256, SPT <= 2 ? (sizeof(typename ST::Compute) == 4 && !ST::kHalf ? 3 : 2) : 1)
+fused2d_kernel(typename ST::Reader f, typename ST::Writer fout, StepT<typename ST::Compute> p) {
+  using T = typename ST::Compute;
   constexpr int Q = 9, TX = kFusedTX, TYT = kFusedThreadsY, TY = TYT * SPT;
   constexpr int NT = TX * TYT;
   extern __shared__ __align__(16) unsigned char smem_raw[];

@@ -1,5 +1,5 @@
-// lb_instantiate.cuh -- launch wrappers for one storage type T; included once per
-// precision translation unit.
+// lb_instantiate.cuh -- launch wrappers for one storage layout; included once per
+// storage translation unit.
 #pragma once
 
 #include "lb_fused2d.cuh"
@@ -50,81 +50,85 @@ cudaError_t allow_smem(K kernel, size_t bytes, size_t* configured) {
 }
 
 // Sites per thread of the fused D2Q9 kernel (2: 32x16 tiles, 4: 32x32 tiles).
-template <typename T, int SPT>
-cudaError_t launch_fused2d(const void* fa, void* fb, const StepT<T>& p, cudaStream_t s) {
+template <typename ST, int SPT>
+cudaError_t launch_fused2d(const void* fa, void* fb, const StepT<typename ST::Compute>& p, cudaStream_t s) {
+  using T = typename ST::Compute;
   static size_t configured = 0;
   const size_t sm = fused2d_smem_bytes<T>(p.smax, SPT);
-  cudaError_t e = allow_smem(fused2d_kernel<T, SPT>, sm, &configured);
+  cudaError_t e = allow_smem(fused2d_kernel<ST, SPT>, sm, &configured);
   if (e != cudaSuccess) return e;
   const dim3 grid((p.nx + kFusedTX - 1) / kFusedTX, (p.ny + kFusedThreadsY * SPT - 1) / (kFusedThreadsY * SPT), 1);
-  fused2d_kernel<T, SPT><<<grid, dim3(kFusedTX, kFusedThreadsY, 1), sm, s>>>((const T*)fa, (T*)fb, p);
+  fused2d_kernel<ST, SPT><<<grid, dim3(kFusedTX, kFusedThreadsY, 1), sm, s>>>(
+      ST::reader(fa, (unsigned)p.N), ST::writer(fb, (unsigned)p.N), p);
   return cudaGetLastError();
 }
 
-template <int LAT, typename T>
+template <int LAT, typename ST>
 cudaError_t l_init(void* f, const double* r1, const double* r2, const double* u, const HostParams& p,
                    cudaStream_t s) {
   if (p.N == 0) return cudaSuccess;
-  init_kernel<LAT, T><<<blocks_for(p.N, 256), 256, 0, s>>>((T*)f, r1, r2, u, p.N);
+  init_kernel<LAT, ST><<<blocks_for(p.N, 256), 256, 0, s>>>(ST::writer(f, (unsigned)p.N), r1, r2, u, p.N);
   return cudaGetLastError();
 }
 
-template <int LAT, typename T, bool FIELDS>
-cudaError_t launch_tiled(const void* f, void* fout, const void* psi, const StepT<T>& p, const FieldOut& fo,
-                         cudaStream_t s) {
+template <int LAT, typename ST, bool FIELDS>
+cudaError_t launch_tiled(const void* f, void* fout, const void* psi, const HostParams& h,
+                         const StepT<typename ST::Compute>& p, const FieldOut& fo, cudaStream_t s) {
+  using T = typename ST::Compute;
   static size_t configured = 0;
   const size_t sm = tiled_smem_bytes<LAT, T>(p.smax);
-  cudaError_t e = allow_smem(tiled_kernel<LAT, T, FIELDS>, sm, &configured);
+  cudaError_t e = allow_smem(tiled_kernel<LAT, ST, FIELDS>, sm, &configured);
   if (e != cudaSuccess) return e;
-  HostParams hp{};
-  hp.nx = p.nx; hp.ny = p.ny; hp.nz = p.nz;
-  tiled_kernel<LAT, T, FIELDS><<<tiled_grid<LAT>(hp), tiled_block<LAT>(), sm, s>>>(
-      (const T*)f, (T*)fout, (const T*)psi, p, fo);
+  typename ST::Writer w = FIELDS ? typename ST::Writer{} : ST::writer(fout, (unsigned)p.N);
+  tiled_kernel<LAT, ST, FIELDS><<<tiled_grid<LAT>(h), tiled_block<LAT>(), sm, s>>>(
+      ST::reader(f, (unsigned)p.N), w, (const T*)psi, p, fo);
   return cudaGetLastError();
 }
 
-template <int LAT, typename T>
+template <int LAT, typename ST>
 cudaError_t l_step(const void* fa, void* fb, void* psi, const HostParams& h, cudaStream_t s, int* nk) {
+  using T = typename ST::Compute;
   const StepT<T> p = convert<T>(h);
   if (LAT == 0) {
     *nk = 1;
-    return h.spt == 4 ? launch_fused2d<T, 4>(fa, fb, p, s) : launch_fused2d<T, 2>(fa, fb, p, s);
+    return h.spt == 4 ? launch_fused2d<ST, 4>(fa, fb, p, s) : launch_fused2d<ST, 2>(fa, fb, p, s);
   }
-  moments_kernel<LAT, T><<<blocks_for(p.N, 256), 256, 0, s>>>((const T*)fa, (T*)psi, p);
+  moments_kernel<LAT, ST><<<blocks_for(p.N, 256), 256, 0, s>>>(ST::reader(fa, (unsigned)p.N), (T*)psi, p);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   *nk = 2;
-  return launch_tiled<LAT, T, false>(fa, fb, psi, p, FieldOut{}, s);
+  return launch_tiled<LAT, ST, false>(fa, fb, psi, h, p, FieldOut{}, s);
 }
 
-template <int LAT, typename T>
+template <int LAT, typename ST>
 cudaError_t l_fields(const void* f, void* psi, const HostParams& h, const FieldOut& fo, cudaStream_t s, int* nk) {
+  using T = typename ST::Compute;
   const StepT<T> p = convert<T>(h);
-  moments_kernel<LAT, T><<<blocks_for(p.N, 256), 256, 0, s>>>((const T*)f, (T*)psi, p);
+  moments_kernel<LAT, ST><<<blocks_for(p.N, 256), 256, 0, s>>>(ST::reader(f, (unsigned)p.N), (T*)psi, p);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   *nk = 2;
-  return launch_tiled<LAT, T, true>(f, nullptr, psi, p, fo, s);
+  return launch_tiled<LAT, ST, true>(f, nullptr, psi, h, p, fo, s);
 }
 
-template <typename T>
-cudaError_t l_to_f64(const void* src, double* dst, long long n, cudaStream_t s) {
-  if (n == 0) return cudaSuccess;
-  convert_kernel<T, double><<<blocks_for(n, 256), 256, 0, s>>>((const T*)src, dst, n);
+template <int LAT, typename ST>
+cudaError_t l_decode(const void* f, double* out, int s0, int count, long long pitch, int N, cudaStream_t s) {
+  if (count <= 0) return cudaSuccess;
+  decode_kernel<LAT, ST><<<blocks_for(count, 256), 256, 0, s>>>(ST::reader(f, (unsigned)N), out, s0, count, pitch);
   return cudaGetLastError();
 }
 
-template <typename T>
-cudaError_t l_from_f64(const double* src, void* dst, long long n, cudaStream_t s) {
-  if (n == 0) return cudaSuccess;
-  convert_kernel<double, T><<<blocks_for(n, 256), 256, 0, s>>>(src, (T*)dst, n);
+template <int LAT, typename ST>
+cudaError_t l_encode(const double* in, void* f, int s0, int count, long long pitch, int N, cudaStream_t s) {
+  if (count <= 0) return cudaSuccess;
+  encode_kernel<LAT, ST><<<blocks_for(count, 256), 256, 0, s>>>(in, ST::writer(f, (unsigned)N), s0, count, pitch);
   return cudaGetLastError();
 }
 
-template <int LAT, typename T>
+template <int LAT, typename ST>
 const Launchers* table() {
-  static const Launchers L = {sizeof(T), l_init<LAT, T>, l_step<LAT, T>, l_fields<LAT, T>, l_to_f64<T>,
-                              l_from_f64<T>};
+  static const Launchers L = {ST::bytes, sizeof(typename ST::Compute), l_init<LAT, ST>, l_step<LAT, ST>,
+                              l_fields<LAT, ST>, l_decode<LAT, ST>, l_encode<LAT, ST>};
   return &L;
 }
 

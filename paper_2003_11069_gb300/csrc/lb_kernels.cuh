@@ -18,6 +18,7 @@
 #pragma once
 
 #include "lb_lattice.cuh"
+#include "lb_storage.cuh"
 
 namespace lbnci {
 
@@ -87,12 +88,11 @@ __device__ __forceinline__ void for_region(int tid, int NT, int RX, int RY, int 
 // Pull the 2Q populations of site (x,y,z) from the post-collision state: from the
 // upstream site x - c_i, or, when that lies beyond a wall, the opposite population
 // of the site itself (halfway bounce-back).
-template <int LAT, typename T>
-__device__ __forceinline__ void pull_site(const T* __restrict__ f, int x, int y, int z, const StepT<T>& p,
+template <int LAT, typename T, typename RD>
+__device__ __forceinline__ void pull_site(const RD& f, int x, int y, int z, const StepT<T>& p,
                                           T out[2][Lattice<LAT>::Q]) {
   constexpr int Q = Lattice<LAT>::Q;
   constexpr bool D3 = Lattice<LAT>::D == 3;
-  const unsigned N = (unsigned)p.N;  // 2*Q*N < 2^32 is checked at creation
   const int xm = x == 0 ? p.nx - 1 : x - 1, xp = x == p.nx - 1 ? 0 : x + 1;
   int ym, yp, zm = 0, zp = 0;
   bool bym = false, byp = false, bzm = false, bzp = false;
@@ -112,28 +112,22 @@ __device__ __forceinline__ void pull_site(const T* __restrict__ f, int x, int y,
     const int sy = cy == 1 ? ym : (cy == -1 ? yp : y);
     const int sz = D3 ? (cz == 1 ? zm : (cz == -1 ? zp : z)) : 0;
     const int src = sx + p.nx * (sy + p.ny * sz);
-#pragma unroll
-    for (int k = 0; k < 2; ++k) {
-      const unsigned off = bounce ? (unsigned)(k * Q + opposite(i)) * N + (unsigned)idx
-                                  : (unsigned)(k * Q + i) * N + (unsigned)src;
-      out[k][i] = f[off];
-    }
+    if (bounce) f.template get<opposite(i)>((unsigned)idx, out[0][i], out[1][i]);
+    else f.template get<i>((unsigned)src, out[0][i], out[1][i]);
   });
 }
 
 // pull_site for a site whose upstream neighbours are all interior (no wrap, no wall):
 // every population comes from a fixed offset idx - c_i.(1, nx, nx ny).
-template <int LAT, typename T>
-__device__ __forceinline__ void pull_interior(const T* __restrict__ f, int idx, const StepT<T>& p,
+template <int LAT, typename T, typename RD>
+__device__ __forceinline__ void pull_interior(const RD& f, int idx, const StepT<T>& p,
                                               T out[2][Lattice<LAT>::Q]) {
   constexpr int Q = Lattice<LAT>::Q;
-  const unsigned N = (unsigned)p.N;
   const int sy = p.nx, sz = p.nx * p.ny;
   static_for<Q>([&](auto I) {
     constexpr int i = decltype(I)::value;
     const int src = idx - cc(i, 0) - sy * cc(i, 1) - sz * cc(i, 2);
-    out[0][i] = f[(unsigned)i * N + (unsigned)src];
-    out[1][i] = f[(unsigned)(Q + i) * N + (unsigned)src];
+    f.template get<i>((unsigned)src, out[0][i], out[1][i]);
   });
 }
 
@@ -145,11 +139,11 @@ __device__ __forceinline__ bool is_interior(int x, int y, int z, const StepT<T>&
   return in;
 }
 
-template <int LAT, typename T>
-__device__ __forceinline__ void pull_any(const T* __restrict__ f, int x, int y, int z, const StepT<T>& p,
+template <int LAT, typename T, typename RD>
+__device__ __forceinline__ void pull_any(const RD& f, int x, int y, int z, const StepT<T>& p,
                                          T out[2][Lattice<LAT>::Q]) {
-  if (is_interior<LAT, T>(x, y, z, p)) pull_interior<LAT, T>(f, x + p.nx * (y + p.ny * z), p, out);
-  else pull_site<LAT, T>(f, x, y, z, p, out);
+  if (is_interior<LAT, T>(x, y, z, p)) pull_interior<LAT, T, RD>(f, x + p.nx * (y + p.ny * z), p, out);
+  else pull_site<LAT, T, RD>(f, x, y, z, p, out);
 }
 
 // psi = (rho1 - rho2)/(rho1 + rho2) of pulled populations (sums in direction order).
@@ -212,12 +206,11 @@ __device__ __forceinline__ void momentum(const T fin[2][Lattice<LAT>::Q], T j[3]
 // (A_s/2)|grad psi| [w_i (c_i.m)^2 - w_i/3] of each component, on the total
 // population; then recolouring f^1 = (rho1/rho) f* + beta rho1 rho2/rho w_i cos(theta_i),
 // f^2 = (rho2/rho) f* - same, cos(theta_i) = c_i.m/|c_i|. m = grad psi/|grad psi|.
-template <int LAT, typename T>
+template <int LAT, typename T, typename WR>
 __device__ __forceinline__ void collide_store(const T fin[2][Lattice<LAT>::Q], T rho1, T rho2, const T u[3],
                                               const T F[3], T g, const T m[3], const StepT<T>& p,
-                                              T* __restrict__ fout, int idx) {
+                                              const WR& fout, int idx) {
   constexpr int Q = Lattice<LAT>::Q;
-  const unsigned N = (unsigned)p.N;
   const T rho = rho1 + rho2;
   const T uF = u[0] * F[0] + u[1] * F[1] + u[2] * F[2];
   const T uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
@@ -243,9 +236,9 @@ __device__ __forceinline__ void collide_store(const T fin[2][Lattice<LAT>::Q], T
       T fs = fi - p.omega * (fi - feq) + S;
       fs += pamp * (w * cm * cm - w3);
       const T rc = seg * w * (cm * inv_len);
-      fout[(unsigned)i * N + (unsigned)idx] = c1 * fs + rc;
-      fout[(unsigned)(Q + i) * N + (unsigned)idx] = c2 * fs - rc;
+      fout.template put<i>((unsigned)idx, c1 * fs + rc, c2 * fs - rc, rho1, rho2);
     });
+    fout.put_rho((unsigned)idx, rho1, rho2);
   } else {
     // FP32: the same operator regrouped per site,
     //   f*_i = (1 - omega) f_i + w_i [K0 + c.u (omega rho (3 + 4.5 c.u) + 9 guo c.F) + 3 guo c.F + pamp (c.m)^2]
@@ -282,18 +275,19 @@ __device__ __forceinline__ void collide_store(const T fin[2][Lattice<LAT>::Q], T
         const T o2 = fs - o1;
         s1 += o1;
         s2 += o2;
-        fout[(unsigned)i * N + (unsigned)idx] = o1;
-        fout[(unsigned)(Q + i) * N + (unsigned)idx] = o2;
+        fout.template put<i>((unsigned)idx, o1, o2, rho1, rho2);
       }
     });
-    fout[(unsigned)idx] = rho1 - s1;
-    fout[(unsigned)Q * N + (unsigned)idx] = rho2 - s2;
+    fout.template put<0>((unsigned)idx, rho1 - s1, rho2 - s2, rho1, rho2);
+    fout.put_rho((unsigned)idx, rho1, rho2);
   }
 }
 
 // ---------------------------------------------------------------------------- moments
-template <int LAT, typename T>
-__global__ void __launch_bounds__(256) moments_kernel(const T* __restrict__ f, T* __restrict__ psi, StepT<T> p) {
+template <int LAT, typename ST>
+__global__ void __launch_bounds__(256) moments_kernel(typename ST::Reader f, typename ST::Compute* __restrict__ psi,
+                                                      StepT<typename ST::Compute> p) {
+  using T = typename ST::Compute;
   constexpr int Q = Lattice<LAT>::Q;
   const int idx = blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= p.N) return;
@@ -318,9 +312,11 @@ size_t tiled_smem_bytes(int smax) {
 
 // Gradient, NCI and collision from a psi array: the psi tile and its halo of radius
 // smax+1 are staged in shared memory; probes recompute the gradient there.
-template <int LAT, typename T, bool FIELDS>
+template <int LAT, typename ST, bool FIELDS>
 __global__ void __launch_bounds__(256)
-tiled_kernel(const T* __restrict__ f, T* __restrict__ fout, const T* __restrict__ psi, StepT<T> p, FieldOut fo) {
+tiled_kernel(typename ST::Reader f, typename ST::Writer fout, const typename ST::Compute* __restrict__ psi,
+             StepT<typename ST::Compute> p, FieldOut fo) {
+  using T = typename ST::Compute;
   constexpr int D = Lattice<LAT>::D;
   constexpr int Q = Lattice<LAT>::Q;
   constexpr int TX = Tile<LAT>::X, TY = Tile<LAT>::Y, TZ = Tile<LAT>::Z;
@@ -458,10 +454,11 @@ tiled_kernel(const T* __restrict__ f, T* __restrict__ fout, const T* __restrict_
 }
 
 // ---------------------------------------------------------------------------- setup
-template <int LAT, typename T>
-__global__ void __launch_bounds__(256) init_kernel(T* __restrict__ f, const double* __restrict__ rho1,
+template <int LAT, typename ST>
+__global__ void __launch_bounds__(256) init_kernel(typename ST::Writer f, const double* __restrict__ rho1,
                                                    const double* __restrict__ rho2,
                                                    const double* __restrict__ u, int N) {
+  using T = typename ST::Compute;
   constexpr int Q = Lattice<LAT>::Q;
   const int idx = blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= N) return;
@@ -474,16 +471,53 @@ __global__ void __launch_bounds__(256) init_kernel(T* __restrict__ f, const doub
     constexpr int i = decltype(I)::value;
     constexpr T w = T(Lattice<LAT>::w(i));
     const T cu = T(cc(i, 0)) * us[0] + T(cc(i, 1)) * us[1] + T(cc(i, 2)) * us[2];
-#pragma unroll
-    for (int k = 0; k < 2; ++k)
-      f[(size_t)(k * Q + i) * n + idx] = w * r[k] * (T(1) + T(3) * cu + T(4.5) * cu * cu - T(1.5) * uu);
+    const T e1 = w * r[0] * (T(1) + T(3) * cu + T(4.5) * cu * cu - T(1.5) * uu);
+    const T e2 = w * r[1] * (T(1) + T(3) * cu + T(4.5) * cu * cu - T(1.5) * uu);
+    f.template put<i>((unsigned)idx, e1, e2, r[0], r[1]);
+  });
+  f.put_rho((unsigned)idx, r[0], r[1]);
+}
+
+// FP64 [2][Q][pitch] copies of sites [s0, s0 + count) of a state and back: the site
+// range lets the host move a state through a bounded staging buffer.
+template <int LAT, typename ST>
+__global__ void __launch_bounds__(256) decode_kernel(typename ST::Reader f, double* __restrict__ out, int s0,
+                                                     int count, long long pitch) {
+  using T = typename ST::Compute;
+  constexpr int Q = Lattice<LAT>::Q;
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= count) return;
+  static_for<Q>([&](auto I) {
+    constexpr int i = decltype(I)::value;
+    T a, b;
+    f.template get<i>((unsigned)(s0 + j), a, b);
+    out[(long long)i * pitch + j] = (double)a;
+    out[(long long)(Q + i) * pitch + j] = (double)b;
   });
 }
 
-template <typename S, typename D>
-__global__ void __launch_bounds__(256) convert_kernel(const S* __restrict__ src, D* __restrict__ dst, long long n) {
-  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) dst[i] = D(src[i]);
+template <int LAT, typename ST>
+__global__ void __launch_bounds__(256) encode_kernel(const double* __restrict__ in, typename ST::Writer f, int s0,
+                                                     int count, long long pitch) {
+  using T = typename ST::Compute;
+  constexpr int Q = Lattice<LAT>::Q;
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= count) return;
+  T v[2][Q];
+  T r1 = T(0), r2 = T(0);
+  static_for<Q>([&](auto I) {
+    constexpr int i = decltype(I)::value;
+    v[0][i] = T(in[(long long)i * pitch + j]);
+    v[1][i] = T(in[(long long)(Q + i) * pitch + j]);
+    r1 += v[0][i];
+    r2 += v[1][i];
+  });
+  static_for<Q>([&](auto I) {
+    constexpr int i = decltype(I)::value;
+    f.template put<i>((unsigned)(s0 + j), v[0][i], v[1][i], r1, r2);
+  });
+  f.put_rho((unsigned)(s0 + j), r1, r2);
 }
+
 
 }  // namespace lbnci

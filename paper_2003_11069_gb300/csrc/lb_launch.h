@@ -1,5 +1,5 @@
 // lb_launch.h -- internal launch table between the C ABI (lb_api.cu) and the
-// per-precision kernel instantiations (lb_fp64.cu, lb_fp32.cu).
+// per-storage kernel instantiations (lb_fp64.cu, lb_fp32.cu, lb_fp16.cu).
 #pragma once
 
 #include <cuda_runtime.h>
@@ -12,24 +12,28 @@ namespace lbnci {
 // arithmetic type once per call.
 struct HostParams {
   int nx, ny, nz, wall_y, wall_z, N, smax;
-  int spt;  // sites per thread of the fused D2Q9 kernel (2 or 4)
+  int spt;      // sites per thread of the fused D2Q9 kernel (2 or 4)
+  int num_sms;  // multiprocessors of the device
   double tau, A_s, beta, A_h, h_min, h_max, g_th, G[3];
 };
 
 struct Launchers {
-  size_t elem;  // bytes per stored population
+  size_t (*state_bytes)(size_t N);  // bytes of one population state
+  size_t compute_elem;              // bytes of the arithmetic type (psi scratch elements)
   cudaError_t (*init)(void* f, const double* rho1, const double* rho2, const double* u,
                       const HostParams& p, cudaStream_t s);
-  // One full step fa -> fb (psi: scratch of N elements). Returns kernels launched via *nk.
+  // One full step fa -> fb (psi: scratch of N compute elements). Kernels launched -> *nk.
   cudaError_t (*step)(const void* fa, void* fb, void* psi, const HostParams& p, cudaStream_t s, int* nk);
   cudaError_t (*fields)(const void* f, void* psi, const HostParams& p, const FieldOut& fo,
                         cudaStream_t s, int* nk);
-  cudaError_t (*to_f64)(const void* src, double* dst, long long n, cudaStream_t s);
-  cudaError_t (*from_f64)(const double* src, void* dst, long long n, cudaStream_t s);
+  // FP64 [2][Q][pitch] copies of sites [s0, s0 + count) of a state, and back.
+  cudaError_t (*decode)(const void* f, double* out, int s0, int count, long long pitch, int N, cudaStream_t s);
+  cudaError_t (*encode)(const double* in, void* f, int s0, int count, long long pitch, int N, cudaStream_t s);
 };
 
 const Launchers* launchers_fp64(int lattice);
 const Launchers* launchers_fp32(int lattice);
+const Launchers* launchers_fp16dev(int lattice);
 
 // Number of thread blocks of the tiled kernels (= partial-sum slots of the fields kernel).
 long long tiled_blocks(int lattice, const HostParams& p);

@@ -17,7 +17,7 @@ from . import build as _build
 
 LB_OK, LB_EINVAL, LB_ENOMEM, LB_ECUDA, LB_ENUMERIC, LB_EUNSUPPORTED = range(6)
 LB_D2Q9, LB_D3Q27 = 0, 1
-LB_FP64, LB_FP32 = 0, 1
+LB_FP64, LB_FP32, LB_FP16DEV = 0, 1, 2
 STATUS = {0: "LB_OK", 1: "LB_EINVAL", 2: "LB_ENOMEM", 3: "LB_ECUDA", 4: "LB_ENUMERIC", 5: "LB_EUNSUPPORTED"}
 
 # Every symbol include/lbnci.h declares.

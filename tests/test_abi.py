@@ -49,6 +49,7 @@ def test_struct_layouts_match_header():
     (dict(A_h=-1.0), lbnci.LB_EINVAL),
     (dict(force=(float("inf"), 0, 0)), lbnci.LB_EINVAL),
     (dict(precision=9), lbnci.LB_EUNSUPPORTED),
+    (dict(precision=3), lbnci.LB_EUNSUPPORTED),
 ])
 def test_config_validation(bad, status):
     with pytest.raises(lbnci.LBError) as ei:
@@ -58,14 +59,16 @@ def test_config_validation(bad, status):
 
 
 def test_workspace_size_formula():
-    for lat, nz, prec, elem, Q in ((0, 1, lbnci.LB_FP64, 8, 9), (0, 1, lbnci.LB_FP32, 4, 9),
-                                   (1, 6, lbnci.LB_FP32, 4, 27)):
+    for lat, nz, prec, state, psi, Q in ((0, 1, lbnci.LB_FP64, 8 * 18, 8, 9), (0, 1, lbnci.LB_FP32, 4 * 18, 4, 9),
+                                         (1, 6, lbnci.LB_FP32, 4 * 54, 4, 27),
+                                         (0, 1, lbnci.LB_FP16DEV, 4 * 9 + 8, 4, 9),
+                                         (1, 6, lbnci.LB_FP16DEV, 4 * 27 + 8, 4, 27)):
         nx, ny = 70, 33
         cfg = lbnci.lb_config_make(lattice=lat, nx=nx, ny=ny, nz=nz, precision=prec, A_h=0.05)
         n = lbnci.lb_workspace_size(cfg)
         N = nx * ny * nz
-        assert n >= (4 * Q + 1) * N * elem
-        assert n <= (4 * Q + 1) * N * elem + 64 * 1024 + N * 10 * 8 // 64
+        assert n >= (2 * state + psi) * N
+        assert n <= (2 * state + psi) * N + 64 * 1024 + N * 10 * 8 // 64
 
 
 def test_null_arguments_are_rejected():

@@ -1,0 +1,146 @@
+"""Reduced-precision storage against the FP64 oracle.
+
+LB_FP16DEV stores populations as FP16 deviations delta = f - w_i rho_ref from the
+lattice-weight equilibrium at rest (FP32 reference densities per site) and computes in
+FP32. Tolerances follow from FP16's 11-bit significand: a stored deviation is rounded
+by at most 2^-11 |delta| (plus 2^-25 near zero), and |delta| <= 0.3 w_i on these
+states, so one step is within 3e-4 of the oracle on the population scale max(|f|, w_i).
+The long-run test states each observable's error (psi and u in L2, the dispersed
+flow rate, the droplet count, mass drift) for FP32 and FP16-dev storage.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2003_11069_gb300 import inputs, lbnci
+
+pytestmark = pytest.mark.gpu
+
+FP16DEV_STEP_TOL = 3e-4
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    lbnci.load()
+
+
+def _cfg(p, precision):
+    return lbnci.lb_config_make(
+        lattice=p.lattice, nx=p.nx, ny=p.ny, nz=p.nz, wall_y=p.wall_y, wall_z=p.wall_z, tau=p.tau,
+        A_s=p.A_s, beta=p.beta, A_h=p.A_h, h_min=p.h_min, h_max=p.h_max, g_th=p.g_th,
+        force=tuple(p.force), precision=precision)
+
+
+def _scale(p, f):
+    _, w, _ = oracle.lattice(p.lattice)
+    return np.maximum(np.abs(f), np.tile(np.repeat(w, oracle.N_of(p)), 2))
+
+
+def _case(lat):
+    if lat == oracle.D2Q9:
+        p = oracle.make_params(lattice=lat, nx=160, ny=64, wall_y=1, tau=1.0, A_s=0.01, beta=0.7, A_h=0.05,
+                               force=(1e-5, 0, 0))
+        fl = inputs.channel_emulsion_2d(160, 64, seed=9, r_lo=10, r_hi=13)
+    else:
+        p = oracle.make_params(lattice=lat, nx=40, ny=22, nz=17, wall_y=1, wall_z=1, tau=1.0, A_s=0.01,
+                               beta=0.7, A_h=0.03, force=(2e-6, 0, 0))
+        fl = inputs.duct_emulsion_3d(40, 22, 17, seed=4, radius=5.0, volume_fraction=0.5)
+    return p, fl
+
+
+@pytest.mark.parametrize("lat", [oracle.D2Q9, oracle.D3Q27])
+def test_fp16dev_roundtrip_quantisation(lat):
+    """set/get through FP16 deviations: each population comes back as
+    w_i rho_ref + fp16(f - w_i rho_ref), rho_ref = sum of the site's populations."""
+    p, fl = _case(lat)
+    f0 = oracle.step(p, oracle.init(p, fl.rho1, fl.rho2), 20)
+    _, w, _ = oracle.lattice(lat)
+    Q, N = len(w), oracle.N_of(p)
+    with lbnci.Sim(_cfg(p, lbnci.LB_FP16DEV)) as sim:
+        sim.set_populations(f0)
+        g = sim.get_populations()
+    f3 = f0.reshape(2, Q, N)
+    rho = f3.sum(axis=1)
+    dev = f3 - w[None, :, None] * rho[:, None, :]
+    bound = 2.0 ** -11 * np.abs(dev) + 2.0 ** -24 + 1e-6 * np.abs(f3)
+    assert np.all(np.abs(g.reshape(2, Q, N) - f3) <= bound)
+    # the deviations really are small compared with the populations
+    assert np.max(np.abs(dev) / w[None, :, None]) < 0.4
+
+
+@pytest.mark.parametrize("lat", [oracle.D2Q9, oracle.D3Q27])
+def test_fp16dev_one_step_tolerance(lat):
+    p, fl = _case(lat)
+    f0 = oracle.step(p, oracle.init(p, fl.rho1, fl.rho2), 20)
+    with lbnci.Sim(_cfg(p, lbnci.LB_FP16DEV)) as sim:
+        sim.set_populations(f0)
+        fq = sim.get_populations()  # the representable state both sides start from
+        fields = sim.fields()
+        sim.step(1)
+        got = sim.get_populations()
+    ref = oracle.step(p, fq, 1)
+    of = oracle.fields(p, fq)
+    Q, N = oracle.Q_of(p), oracle.N_of(p)
+    ok = fields["hit"] == of["hit"]
+    assert ok.mean() > 0.99
+    rel = (np.abs(got - ref) / _scale(p, ref)).reshape(2 * Q, N)
+    assert rel[:, ok].max() <= FP16DEV_STEP_TOL, rel[:, ok].max()
+
+
+def _droplets(psi2d):
+    """Connected components of psi > 0 (4-connectivity, periodic in x)."""
+    from scipy import ndimage
+    lab, n = ndimage.label(psi2d > 0)
+    parent = list(range(n + 1))
+
+    def find(a):
+        while parent[a] != a:
+            parent[a] = parent[parent[a]]
+            a = parent[a]
+        return a
+    left, right = lab[:, 0], lab[:, -1]
+    for a, b in zip(left, right):
+        if a and b:
+            ra, rb = find(a), find(b)
+            if ra != rb:
+                parent[ra] = rb
+    return len({find(a) for a in range(1, n + 1)})
+
+
+@pytest.mark.parametrize("A_h,steps,bounds", [
+    # no NCI: rounding differences stay small over 2000 steps
+    (0.0, 2000, {"fp32": (3e-3, 2e-3, 2e-3, 1e-5), "fp16dev": (3e-3, 3e-3, 3e-3, 1e-3)}),
+    # NCI on: its discrete decisions flip at near-ties and the packed flow amplifies
+    # the difference, so pointwise agreement is only expected over short horizons
+    (0.05, 100, {"fp32": (5e-4, 5e-3, 5e-3, 1e-5), "fp16dev": (1e-3, 1e-2, 1e-2, 1e-3)}),
+])
+def test_observable_errors_fp32_and_fp16dev(A_h, steps, bounds):
+    """512 x 64 crop of the channel workload from the same initial fields: each
+    observable's error against the FP64 oracle (relative L2 of psi and of u, relative
+    dispersed flow rate, droplet count, relative mass drift)."""
+    nx, ny = 512, 64
+    p = oracle.make_params(lattice=oracle.D2Q9, nx=nx, ny=ny, wall_y=1, tau=1.0, A_s=0.01, beta=0.7, A_h=A_h,
+                           force=(1e-5, 0, 0))
+    fl = inputs.channel_emulsion_2d(nx, ny, seed=1234)
+    f_ref = oracle.step(p, oracle.init(p, fl.rho1, fl.rho2), steps, nthreads=0)
+    o_ref = oracle.observables(p, f_ref)
+    fd_ref = oracle.fields(p, f_ref)
+    m0 = oracle.observables(p, oracle.init(p, fl.rho1, fl.rho2))["mass"]
+    psi_ref = fd_ref["psi"]
+    u_ref = fd_ref["u"][:2]
+    n_ref = _droplets(psi_ref.reshape(ny, nx))
+    for name, prec in (("fp32", lbnci.LB_FP32), ("fp16dev", lbnci.LB_FP16DEV)):
+        with lbnci.Sim(_cfg(p, prec)) as sim:
+            sim.init_fields(fl.rho1, fl.rho2)
+            sim.step(steps)
+            fd = sim.fields()
+            obs = sim.observables()
+        rep = dict(L2_psi=np.linalg.norm(fd["psi"] - psi_ref) / np.linalg.norm(psi_ref),
+                   L2_u=np.linalg.norm(fd["u"][:2] - u_ref) / np.linalg.norm(u_ref),
+                   Q_d=abs(obs["flow_rate_disp"] - o_ref["flow_rate_disp"]) / abs(o_ref["flow_rate_disp"]),
+                   mass=float(np.max(np.abs(obs["mass"] - m0) / m0)),
+                   droplets=_droplets(fd["psi"].reshape(ny, nx)))
+        print(f"A_h={A_h} steps={steps} {name}: {rep} (droplets in the oracle: {n_ref})")
+        b = bounds[name]
+        assert rep["L2_psi"] <= b[0] and rep["L2_u"] <= b[1] and rep["Q_d"] <= b[2] and rep["mass"] <= b[3], rep
+        assert rep["droplets"] == n_ref
