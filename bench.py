@@ -52,6 +52,12 @@ WORKLOADS = {
                    gen=lambda nx, ny, nz, seed: inputs.duct_emulsion_3d(nx, ny, nz, seed=seed),
                    desc="D3Q27 packed-emulsion square duct 512x128x128, walls y,z, FCC droplets R 10 "
                         "vf 0.7 target, G=2e-6, A_h=0.03"),
+    "ensemble": dict(lattice=0, nx=0, ny=0, nz=1, wall_y=1, wall_z=0, tau=1.0, A_s=0.01, beta=0.7,
+                     A_h=0.05, force=(1e-5, 0.0, 0.0), members=96,
+                     gen=lambda nx, ny, nz, seed: inputs.channel_emulsion_2d(nx, ny, seed=seed),
+                     desc="96 independent D2Q9 channels, length 512-2048, width 64-256, area fraction "
+                          "0.7-0.9, G log-uniform 1e-6..1e-4, A_h uniform 0..0.1, one batched launch per "
+                          "step (CUDA graph), autotuned tile shape"),
     "droplet2d": dict(lattice=0, nx=128, ny=128, nz=1, wall_y=0, wall_z=0, tau=1.0, A_s=0.01, beta=0.7,
                       A_h=0.05, force=(0.0, 0.0, 0.0),
                       gen=lambda nx, ny, nz, seed: inputs.droplet(nx, ny, radius=30),
@@ -249,6 +255,59 @@ def run_reference(args, w):
     return 0
 
 
+def run_ensemble(args, w, lbnci, torch, prec, ws, rank, local, dist):
+    """The ensemble workload: every member advanced by one batched launch per step."""
+    members = inputs.ensemble_channels(w["members"], seed=1234 + rank)
+    stream = torch.cuda.Stream()
+    cfgs = [lbnci.lb_config_make(nx=m.nx, ny=m.ny, wall_y=1, tau=w["tau"], A_s=w["A_s"], beta=w["beta"],
+                                 A_h=m.A_h, force=(m.force, 0.0, 0.0), precision=prec,
+                                 stream=stream.cuda_stream) for m in members]
+    N = sum(m.nx * m.ny for m in members)
+    ens = lbnci.Ensemble(cfgs)
+    for mv, m in zip(ens.members, members):
+        mv.init_fields(m.fields.rho1, m.fields.rho2)
+    spt = ens.tune()
+    t32x16, t32x32 = ens.tune_times()
+    ens.step(args.warmup)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    launches0 = ens.launches()
+    start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        start.record(stream)
+        ens.step(args.steps)  # the state (2.9 GB in FP32) is far larger than L2
+        end.record(stream)
+        torch.cuda.synchronize()
+    launches = ens.launches() - launches0
+    total_ms = max_over_ranks(start.elapsed_time(end), dist, "cuda")
+    obs = [mv.observables(allow_numeric=True) for mv in ens.members]
+    # the same lattices stepped one launch per member per step, for comparison
+    seq_ms = None
+    if not args.no_e2e:
+        sims = [lbnci.Sim(c) for c in cfgs]  # on the same stream as the ensemble
+        for sm, m in zip(sims, members):
+            sm.init_fields(m.fields.rho1, m.fields.rho2)
+        ks = max(3, args.steps // 4)
+        for sm in sims:
+            sm.step(2)
+        torch.cuda.synchronize()
+        s2, e2 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s2.record(stream)
+        for _ in range(ks):
+            for sm in sims:
+                sm.step(1)
+        e2.record(stream)
+        torch.cuda.synchronize()
+        seq_ms = s2.elapsed_time(e2) / ks
+        for sm in sims:
+            sm.close()
+    ens.close()
+    return N, total_ms, launches, clk.summary(), obs, {"tile": f"32x{8 * spt}", "tune_ms_per_step":
+                                                      {"32x16": round(t32x16, 4), "32x32": round(t32x32, 4)},
+                                                      "one_launch_per_member_ms_per_step": seq_ms}
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -281,6 +340,8 @@ def main(argv=None):
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     lbnci.load()
+    if args.workload == "ensemble":
+        return main_ensemble(args, w, lbnci, torch, ws, rank, local, dist)
     stream = torch.cuda.Stream()
     prec = {"fp32": lbnci.LB_FP32, "fp64": lbnci.LB_FP64, "fp16dev": lbnci.LB_FP16DEV}[args.precision]
     nx, ny, nz = w["nx"], w["ny"], w["nz"]
@@ -384,6 +445,38 @@ def main(argv=None):
         "gpu_launches": int(launches),
         "clocks": clocks,
         "observables": {"n_nci": obs["n_nci"], "n_interface": obs["n_interface"], "n_bad": obs["n_bad"]},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main_ensemble(args, w, lbnci, torch, ws, rank, local, dist):
+    prec = {"fp32": lbnci.LB_FP32, "fp64": lbnci.LB_FP64, "fp16dev": lbnci.LB_FP16DEV}[args.precision]
+    N, total_ms, launches, clocks, obs, extra = run_ensemble(args, w, lbnci, torch, prec, ws, rank, local, dist)
+    if dist:
+        dist.destroy_process_group()
+    if rank != 0:
+        return 0
+    ms_per_step = total_ms / args.steps
+    value = whole_job_mlups(N, args.steps, ws, total_ms * 1e-3)
+    peak, peak_kind = measured_hbm_peak()
+    bpsite = alg_bytes_per_site(0, args.precision)
+    achieved = bpsite * N / (ms_per_step * 1e-3) / 1e9
+    seq = extra["one_launch_per_member_ms_per_step"]
+    line = {
+        "metric": "MLUPS", "value": round(value, 2), "unit": "MLUPS", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(ms_per_step, 5), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": {"fp32": "f32", "fp64": "f64", "fp16dev": "f16 storage / f32 compute"}[args.precision],
+        "data": "synthetic",
+        "config": {"workload": w["desc"], "sites": N, "members": w["members"], "precision": args.precision,
+                   "l2": "state larger than L2 (not flushed)", **extra,
+                   "speedup_vs_one_launch_per_member": round(seq / ms_per_step, 3) if seq else None},
+        "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                     "frac": round(achieved / peak, 4), "traffic": None,
+                     "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)", "kernel": "fused2d_batch_kernel",
+                     "alg_bytes_per_site": bpsite},
+        "cpu_baseline": None, "e2e": None, "gpu_launches": int(launches), "clocks": clocks,
+        "flow_rate_disp": {"min": min(o["flow_rate_disp"] for o in obs), "max": max(o["flow_rate_disp"] for o in obs)},
     }
     print(json.dumps(line), flush=True)
     return 0

@@ -72,6 +72,17 @@ typedef enum {
                      rho_k per site; arithmetic in FP32 */
 } lb_precision;
 
+typedef enum {
+  /* Guo forcing of the mixture with u = (j + F/2)/rho, F = G + F_rep (default) */
+  LB_FORCE_GUO = 0,
+  /* The paper's own insertion ("Materials and Methods", last paragraph): exact
+   * difference method, the near-contact force acting on the dispersed phase only. The
+   * relaxation uses u = j/rho; after recolouring component k gains
+   * f_eq(rho_k, u + dU_k) - f_eq(rho_k, u), dU_k = F_k/rho_k, with F_1 = G rho_1/rho +
+   * F_rep and F_2 = G rho_2/rho. Reported velocities are still (j + F/2)/rho. */
+  LB_FORCE_EDM_DISPERSED = 1
+} lb_forcing;
+
 typedef struct {
   int lattice;          /* lb_lattice */
   int nx, ny, nz;       /* lattice size; nz = 1 for D2Q9 */
@@ -87,6 +98,7 @@ typedef struct {
   void* stream;         /* cudaStream_t for all work; NULL = the legacy default stream */
   void* workspace;      /* optional caller-owned device memory, 256-byte aligned */
   size_t workspace_bytes;
+  int forcing;          /* lb_forcing: how G and F_rep enter the populations */
 } lb_config;
 
 typedef struct lb_sim lb_sim;
@@ -148,6 +160,42 @@ const char* lb_last_error(const lb_sim* sim);
 
 /* Step kernels launched by this sim since lb_create (for launch accounting). */
 long long lb_kernel_launches(const lb_sim* sim);
+
+/* ------------------------------------------------------------------------------
+ * Ensembles: n independent D2Q9 lattices of different sizes and parameters (each a
+ * full lb_config: size, walls, tau, A_s, beta, A_h, h_min, h_max, g_th, force) stepped
+ * together, one batched kernel launch per step for all members, replayed from a CUDA
+ * graph. This serves the paper's parameter studies (flow rate against the driving
+ * force and the near-contact strength, "Results": Figs. 2-3) as one job. All members
+ * must share the precision. The work runs on cfgs[0].stream, or on a stream of the
+ * ensemble's own when that is NULL (graph capture needs a non-default stream).
+ * lb_ensemble_create allocates one device block for all members (cfgs[m].workspace is
+ * ignored). Each member is an ordinary lb_sim owned by the ensemble (see
+ * lb_ensemble_member): every lb_* call works on it except lb_step and lb_destroy. */
+typedef struct lb_ensemble lb_ensemble;
+
+lb_status lb_ensemble_create(const lb_config* cfgs, int n, lb_ensemble** out);
+
+/* Member m's sim handle (owned by the ensemble; valid until lb_ensemble_destroy). Use it
+ * for lb_init_fields, lb_observables, lb_fields, lb_get/set_populations. */
+lb_status lb_ensemble_member(lb_ensemble* ens, int m, lb_sim** out);
+
+/* Advance every member by nsteps. Asynchronous on the ensemble's stream. */
+lb_status lb_ensemble_step(lb_ensemble* ens, long long nsteps);
+
+/* Autotuner: time each supported tile shape (32 x 16 and 32 x 32 sites per block) of
+ * the batched step on the current state -- writing only the members' back buffers, so
+ * the state is unchanged -- and keep the fastest; *spt_out (optional) = 2 or 4. */
+lb_status lb_ensemble_tune(lb_ensemble* ens, int* spt_out);
+/* Per-step times (ms) the last lb_ensemble_tune measured for the two shapes. */
+lb_status lb_ensemble_tune_times(const lb_ensemble* ens, float* ms_32x16, float* ms_32x32);
+
+/* Batched step launches since creation; last failure on this ensemble. */
+long long lb_ensemble_launches(const lb_ensemble* ens);
+const char* lb_ensemble_last_error(const lb_ensemble* ens);
+
+/* Release the ensemble and all its members. NULL is allowed. */
+void lb_ensemble_destroy(lb_ensemble* ens);
 
 /* Observables with no allocation at all. The paper has no counterpart: this is a
  * convenience for callers that cannot let a library allocate device memory (work

@@ -37,6 +37,7 @@ class Params(ctypes.Structure):
         ("A_h", ctypes.c_double), ("h_min", ctypes.c_double), ("h_max", ctypes.c_double),
         ("g_th", ctypes.c_double),
         ("force", ctypes.c_double * 3),
+        ("forcing", ctypes.c_int),
     ]
 
 
@@ -84,7 +85,7 @@ def _f64(a):
 
 
 def make_params(lattice=D2Q9, nx=8, ny=8, nz=1, wall_y=0, wall_z=0, tau=1.0, A_s=0.0,
-                beta=0.0, A_h=0.0, h_min=2.0, h_max=4.0, g_th=0.05, force=(0.0, 0.0, 0.0)):
+                beta=0.0, A_h=0.0, h_min=2.0, h_max=4.0, g_th=0.05, force=(0.0, 0.0, 0.0), forcing=0):
     p = Params()
     p.lattice, p.nx, p.ny, p.nz = lattice, nx, ny, nz
     p.wall_y, p.wall_z = wall_y, wall_z
@@ -92,6 +93,7 @@ def make_params(lattice=D2Q9, nx=8, ny=8, nz=1, wall_y=0, wall_z=0, tau=1.0, A_s
     p.h_min, p.h_max, p.g_th = h_min, h_max, g_th
     for a in range(3):
         p.force[a] = force[a]
+    p.forcing = forcing
     return p
 
 

@@ -28,6 +28,12 @@
  *     f^2 = (rho2/rho) f - same, cos(theta_i) = c_i.m/|c_i| (0 for the rest vector);
  *   - walls: a solid neighbour contributes the psi of its mirror image across the
  *     wall plane to the gradient (neutral wetting);
+ *   - forcing = 1 (the paper's own insertion of the force, end of "Materials and
+ *     Methods": exact difference method, NCI force on the dispersed phase only): the
+ *     relaxation uses u = j/rho; after recolouring component k gains
+ *     f_eq_i(rho_k, u + dU_k) - f_eq_i(rho_k, u), dU_k = F_k/rho_k, with
+ *     F_1 = G rho_1/rho + F_rep and F_2 = G rho_2/rho (the body force acts on the
+ *     mixture in proportion to mass); the reported velocity is still (j + F/2)/rho;
  *   - NCI ray: x is an interface site when |grad psi| > g_th; for s = 1..floor(h_max)
  *     the probe y = x + round(s n) (round half away from zero per component);
  *     a probe in a wall ends the search; the first probe with |grad psi(y)| > g_th
@@ -254,7 +260,9 @@ static void nci(const orc_params* p, const lattice_t* L, const double* grad,
 }
 
 /* Stages 5-7 at one site: BGK + Guo source + perturbation on the total
- * population, then recolouring. fin is [2][Q] with stride `st`, fout with `so`. */
+ * population, then recolouring. fin is [2][Q] with stride `st`, fout with `so`.
+ * With forcing = 1 the force enters instead by the exact difference method after
+ * recolouring (see the header comment). */
 static void collide(const orc_params* p, const lattice_t* L, const double* fin, long st,
                     const double grad[3], const double F[3], double* fout, long so,
                     double* u_out) {
@@ -271,6 +279,9 @@ static void collide(const orc_params* p, const lattice_t* L, const double* fin, 
   double u[3];
   for (int a = 0; a < 3; ++a) u[a] = (j[a] + 0.5 * F[a]) / rho;
   if (u_out) for (int a = 0; a < 3; ++a) u_out[a] = u[a];
+  const int edm = p->forcing == 1;
+  double ueq[3];  /* velocity of the equilibrium the populations relax to */
+  for (int a = 0; a < 3; ++a) ueq[a] = edm ? j[a] / rho : u[a];
 
   double g = sqrt(grad[0] * grad[0] + grad[1] * grad[1] + grad[2] * grad[2]);
   double m[3] = {0.0, 0.0, 0.0}; /* unit colour gradient, grad psi/|grad psi| */
@@ -280,22 +291,45 @@ static void collide(const orc_params* p, const lattice_t* L, const double* fin, 
   double guo = 1.0 - 0.5 * omega;
   double uF = u[0] * F[0] + u[1] * F[1] + u[2] * F[2];
   double seg = p->beta * rho1 * rho2 / rho;
+  /* exact difference method: velocity shift of each component */
+  double dU[2][3] = {{0.0, 0.0, 0.0}, {0.0, 0.0, 0.0}};
+  if (edm) {
+    for (int a = 0; a < 3; ++a) {
+      double G = p->force[a], Frep = F[a] - p->force[a];
+      if (rho1 > 0.0) dU[0][a] = (G * rho1 / rho + Frep) / rho1;
+      if (rho2 > 0.0) dU[1][a] = (G * rho2 / rho) / rho2;
+    }
+  }
   for (int i = 0; i < Q; ++i) {
     double fi = fin[i * st] + fin[(Q + i) * st];
     double cu = L->c[i][0] * u[0] + L->c[i][1] * u[1] + L->c[i][2] * u[2];
     double cF = L->c[i][0] * F[0] + L->c[i][1] * F[1] + L->c[i][2] * F[2];
     double cm = L->c[i][0] * m[0] + L->c[i][1] * m[1] + L->c[i][2] * m[2];
-    /* Omega^(1): BGK towards f_eq(rho, u), plus the Guo source term. */
-    double S = guo * L->w[i] * (3.0 * (cF - uF) + 9.0 * cu * cF);
-    double fs = fi - omega * (fi - feq(L, i, rho, u)) + S;
+    double fs;
+    if (!edm) {
+      /* Omega^(1): BGK towards f_eq(rho, u), plus the Guo source term. */
+      double S = guo * L->w[i] * (3.0 * (cF - uF) + 9.0 * cu * cF);
+      fs = fi - omega * (fi - feq(L, i, rho, u)) + S;
+    } else {
+      fs = fi - omega * (fi - feq(L, i, rho, ueq));
+    }
     /* Omega^(2): perturbation, summed over the two components. */
     double pert = 2.0 * (0.5 * p->A_s) * g * (L->w[i] * cm * cm - L->w[i] / 3.0);
     fs += pert;
     /* Omega^(3): recolouring. */
     double cos_t = cm * L->inv_len[i];
     double rc = seg * L->w[i] * cos_t;
-    fout[i * so] = rho1 / rho * fs + rc;
-    fout[(Q + i) * so] = rho2 / rho * fs - rc;
+    double o1 = rho1 / rho * fs + rc;
+    double o2 = rho2 / rho * fs - rc;
+    if (edm) {
+      /* forcing: f_eq(rho_k, u + dU_k) - f_eq(rho_k, u) for each component */
+      double u1[3], u2[3];
+      for (int a = 0; a < 3; ++a) { u1[a] = ueq[a] + dU[0][a]; u2[a] = ueq[a] + dU[1][a]; }
+      o1 += feq(L, i, rho1, u1) - feq(L, i, rho1, ueq);
+      o2 += feq(L, i, rho2, u2) - feq(L, i, rho2, ueq);
+    }
+    fout[i * so] = o1;
+    fout[(Q + i) * so] = o2;
   }
 }
 

@@ -36,6 +36,8 @@ typedef struct {
   double h_min, h_max; /* NCI cut-offs in lattice units */
   double g_th;   /* |grad psi| above which a site belongs to an interface */
   double force[3]; /* uniform body-force density G */
+  int forcing;   /* 0: Guo forcing of the mixture; 1: exact difference method with the
+                    NCI force on the dispersed phase only (see lbnci_oracle.c) */
 } orc_params;
 
 /* Lattice tables: c[Q][3], w[Q], opp[Q]. Returns Q, or -1 for an unknown lattice. */

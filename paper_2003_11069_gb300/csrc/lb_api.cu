@@ -10,6 +10,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <mutex>
+#include <vector>
 #include <new>
 
 #include "lbnci.h"
@@ -55,7 +56,7 @@ using namespace lbnci;
 
 struct lb_sim {
   lb_config cfg;
-  HostParams p;
+  HostParams p{};
   const Launchers* L;
   int Q;
   int device;
@@ -71,6 +72,7 @@ struct lb_sim {
   void* base;      // cudaMalloc'd block
   long long step;
   long long launches;
+  bool in_ensemble;  // stepped by its ensemble only
   char err[256];
 };
 
@@ -121,6 +123,8 @@ lb_status validate(const lb_config* c, HostParams* p, Layout* lay, long long* nb
   if (!(c->g_th >= 0.0) || !std::isfinite(c->g_th)) return fail(nullptr, LB_EINVAL, "g_th must be >= 0");
   for (int a = 0; a < 3; ++a)
     if (!std::isfinite(c->force[a])) return fail(nullptr, LB_EINVAL, "force must be finite");
+  if (c->forcing != LB_FORCE_GUO && c->forcing != LB_FORCE_EDM_DISPERSED)
+    return fail(nullptr, LB_EINVAL, "unknown forcing scheme %d", c->forcing);
   int smax = 0;
   if (c->A_h > 0.0) {
     if (!(c->h_min > 0.0 && c->h_min <= c->h_max && c->h_max < kMaxProbe + 1.0))
@@ -140,6 +144,8 @@ lb_status validate(const lb_config* c, HostParams* p, Layout* lay, long long* nb
   for (int a = 0; a < 3; ++a) p->G[a] = c->force[a];
   if (c->lattice == LB_D2Q9) p->G[2] = 0.0;
   p->smax = smax;
+  p->forcing = c->forcing;
+  p->num_sms = 1;
   // Tile of the fused D2Q9 kernel: LBNCI_FUSED_SPT=2 (32x16, the default) or 4 (32x32).
   p->spt = 2;
   if (const char* e = std::getenv("LBNCI_FUSED_SPT")) p->spt = std::atoi(e) == 4 ? 4 : 2;
@@ -192,7 +198,7 @@ extern "C" {
 
 lb_status lb_workspace_size(const lb_config* cfg, size_t* bytes) {
   if (!bytes) return fail(nullptr, LB_EINVAL, "bytes is NULL");
-  HostParams p;
+  HostParams p{};
   Layout lay;
   long long nb;
   lb_status st = validate(cfg, &p, &lay, &nb);
@@ -204,7 +210,7 @@ lb_status lb_workspace_size(const lb_config* cfg, size_t* bytes) {
 lb_status lb_create(const lb_config* cfg, lb_sim** out) {
   if (!out) return fail(nullptr, LB_EINVAL, "out is NULL");
   *out = nullptr;
-  HostParams p;
+  HostParams p{};
   Layout lay;
   long long nblocks;
   lb_status st = validate(cfg, &p, &lay, &nblocks);
@@ -297,6 +303,7 @@ lb_status lb_init_fields(lb_sim* s, const double* rho1, const double* rho2, cons
 lb_status lb_step(lb_sim* s, long long nsteps) {
   if (!s) return fail(nullptr, LB_EINVAL, "sim is NULL");
   if (nsteps < 0) return fail(s, LB_EINVAL, "nsteps must be >= 0");
+  if (s->in_ensemble) return fail(s, LB_EINVAL, "an ensemble member is stepped by lb_ensemble_step");
   for (long long t = 0; t < nsteps; ++t) {
     int nk = 0;
     cudaError_t e = s->L->step(s->fa, s->fb, s->psi, s->p, s->stream, &nk);
@@ -496,7 +503,7 @@ lb_status noalloc_scratch(void** out) {
 extern "C" lb_status lb_observables_noalloc(const lb_config* cfg, const void* f, lb_obs* out) {
   if (!out) return fail(nullptr, LB_EINVAL, "out is NULL");
   if (!f) return fail(nullptr, LB_EINVAL, "f is NULL");
-  HostParams p;
+  HostParams p{};
   Layout lay;
   long long nblocks;
   lb_status st = validate(cfg, &p, &lay, &nblocks);
@@ -545,3 +552,248 @@ extern "C" lb_status lb_observables_noalloc(const lb_config* cfg, const void* f,
   return out->n_bad > 0 ? fail(nullptr, LB_ENUMERIC, "non-finite or non-positive density at %lld sites", out->n_bad)
                         : LB_OK;
 }
+
+// ---------------------------------------------------------------------------------
+// Ensembles: many independent D2Q9 lattices (different sizes and parameters) stepped
+// together by one batched launch per step, replayed from a CUDA graph.
+struct lb_ensemble {
+  int n;
+  const Launchers* L;
+  cudaStream_t stream;
+  bool own_stream;
+  std::vector<lb_sim*> members;
+  void* base;              // one allocation holding every member's workspace
+  std::vector<unsigned char> host_members;  // BatchMember records (host copy)
+  void* d_members;         // device copy of the member records
+  int* d_tile0;            // first tile of every member, n + 1 entries
+  int spt;                 // tile shape: 32 x (8 spt) sites per block
+  int total_tiles;
+  int smax_max;
+  int parity;              // 0: the current state is every member's buffer 0
+  cudaGraphExec_t graph;   // two steps (parity 0 -> 1 -> 0), valid for the current spt
+  bool graph_ok;
+  long long launches;
+  float tune_ms[2];        // last autotuner timings per step for spt = 2 and 4
+  char err[256];
+};
+
+namespace {
+
+lb_status efail(lb_ensemble* e, lb_status st, const char* fmt, ...) {
+  char* dst = e ? e->err : g_err;
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(dst, 256, fmt, ap);
+  va_end(ap);
+  return st;
+}
+
+lb_status ecuda(lb_ensemble* e, cudaError_t c, const char* what) {
+  cudaGetLastError();
+  return efail(e, LB_ECUDA, "%s: %s", what, cudaGetErrorString(c));
+}
+
+// Tile offsets for the current tile shape, uploaded to the device.
+lb_status ens_layout(lb_ensemble* e) {
+  std::vector<int> t0(e->n + 1, 0);
+  for (int m = 0; m < e->n; ++m) t0[m + 1] = t0[m] + e->L->batch_tiles(e->members[m]->p, e->spt);
+  e->total_tiles = t0[e->n];
+  cudaError_t c = cudaMemcpyAsync(e->d_tile0, t0.data(), sizeof(int) * (e->n + 1), cudaMemcpyHostToDevice, e->stream);
+  if (c == cudaSuccess) c = cudaStreamSynchronize(e->stream);
+  if (c != cudaSuccess) return ecuda(e, c, "tile table upload");
+  if (e->graph_ok) { cudaGraphExecDestroy(e->graph); e->graph_ok = false; }
+  return LB_OK;
+}
+
+cudaError_t ens_launch(lb_ensemble* e, int parity) {
+  return e->L->batch_step(e->d_members, e->d_tile0, e->n, e->total_tiles, parity, e->spt, e->smax_max, e->stream);
+}
+
+}  // namespace
+
+extern "C" {
+
+lb_status lb_ensemble_create(const lb_config* cfgs, int n, lb_ensemble** out) {
+  if (!out) return efail(nullptr, LB_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (!cfgs || n < 1) return efail(nullptr, LB_EINVAL, "an ensemble needs n >= 1 configurations");
+  for (int m = 0; m < n; ++m) {
+    if (cfgs[m].lattice != LB_D2Q9) return efail(nullptr, LB_EUNSUPPORTED, "ensembles are D2Q9 only (member %d)", m);
+    if (cfgs[m].precision != cfgs[0].precision)
+      return efail(nullptr, LB_EINVAL, "all members need the same precision (member %d)", m);
+  }
+  std::vector<size_t> ws(n);
+  size_t total = 0;
+  for (int m = 0; m < n; ++m) {
+    lb_config c = cfgs[m];
+    c.workspace = nullptr;
+    lb_status st = lb_workspace_size(&c, &ws[m]);
+    if (st != LB_OK) return efail(nullptr, st, "member %d: %s", m, g_err);
+    total += align256(ws[m]);
+  }
+  lb_ensemble* e = new (std::nothrow) lb_ensemble();
+  if (!e) return efail(nullptr, LB_ENOMEM, "host allocation failed");
+  e->n = n;
+  e->L = launchers_for(&cfgs[0]);
+  e->spt = 2;
+  e->stream = (cudaStream_t)cfgs[0].stream;
+  cudaError_t c = cudaSuccess;
+  if (!e->stream) {  // graph capture needs a stream other than the legacy default one
+    c = cudaStreamCreateWithFlags(&e->stream, cudaStreamNonBlocking);
+    if (c != cudaSuccess) { delete e; return efail(nullptr, LB_ECUDA, "stream creation failed: %s", cudaGetErrorString(c)); }
+    e->own_stream = true;
+  }
+  c = cudaMalloc(&e->base, total);
+  if (c != cudaSuccess) {
+    cudaGetLastError();
+    lb_ensemble_destroy(e);
+    return efail(nullptr, c == cudaErrorMemoryAllocation ? LB_ENOMEM : LB_ECUDA, "cudaMalloc of %zu bytes failed", total);
+  }
+  size_t off = 0;
+  for (int m = 0; m < n; ++m) {
+    lb_config cm = cfgs[m];
+    cm.stream = e->stream;
+    cm.workspace = (unsigned char*)e->base + off;
+    cm.workspace_bytes = ws[m];
+    off += align256(ws[m]);
+    lb_sim* s = nullptr;
+    lb_status st = lb_create(&cm, &s);
+    if (st != LB_OK) { lb_ensemble_destroy(e); return efail(nullptr, st, "member %d: %s", m, g_err); }
+    s->in_ensemble = true;
+    e->members.push_back(s);
+    e->smax_max = std::max(e->smax_max, s->p.smax);
+  }
+  const size_t rec = e->L->batch_member_bytes;
+  e->host_members.resize(rec * n);
+  for (int m = 0; m < n; ++m)
+    e->L->batch_fill(e->host_members.data() + rec * m, e->members[m]->p, e->members[m]->fa, e->members[m]->fb);
+  c = cudaMalloc(&e->d_members, rec * n);
+  if (c == cudaSuccess) c = cudaMalloc((void**)&e->d_tile0, sizeof(int) * (n + 1));
+  if (c == cudaSuccess)
+    c = cudaMemcpyAsync(e->d_members, e->host_members.data(), rec * n, cudaMemcpyHostToDevice, e->stream);
+  if (c != cudaSuccess) {
+    cudaGetLastError();
+    lb_ensemble_destroy(e);
+    return efail(nullptr, LB_ECUDA, "member table: %s", cudaGetErrorString(c));
+  }
+  lb_status st = ens_layout(e);
+  if (st != LB_OK) { lb_ensemble_destroy(e); return efail(nullptr, st, "%s", "tile table upload failed"); }
+  *out = e;
+  return LB_OK;
+}
+
+lb_status lb_ensemble_member(lb_ensemble* e, int m, lb_sim** out) {
+  if (!e || !out) return efail(e, LB_EINVAL, "NULL argument");
+  if (m < 0 || m >= e->n) return efail(e, LB_EINVAL, "member %d out of range [0, %d)", m, e->n);
+  *out = e->members[m];
+  return LB_OK;
+}
+
+lb_status lb_ensemble_step(lb_ensemble* e, long long nsteps) {
+  if (!e) return efail(nullptr, LB_EINVAL, "ensemble is NULL");
+  if (nsteps < 0) return efail(e, LB_EINVAL, "nsteps must be >= 0");
+  cudaError_t c;
+  long long left = nsteps;
+  if (left > 0 && e->parity == 1) {  // back to parity 0, where the two-step graph starts
+    c = ens_launch(e, 1);
+    if (c != cudaSuccess) return ecuda(e, c, "ensemble step launch");
+    ++e->launches;
+    e->parity = 0;
+    --left;
+  }
+  if (left >= 2 && !e->graph_ok) {
+    cudaGraph_t g;
+    c = cudaStreamBeginCapture(e->stream, cudaStreamCaptureModeThreadLocal);
+    if (c == cudaSuccess) {
+      cudaError_t c1 = ens_launch(e, 0);
+      cudaError_t c2 = ens_launch(e, 1);
+      c = cudaStreamEndCapture(e->stream, &g);
+      if (c == cudaSuccess && (c1 != cudaSuccess || c2 != cudaSuccess)) c = c1 != cudaSuccess ? c1 : c2;
+      if (c == cudaSuccess) {
+        c = cudaGraphInstantiate(&e->graph, g, 0);
+        cudaGraphDestroy(g);
+      }
+    }
+    if (c != cudaSuccess) return ecuda(e, c, "ensemble graph capture");
+    e->graph_ok = true;
+  }
+  for (; left >= 2; left -= 2) {
+    c = cudaGraphLaunch(e->graph, e->stream);
+    if (c != cudaSuccess) return ecuda(e, c, "ensemble graph launch");
+    e->launches += 2;
+  }
+  if (left == 1) {
+    c = ens_launch(e, 0);
+    if (c != cudaSuccess) return ecuda(e, c, "ensemble step launch");
+    ++e->launches;
+    e->parity = 1;
+  }
+  // the members' current state buffer follows the parity
+  const bool odd = (nsteps & 1) != 0;
+  for (lb_sim* s : e->members) {
+    if (odd) std::swap(s->fa, s->fb);
+    s->step += nsteps;
+  }
+  return LB_OK;
+}
+
+lb_status lb_ensemble_tune(lb_ensemble* e, int* spt_out) {
+  if (!e) return efail(nullptr, LB_EINVAL, "ensemble is NULL");
+  // Time each tile shape on the current state, writing only the back buffers (the
+  // state itself is unchanged), and keep the fastest.
+  const int shapes[2] = {2, 4};
+  cudaEvent_t t0, t1;
+  cudaError_t c = cudaEventCreate(&t0);
+  if (c == cudaSuccess) c = cudaEventCreate(&t1);
+  if (c != cudaSuccess) return ecuda(e, c, "event creation");
+  int best = e->spt;
+  float best_ms = 1e30f;
+  for (int k = 0; k < 2 && c == cudaSuccess; ++k) {
+    e->spt = shapes[k];
+    lb_status st = ens_layout(e);
+    if (st != LB_OK) { cudaEventDestroy(t0); cudaEventDestroy(t1); return st; }
+    c = ens_launch(e, e->parity);  // warm-up
+    if (c == cudaSuccess) c = cudaEventRecord(t0, e->stream);
+    for (int r = 0; r < 5 && c == cudaSuccess; ++r) c = ens_launch(e, e->parity);
+    if (c == cudaSuccess) c = cudaEventRecord(t1, e->stream);
+    if (c == cudaSuccess) c = cudaEventSynchronize(t1);
+    float ms = 0.f;
+    if (c == cudaSuccess) c = cudaEventElapsedTime(&ms, t0, t1);
+    e->launches += 6;
+    e->tune_ms[k] = ms / 5.f;
+    if (c == cudaSuccess && ms < best_ms) { best_ms = ms; best = shapes[k]; }
+  }
+  cudaEventDestroy(t0);
+  cudaEventDestroy(t1);
+  if (c != cudaSuccess) return ecuda(e, c, "autotune");
+  e->spt = best;
+  lb_status st = ens_layout(e);
+  if (st != LB_OK) return st;
+  if (spt_out) *spt_out = best;
+  return LB_OK;
+}
+
+lb_status lb_ensemble_tune_times(const lb_ensemble* e, float* ms2, float* ms4) {
+  if (!e) return efail(nullptr, LB_EINVAL, "ensemble is NULL");
+  if (ms2) *ms2 = e->tune_ms[0];
+  if (ms4) *ms4 = e->tune_ms[1];
+  return LB_OK;
+}
+
+long long lb_ensemble_launches(const lb_ensemble* e) { return e ? e->launches : 0; }
+
+const char* lb_ensemble_last_error(const lb_ensemble* e) { return e ? e->err : g_err; }
+
+void lb_ensemble_destroy(lb_ensemble* e) {
+  if (!e) return;
+  if (e->stream) cudaStreamSynchronize(e->stream);
+  if (e->graph_ok) cudaGraphExecDestroy(e->graph);
+  for (lb_sim* s : e->members) lb_destroy(s);
+  if (e->d_members) cudaFree(e->d_members);
+  if (e->d_tile0) cudaFree(e->d_tile0);
+  if (e->base) cudaFree(e->base);
+  if (e->own_stream) cudaStreamDestroy(e->stream);
+  delete e;
+}
+
+}  // extern "C"

@@ -27,19 +27,25 @@ size_t fused2d_smem_bytes(int smax, int spt) {
   return sizeof(T) * (psi + ng);
 }
 
+// Resident blocks per SM the fused kernels are built for (their register budget).
 template <typename ST, int SPT>
-__global__ void __launch_bounds__(256, SPT <= 2 ? (sizeof(typename ST::Compute) == 4 && !ST::kHalf ? 3 : 2) : 1)
-fused2d_kernel(typename ST::Reader f, typename ST::Writer fout, StepT<typename ST::Compute> p) {
+constexpr int fused2d_min_blocks() {
+  return SPT <= 2 ? (sizeof(typename ST::Compute) == 4 && !ST::kHalf ? 3 : 2) : 1;
+}
+
+// One 32 x (8*SPT) tile with origin (x0, y0) of a lattice; the whole block calls it.
+template <typename ST, int SPT>
+__device__ __forceinline__ void fused2d_tile(const typename ST::Reader& f, const typename ST::Writer& fout,
+                                             const StepT<typename ST::Compute>& p, int x0, int y0,
+                                             unsigned char* smem_raw) {
   using T = typename ST::Compute;
   constexpr int Q = 9, TX = kFusedTX, TYT = kFusedThreadsY, TY = TYT * SPT;
   constexpr int NT = TX * TYT;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
   const int S = p.smax, R = S + 1;
   const int RX = TX + 2 * R, RY = TY + 2 * R;
   const int GX = TX + 2 * S, GY = TY + 2 * S, GXY = GX * GY;
   T* s_psi = reinterpret_cast<T*>(smem_raw);
   T* s_ng = s_psi + RX * RY;  // [3][GXY]: n_x, n_y, |grad psi|
-  const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
   const int tx = threadIdx.x, ty = threadIdx.y, tid = tx + TX * ty;
 
   // phase 1: own sites into registers, their psi into shared memory; an own position
@@ -149,8 +155,48 @@ fused2d_kernel(typename ST::Reader f, typename ST::Writer fout, StepT<typename S
 #pragma unroll
     for (int a = 0; a < 3; ++a) u[a] = M<T>::div(j[a] + T(0.5) * F[a], rho);
     const T m[3] = {-n0, -n1, T(0)};
-    collide_store<0, T>(fin[s], rho1, rho2, u, F, g, m, p, fout, idx);
+    collide_store<0, T>(fin[s], rho1, rho2, j, u, F, g, m, p, fout, idx);
   }
+}
+
+template <typename ST, int SPT>
+__global__ void __launch_bounds__(256, (fused2d_min_blocks<ST, SPT>()))
+fused2d_kernel(typename ST::Reader f, typename ST::Writer fout, StepT<typename ST::Compute> p) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  fused2d_tile<ST, SPT>(f, fout, p, blockIdx.x * kFusedTX, blockIdx.y * (kFusedThreadsY * SPT), smem_raw);
+}
+
+// One lattice of an ensemble: its step parameters, its two state buffers and the
+// number of its tile columns; tiles of member m are blocks [tile0[m], tile0[m+1]).
+template <typename T>
+struct BatchMember {
+  StepT<T> p;
+  const void* buf[2];
+  int ntx;
+};
+
+// The D2Q9 step of every member of an ensemble in one launch: block b finds its member
+// by binary search over the tile offsets, then steps one tile of it with the member's
+// own parameters, reading buf[parity] and writing buf[1 - parity].
+template <typename ST, int SPT>
+__global__ void __launch_bounds__(256, (fused2d_min_blocks<ST, SPT>()))
+fused2d_batch_kernel(const BatchMember<typename ST::Compute>* __restrict__ members, const int* __restrict__ tile0,
+                     int nmembers, int parity) {
+  using T = typename ST::Compute;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int b = blockIdx.x;
+  int lo = 0, hi = nmembers - 1;
+  while (lo < hi) {  // last member whose first tile is <= b
+    const int mid = (lo + hi + 1) >> 1;
+    if (tile0[mid] <= b) lo = mid; else hi = mid - 1;
+  }
+  const BatchMember<T>& mb = members[lo];
+  const StepT<T> p = mb.p;
+  const int t = b - tile0[lo];
+  const int by = t / mb.ntx, bx = t - by * mb.ntx;
+  const unsigned N = (unsigned)p.N;
+  fused2d_tile<ST, SPT>(ST::reader(mb.buf[parity], N), ST::writer(const_cast<void*>(mb.buf[1 - parity]), N), p,
+                        bx * kFusedTX, by * (kFusedThreadsY * SPT), smem_raw);
 }
 
 }  // namespace lbnci

@@ -6,6 +6,8 @@
 #include "lb_kernels.cuh"
 #include "lb_launch.h"
 
+#include <cstring>
+
 namespace lbnci {
 namespace {
 
@@ -14,6 +16,7 @@ StepT<T> convert(const HostParams& h) {
   StepT<T> p;
   p.nx = h.nx; p.ny = h.ny; p.nz = h.nz; p.wall_y = h.wall_y; p.wall_z = h.wall_z;
   p.N = h.N; p.smax = h.smax;
+  p.edm = h.forcing == 1;
   // Derived constants computed in T exactly as the per-site formulas would.
   p.omega = T(1) / T(h.tau);
   p.guo = T(1) - T(0.5) * p.omega;
@@ -125,10 +128,47 @@ cudaError_t l_encode(const double* in, void* f, int s0, int count, long long pit
   return cudaGetLastError();
 }
 
+template <typename ST>
+void l_batch_fill(void* dst, const HostParams& h, const void* buf0, const void* buf1) {
+  BatchMember<typename ST::Compute> m;
+  m.p = convert<typename ST::Compute>(h);
+  m.buf[0] = buf0;
+  m.buf[1] = buf1;
+  m.ntx = (h.nx + kFusedTX - 1) / kFusedTX;
+  memcpy(dst, &m, sizeof(m));
+}
+
+int l_batch_tiles(const HostParams& h, int spt) {
+  const int ty = kFusedThreadsY * spt;
+  return ((h.nx + kFusedTX - 1) / kFusedTX) * ((h.ny + ty - 1) / ty);
+}
+
+template <typename ST, int SPT>
+cudaError_t launch_batch(const void* members, const int* tile0, int n, int total_tiles, int parity, int smax_max,
+                         cudaStream_t s) {
+  static size_t configured = 0;
+  const size_t sm = fused2d_smem_bytes<typename ST::Compute>(smax_max, SPT);
+  cudaError_t e = allow_smem(fused2d_batch_kernel<ST, SPT>, sm, &configured);
+  if (e != cudaSuccess) return e;
+  fused2d_batch_kernel<ST, SPT><<<total_tiles, dim3(kFusedTX, kFusedThreadsY, 1), sm, s>>>(
+      (const BatchMember<typename ST::Compute>*)members, tile0, n, parity);
+  return cudaGetLastError();
+}
+
+template <int LAT, typename ST>
+cudaError_t l_batch_step(const void* members, const int* tile0, int n, int total_tiles, int parity, int spt,
+                         int smax_max, cudaStream_t s) {
+  if (LAT != 0) return cudaErrorNotSupported;
+  return spt == 4 ? launch_batch<ST, 4>(members, tile0, n, total_tiles, parity, smax_max, s)
+                  : launch_batch<ST, 2>(members, tile0, n, total_tiles, parity, smax_max, s);
+}
+
 template <int LAT, typename ST>
 const Launchers* table() {
   static const Launchers L = {ST::bytes, sizeof(typename ST::Compute), l_init<LAT, ST>, l_step<LAT, ST>,
-                              l_fields<LAT, ST>, l_decode<LAT, ST>, l_encode<LAT, ST>};
+                              l_fields<LAT, ST>, l_decode<LAT, ST>, l_encode<LAT, ST>,
+                              sizeof(BatchMember<typename ST::Compute>), l_batch_fill<ST>, l_batch_tiles,
+                              l_batch_step<LAT, ST>};
   return &L;
 }
 

@@ -206,81 +206,137 @@ __device__ __forceinline__ void momentum(const T fin[2][Lattice<LAT>::Q], T j[3]
 // (A_s/2)|grad psi| [w_i (c_i.m)^2 - w_i/3] of each component, on the total
 // population; then recolouring f^1 = (rho1/rho) f* + beta rho1 rho2/rho w_i cos(theta_i),
 // f^2 = (rho2/rho) f* - same, cos(theta_i) = c_i.m/|c_i|. m = grad psi/|grad psi|.
+// f_eq of the second-order lattice BGK model, c_s^2 = 1/3, for direction i.
+template <int LAT, int I, typename T>
+__device__ __forceinline__ T feq_dir(T rho, const T v[3]) {
+  constexpr T w = T(Lattice<LAT>::w(I));
+  constexpr T cx = T(cc(I, 0)), cy = T(cc(I, 1)), cz = T(cc(I, 2));
+  const T cu = cx * v[0] + cy * v[1] + cz * v[2];
+  const T uu = v[0] * v[0] + v[1] * v[1] + v[2] * v[2];
+  return w * rho * (T(1) + T(3) * cu + T(4.5) * cu * cu - T(1.5) * uu);
+}
+
+// The collision written term by term as in the oracle (FP64 rounds exactly like it):
+// Guo forcing, or, with p.edm, relaxation towards f_eq(rho, j/rho) and the exact
+// difference method after recolouring, component k gaining
+// f_eq(rho_k, u + dU_k) - f_eq(rho_k, u), dU_k = F_k/rho_k, F_1 = G rho_1/rho + F_rep,
+// F_2 = G rho_2/rho (the near-contact force acts on the dispersed phase only).
 template <int LAT, typename T, typename WR>
-__device__ __forceinline__ void collide_store(const T fin[2][Lattice<LAT>::Q], T rho1, T rho2, const T u[3],
-                                              const T F[3], T g, const T m[3], const StepT<T>& p,
+__device__ __forceinline__ void collide_exact(const T fin[2][Lattice<LAT>::Q], T rho1, T rho2, const T j[3],
+                                              const T u[3], const T F[3], T g, const T m[3], const StepT<T>& p,
                                               const WR& fout, int idx) {
   constexpr int Q = Lattice<LAT>::Q;
+  const T rho = rho1 + rho2;
+  const bool edm = p.edm != 0;
+  T ueq[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) ueq[a] = edm ? M<T>::div(j[a], rho) : u[a];
+  T u1[3], u2[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    T d1 = T(0), d2 = T(0);
+    if (edm) {
+      const T G = p.G[a], Frep = F[a] - p.G[a];
+      if (rho1 > T(0)) d1 = M<T>::div(M<T>::div(G * rho1, rho) + Frep, rho1);
+      if (rho2 > T(0)) d2 = M<T>::div(M<T>::div(G * rho2, rho), rho2);
+    }
+    u1[a] = ueq[a] + d1;
+    u2[a] = ueq[a] + d2;
+  }
+  const T uF = u[0] * F[0] + u[1] * F[1] + u[2] * F[2];
+  const T seg = M<T>::div(p.beta * rho1 * rho2, rho);
+  const T pamp = p.pamp * g;
+  const T c1 = M<T>::div(rho1, rho), c2 = M<T>::div(rho2, rho);
+  static_for<Q>([&](auto I) {
+    constexpr int i = decltype(I)::value;
+    constexpr T w = T(Lattice<LAT>::w(i));
+    constexpr T cx = T(cc(i, 0)), cy = T(cc(i, 1)), cz = T(cc(i, 2));
+    constexpr T w3 = w / T(3);
+    constexpr T inv_len = speed2(i) == 0 ? T(0)
+                        : T(1) / (speed2(i) == 1 ? T(1) : (speed2(i) == 2 ? T(1.4142135623730951)
+                                                                           : T(1.7320508075688772)));
+    const T fi = fin[0][i] + fin[1][i];
+    const T cm = cx * m[0] + cy * m[1] + cz * m[2];
+    T fs;
+    if (!edm) {
+      const T cu = cx * u[0] + cy * u[1] + cz * u[2];
+      const T cF = cx * F[0] + cy * F[1] + cz * F[2];
+      const T S = p.guo * w * (T(3) * (cF - uF) + T(9) * cu * cF);
+      fs = fi - p.omega * (fi - feq_dir<LAT, i, T>(rho, u)) + S;
+    } else {
+      fs = fi - p.omega * (fi - feq_dir<LAT, i, T>(rho, ueq));
+    }
+    fs += pamp * (w * cm * cm - w3);
+    const T rc = seg * w * (cm * inv_len);
+    T o1 = c1 * fs + rc;
+    T o2 = c2 * fs - rc;
+    if (edm) {
+      o1 += feq_dir<LAT, i, T>(rho1, u1) - feq_dir<LAT, i, T>(rho1, ueq);
+      o2 += feq_dir<LAT, i, T>(rho2, u2) - feq_dir<LAT, i, T>(rho2, ueq);
+    }
+    fout.template put<i>((unsigned)idx, o1, o2, rho1, rho2);
+  });
+  fout.put_rho((unsigned)idx, rho1, rho2);
+}
+
+// BGK relaxation towards f_eq(rho, u) with the Guo source, plus the perturbation
+// (A_s/2)|grad psi| [w_i (c_i.m)^2 - w_i/3] of each component, on the total
+// population; then recolouring f^1 = (rho1/rho) f* + beta rho1 rho2/rho w_i cos(theta_i),
+// f^2 = (rho2/rho) f* - same, cos(theta_i) = c_i.m/|c_i|. m = grad psi/|grad psi|.
+template <int LAT, typename T, typename WR>
+__device__ __forceinline__ void collide_store(const T fin[2][Lattice<LAT>::Q], T rho1, T rho2, const T j[3],
+                                              const T u[3], const T F[3], T g, const T m[3], const StepT<T>& p,
+                                              const WR& fout, int idx) {
+  constexpr int Q = Lattice<LAT>::Q;
+  if (std::is_same<T, double>::value || p.edm) {
+    collide_exact<LAT, T, WR>(fin, rho1, rho2, j, u, F, g, m, p, fout, idx);
+    return;
+  }
   const T rho = rho1 + rho2;
   const T uF = u[0] * F[0] + u[1] * F[1] + u[2] * F[2];
   const T uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
   const T seg = M<T>::div(p.beta * rho1 * rho2, rho);
   const T pamp = p.pamp * g;
-  const T c1 = M<T>::div(rho1, rho), c2 = M<T>::div(rho2, rho);
-  if constexpr (std::is_same<T, double>::value) {
-    // FP64: the expressions exactly as written above, in the oracle's order.
-    static_for<Q>([&](auto I) {
-      constexpr int i = decltype(I)::value;
+  const T c1 = M<T>::div(rho1, rho);
+  // FP32: the same operator regrouped per site,
+  //   f*_i = (1 - omega) f_i + w_i [K0 + c.u (omega rho (3 + 4.5 c.u) + 9 guo c.F) + 3 guo c.F + pamp (c.m)^2]
+  //   K0 = omega rho (1 - 1.5 u.u) - 3 guo u.F - pamp/3,
+  // so that each direction costs a short chain of multiply-adds. The rest population
+  // of each component is set to rho_k minus the others (its exact value), so per-site
+  // mass is kept to the rounding of one sum instead of drifting with the coherent
+  // rounding of K0.
+  const T orho = p.omega * rho;
+  const T K0 = orho * (T(1) - T(1.5) * uu) - T(3) * p.guo * uF - pamp * T(1.0 / 3.0);
+  const T a3 = T(3) * orho, a45 = T(4.5) * orho, g3 = T(3) * p.guo, g9 = T(9) * p.guo;
+  const T om1 = T(1) - p.omega;
+  T s1 = T(0), s2 = T(0);
+  static_for<Q>([&](auto I) {
+    constexpr int i = decltype(I)::value;
+    if constexpr (i > 0) {
       constexpr T w = T(Lattice<LAT>::w(i));
-      constexpr T cx = T(cc(i, 0)), cy = T(cc(i, 1)), cz = T(cc(i, 2));
-      constexpr T w3 = w / T(3);
-      constexpr T inv_len = speed2(i) == 0 ? T(0)
-                          : T(1) / (speed2(i) == 1 ? T(1) : (speed2(i) == 2 ? T(1.4142135623730951)
-                                                                             : T(1.7320508075688772)));
+      constexpr int ix = cc(i, 0), iy = cc(i, 1), iz = cc(i, 2);
+      constexpr T wl = T(Lattice<LAT>::w(i) / (speed2(i) == 1 ? 1.0 : (speed2(i) == 2 ? 1.4142135623730951
+                                                                                       : 1.7320508075688772)));
+      auto dotc = [&](const T v[3]) {
+        T r = T(0);
+        if constexpr (ix == 1) r += v[0]; else if constexpr (ix == -1) r -= v[0];
+        if constexpr (iy == 1) r += v[1]; else if constexpr (iy == -1) r -= v[1];
+        if constexpr (iz == 1) r += v[2]; else if constexpr (iz == -1) r -= v[2];
+        return r;
+      };
       const T fi = fin[0][i] + fin[1][i];
-      const T cu = cx * u[0] + cy * u[1] + cz * u[2];
-      const T cF = cx * F[0] + cy * F[1] + cz * F[2];
-      const T cm = cx * m[0] + cy * m[1] + cz * m[2];
-      const T S = p.guo * w * (T(3) * (cF - uF) + T(9) * cu * cF);
-      const T feq = w * rho * (T(1) + T(3) * cu + T(4.5) * cu * cu - T(1.5) * uu);
-      T fs = fi - p.omega * (fi - feq) + S;
-      fs += pamp * (w * cm * cm - w3);
-      const T rc = seg * w * (cm * inv_len);
-      fout.template put<i>((unsigned)idx, c1 * fs + rc, c2 * fs - rc, rho1, rho2);
-    });
-    fout.put_rho((unsigned)idx, rho1, rho2);
-  } else {
-    // FP32: the same operator regrouped per site,
-    //   f*_i = (1 - omega) f_i + w_i [K0 + c.u (omega rho (3 + 4.5 c.u) + 9 guo c.F) + 3 guo c.F + pamp (c.m)^2]
-    //   K0 = omega rho (1 - 1.5 u.u) - 3 guo u.F - pamp/3,
-    // so that each direction costs a short chain of multiply-adds. The rest population
-    // of each component is set to rho_k minus the others (its exact value), so per-site
-    // mass is kept to the rounding of one sum instead of drifting with the coherent
-    // rounding of K0.
-    (void)c2;
-    const T orho = p.omega * rho;
-    const T K0 = orho * (T(1) - T(1.5) * uu) - T(3) * p.guo * uF - pamp * T(1.0 / 3.0);
-    const T a3 = T(3) * orho, a45 = T(4.5) * orho, g3 = T(3) * p.guo, g9 = T(9) * p.guo;
-    const T om1 = T(1) - p.omega;
-    T s1 = T(0), s2 = T(0);
-    static_for<Q>([&](auto I) {
-      constexpr int i = decltype(I)::value;
-      if constexpr (i > 0) {
-        constexpr T w = T(Lattice<LAT>::w(i));
-        constexpr int ix = cc(i, 0), iy = cc(i, 1), iz = cc(i, 2);
-        constexpr T wl = T(Lattice<LAT>::w(i) / (speed2(i) == 1 ? 1.0 : (speed2(i) == 2 ? 1.4142135623730951
-                                                                                         : 1.7320508075688772)));
-        auto dotc = [&](const T v[3]) {
-          T r = T(0);
-          if constexpr (ix == 1) r += v[0]; else if constexpr (ix == -1) r -= v[0];
-          if constexpr (iy == 1) r += v[1]; else if constexpr (iy == -1) r -= v[1];
-          if constexpr (iz == 1) r += v[2]; else if constexpr (iz == -1) r -= v[2];
-          return r;
-        };
-        const T fi = fin[0][i] + fin[1][i];
-        const T cu = dotc(u), cF = dotc(F), cm = dotc(m);
-        const T B = K0 + cu * (a3 + a45 * cu + g9 * cF) + g3 * cF + pamp * (cm * cm);
-        const T fs = om1 * fi + w * B;
-        const T o1 = c1 * fs + seg * wl * cm;
-        const T o2 = fs - o1;
-        s1 += o1;
-        s2 += o2;
-        fout.template put<i>((unsigned)idx, o1, o2, rho1, rho2);
-      }
-    });
-    fout.template put<0>((unsigned)idx, rho1 - s1, rho2 - s2, rho1, rho2);
-    fout.put_rho((unsigned)idx, rho1, rho2);
-  }
+      const T cu = dotc(u), cF = dotc(F), cm = dotc(m);
+      const T B = K0 + cu * (a3 + a45 * cu + g9 * cF) + g3 * cF + pamp * (cm * cm);
+      const T fs = om1 * fi + w * B;
+      const T o1 = c1 * fs + seg * wl * cm;
+      const T o2 = fs - o1;
+      s1 += o1;
+      s2 += o2;
+      fout.template put<i>((unsigned)idx, o1, o2, rho1, rho2);
+    }
+  });
+  fout.template put<0>((unsigned)idx, rho1 - s1, rho2 - s2, rho1, rho2);
+  fout.put_rho((unsigned)idx, rho1, rho2);
 }
 
 // ---------------------------------------------------------------------------- moments
@@ -423,7 +479,7 @@ tiled_kernel(typename ST::Reader f, typename ST::Writer fout, const typename ST:
       red[9] = bad ? 1.0 : 0.0;
     } else {
       const T m[3] = {-n[0], -n[1], -n[2]};
-      collide_store<LAT, T>(fin, rho1, rho2, u, F, g, m, p, fout, idx);
+      collide_store<LAT, T>(fin, rho1, rho2, j, u, F, g, m, p, fout, idx);
     }
   }
 

@@ -65,6 +65,7 @@ struct StepT {
   int wall_y, wall_z;
   int N;        // nx*ny*nz (< 2^31)
   int smax;     // probe steps of the NCI ray search (0 = NCI off)
+  int edm;      // 1: exact difference method, NCI force on the dispersed phase only
   T omega;      // 1/tau
   T guo;        // 1 - omega/2 (Guo source prefactor)
   T pamp;       // 2 * (A_s/2): perturbation amplitude summed over both components

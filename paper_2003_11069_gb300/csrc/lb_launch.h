@@ -14,6 +14,7 @@ struct HostParams {
   int nx, ny, nz, wall_y, wall_z, N, smax;
   int spt;      // sites per thread of the fused D2Q9 kernel (2 or 4)
   int num_sms;  // multiprocessors of the device
+  int forcing;  // 0: Guo, 1: exact difference method on the dispersed phase
   double tau, A_s, beta, A_h, h_min, h_max, g_th, G[3];
 };
 
@@ -29,6 +30,13 @@ struct Launchers {
   // FP64 [2][Q][pitch] copies of sites [s0, s0 + count) of a state, and back.
   cudaError_t (*decode)(const void* f, double* out, int s0, int count, long long pitch, int N, cudaStream_t s);
   cudaError_t (*encode)(const double* in, void* f, int s0, int count, long long pitch, int N, cudaStream_t s);
+  // Ensembles of D2Q9 lattices: bytes of one member record, filling one on the host,
+  // tile counts per member for a tile shape, and the batched step over all members.
+  size_t batch_member_bytes;
+  void (*batch_fill)(void* dst, const HostParams& p, const void* buf0, const void* buf1);
+  int (*batch_tiles)(const HostParams& p, int spt);
+  cudaError_t (*batch_step)(const void* members, const int* tile0, int n, int total_tiles, int parity, int spt,
+                            int smax_max, cudaStream_t s);
 };
 
 const Launchers* launchers_fp64(int lattice);

@@ -47,8 +47,8 @@ struct Plain {
     }
     __device__ __forceinline__ void put_rho(unsigned, T, T) const {}
   };
-  static Reader reader(const void* base, unsigned N) { return Reader{(const T*)base, N}; }
-  static Writer writer(void* base, unsigned N) { return Writer{(T*)base, N}; }
+  __host__ __device__ static Reader reader(const void* base, unsigned N) { return Reader{(const T*)base, N}; }
+  __host__ __device__ static Writer writer(void* base, unsigned N) { return Writer{(T*)base, N}; }
 };
 
 template <int LAT>
@@ -56,7 +56,7 @@ struct HalfDev {
   using Compute = float;
   static constexpr int Q = Lattice<LAT>::Q;
   static constexpr bool kHalf = true;
-  static size_t rho_offset(size_t N) { return ((size_t)Q * N * sizeof(__half2) + 255) & ~(size_t)255; }
+  __host__ __device__ static size_t rho_offset(size_t N) { return ((size_t)Q * N * sizeof(__half2) + 255) & ~(size_t)255; }
   static size_t bytes(size_t N) { return rho_offset(N) + N * sizeof(float2); }
 
   struct Reader {
@@ -85,10 +85,10 @@ struct HalfDev {
       rho[site] = make_float2(r1, r2);
     }
   };
-  static Reader reader(const void* base, unsigned N) {
+  __host__ __device__ static Reader reader(const void* base, unsigned N) {
     return Reader{(const __half2*)base, (const float2*)((const char*)base + rho_offset(N)), N};
   }
-  static Writer writer(void* base, unsigned N) {
+  __host__ __device__ static Writer writer(void* base, unsigned N) {
     return Writer{(__half2*)base, (float2*)((char*)base + rho_offset(N)), N};
   }
 };

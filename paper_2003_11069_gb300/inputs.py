@@ -201,3 +201,36 @@ def duct_emulsion_3d(nx: int, ny: int, nz: int, seed: int, radius: float = 10.0,
     return Fields(nx, ny, nz, r1, r2, {
         "kind": "duct_emulsion_3d", "seed": seed, "droplets": len(radii),
         "volume_fraction": frac, "r_mean": float(radii.mean())})
+
+
+@dataclass
+class Member:
+    """One channel of an ensemble: its size, its physical parameters and its fields."""
+    nx: int
+    ny: int
+    force: float
+    A_h: float
+    fields: Fields
+
+
+def ensemble_channels(n: int, seed: int, nx_range=(512, 2048), ny_range=(64, 256), af_range=(0.7, 0.9),
+                      force_range=(1e-6, 1e-4), ah_range=(0.0, 0.1), r_lo: float = 12.0,
+                      r_hi: float = 16.0) -> list:
+    """n independent packed-emulsion channels for a parameter sweep: lengths and widths
+    uniform in the given ranges (lengths rounded to multiples of 32), target area
+    fractions uniform, body force log-uniform, NCI strength uniform, droplet radii as in
+    channel_emulsion_2d. The flow-rate-versus-forcing study of the paper's soft flowing
+    crystals (Results, Fig. 3) sweeps the same two controls."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for m in range(n):
+        nx = int(rng.integers(nx_range[0] // 32, nx_range[1] // 32 + 1)) * 32
+        ny = int(rng.integers(ny_range[0], ny_range[1] + 1))
+        af = float(rng.uniform(*af_range))
+        g = float(np.exp(rng.uniform(np.log(force_range[0]), np.log(force_range[1]))))
+        ah = float(rng.uniform(*ah_range))
+        fl = channel_emulsion_2d(nx, ny, seed=int(rng.integers(1 << 30)), r_lo=r_lo, r_hi=r_hi,
+                                 area_fraction=af)
+        fl.meta["target_area_fraction"] = af
+        out.append(Member(nx, ny, g, ah, fl))
+    return out

@@ -18,12 +18,15 @@ from . import build as _build
 LB_OK, LB_EINVAL, LB_ENOMEM, LB_ECUDA, LB_ENUMERIC, LB_EUNSUPPORTED = range(6)
 LB_D2Q9, LB_D3Q27 = 0, 1
 LB_FP64, LB_FP32, LB_FP16DEV = 0, 1, 2
+LB_FORCE_GUO, LB_FORCE_EDM_DISPERSED = 0, 1
 STATUS = {0: "LB_OK", 1: "LB_EINVAL", 2: "LB_ENOMEM", 3: "LB_ECUDA", 4: "LB_ENUMERIC", 5: "LB_EUNSUPPORTED"}
 
 # Every symbol include/lbnci.h declares.
 EXPORTS = ("lb_workspace_size", "lb_create", "lb_init_fields", "lb_step", "lb_observables",
            "lb_fields", "lb_get_populations", "lb_set_populations", "lb_destroy",
-           "lb_last_error", "lb_kernel_launches", "lb_observables_noalloc")
+           "lb_last_error", "lb_kernel_launches", "lb_observables_noalloc",
+           "lb_ensemble_create", "lb_ensemble_member", "lb_ensemble_step", "lb_ensemble_tune",
+           "lb_ensemble_tune_times", "lb_ensemble_launches", "lb_ensemble_last_error", "lb_ensemble_destroy")
 
 
 class lb_config(ctypes.Structure):
@@ -39,6 +42,7 @@ class lb_config(ctypes.Structure):
         ("stream", ctypes.c_void_p),
         ("workspace", ctypes.c_void_p),
         ("workspace_bytes", ctypes.c_size_t),
+        ("forcing", ctypes.c_int),
     ]
 
 
@@ -97,9 +101,22 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
     lib.lb_kernel_launches.argtypes = [simp]
     lib.lb_kernel_launches.restype = ctypes.c_longlong
     lib.lb_observables_noalloc.argtypes = [cfgp, vp, ctypes.POINTER(lb_obs)]
+    lib.lb_ensemble_create.argtypes = [cfgp, ctypes.c_int, ctypes.POINTER(ctypes.c_void_p)]
+    lib.lb_ensemble_member.argtypes = [simp, ctypes.c_int, ctypes.POINTER(ctypes.c_void_p)]
+    lib.lb_ensemble_step.argtypes = [simp, ctypes.c_longlong]
+    lib.lb_ensemble_tune.argtypes = [simp, ctypes.POINTER(ctypes.c_int)]
+    lib.lb_ensemble_tune_times.argtypes = [simp, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_float)]
+    lib.lb_ensemble_launches.argtypes = [simp]
+    lib.lb_ensemble_launches.restype = ctypes.c_longlong
+    lib.lb_ensemble_last_error.argtypes = [simp]
+    lib.lb_ensemble_last_error.restype = ctypes.c_char_p
+    lib.lb_ensemble_destroy.argtypes = [simp]
+    lib.lb_ensemble_destroy.restype = None
     for name in EXPORTS:
         fn = getattr(lib, name)
-        if fn.restype is ctypes.c_int or name not in ("lb_destroy", "lb_last_error", "lb_kernel_launches"):
+        if fn.restype is ctypes.c_int or name not in ("lb_destroy", "lb_last_error", "lb_kernel_launches",
+                                                      "lb_ensemble_launches", "lb_ensemble_last_error",
+                                                      "lb_ensemble_destroy"):
             fn.restype = ctypes.c_int
     _lib = lib
     return lib
@@ -145,7 +162,8 @@ def _check(st: int, sim=None) -> int:
 
 def lb_config_make(lattice=LB_D2Q9, nx=64, ny=64, nz=1, wall_y=0, wall_z=0, tau=1.0, A_s=0.0,
                    beta=0.0, A_h=0.0, h_min=2.0, h_max=4.0, g_th=0.05, force=(0.0, 0.0, 0.0),
-                   precision=LB_FP64, stream=None, workspace=None, workspace_bytes=0) -> lb_config:
+                   precision=LB_FP64, stream=None, workspace=None, workspace_bytes=0,
+                   forcing=LB_FORCE_GUO) -> lb_config:
     c = lb_config()
     c.lattice, c.nx, c.ny, c.nz, c.wall_y, c.wall_z = lattice, nx, ny, nz, wall_y, wall_z
     c.tau, c.A_s, c.beta, c.A_h, c.h_min, c.h_max, c.g_th = tau, A_s, beta, A_h, h_min, h_max, g_th
@@ -155,6 +173,7 @@ def lb_config_make(lattice=LB_D2Q9, nx=64, ny=64, nz=1, wall_y=0, wall_z=0, tau=
     c.stream = stream
     c.workspace = workspace
     c.workspace_bytes = workspace_bytes
+    c.forcing = forcing
     return c
 
 
@@ -306,3 +325,73 @@ class Sim:
 
     def launches(self) -> int:
         return lb_kernel_launches(self.h)
+
+
+def _echeck(st: int, ens=None) -> int:
+    if st != LB_OK:
+        msg = load().lb_ensemble_last_error(ens)
+        raise LBError(st, msg.decode() if msg else "")
+    return st
+
+
+class Ensemble:
+    """Owning wrapper of lb_ensemble_*: members are Sim-like views (no ownership)."""
+
+    def __init__(self, cfgs):
+        arr = (lb_config * len(cfgs))(*cfgs)
+        h = ctypes.c_void_p()
+        _echeck(load().lb_ensemble_create(arr, len(cfgs), ctypes.byref(h)))
+        self.h = h
+        self.cfgs = list(cfgs)
+        self.members = []
+        for m, c in enumerate(cfgs):
+            sh = ctypes.c_void_p()
+            _echeck(load().lb_ensemble_member(self.h, m, ctypes.byref(sh)), self.h)
+            self.members.append(_MemberView(sh, c))
+
+    def step(self, n=1):
+        _echeck(load().lb_ensemble_step(self.h, int(n)), self.h)
+
+    def tune(self) -> int:
+        v = ctypes.c_int(0)
+        _echeck(load().lb_ensemble_tune(self.h, ctypes.byref(v)), self.h)
+        return v.value
+
+    def tune_times(self):
+        a, b = ctypes.c_float(0), ctypes.c_float(0)
+        _echeck(load().lb_ensemble_tune_times(self.h, ctypes.byref(a), ctypes.byref(b)), self.h)
+        return a.value, b.value
+
+    def launches(self) -> int:
+        return int(load().lb_ensemble_launches(self.h))
+
+    def close(self):
+        if self.h:
+            load().lb_ensemble_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+
+class _MemberView(Sim):
+    """An ensemble member: a Sim whose handle belongs to the ensemble."""
+
+    def __init__(self, h, cfg):  # noqa: D401 - no lb_create here
+        self._ws = None
+        self.cfg = cfg
+        self.h = h
+        self.Q = 9 if cfg.lattice == LB_D2Q9 else 27
+        self.N = cfg.nx * cfg.ny * cfg.nz
+
+    def close(self):
+        self.h = None  # the ensemble releases it

@@ -34,6 +34,7 @@ def test_struct_layouts_match_header():
     assert lbnci.lb_config.precision.offset == 24 + 10 * 8
     assert lbnci.lb_config.stream.offset == 24 + 10 * 8 + 8
     assert ctypes.sizeof(lbnci.lb_obs) == 7 * 8 + 4 * 8
+    assert lbnci.lb_config.forcing.offset == lbnci.lb_config.workspace_bytes.offset + 8
 
 
 @pytest.mark.parametrize("bad,status", [
@@ -50,6 +51,7 @@ def test_struct_layouts_match_header():
     (dict(force=(float("inf"), 0, 0)), lbnci.LB_EINVAL),
     (dict(precision=9), lbnci.LB_EUNSUPPORTED),
     (dict(precision=3), lbnci.LB_EUNSUPPORTED),
+    (dict(forcing=2), lbnci.LB_EINVAL),
 ])
 def test_config_validation(bad, status):
     with pytest.raises(lbnci.LBError) as ei:

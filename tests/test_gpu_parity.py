@@ -25,7 +25,7 @@ def _cfg(p, precision=lbnci.LB_FP64):
     return lbnci.lb_config_make(
         lattice=p.lattice, nx=p.nx, ny=p.ny, nz=p.nz, wall_y=p.wall_y, wall_z=p.wall_z,
         tau=p.tau, A_s=p.A_s, beta=p.beta, A_h=p.A_h, h_min=p.h_min, h_max=p.h_max, g_th=p.g_th,
-        force=tuple(p.force), precision=precision)
+        force=tuple(p.force), precision=precision, forcing=p.forcing)
 
 
 def _scale(p, f):
@@ -283,3 +283,42 @@ def test_fp32_ragged_and_tiny(nx, ny, walls):
     assert ok.mean() > 0.9
     rel = (np.abs(got - ref) / _scale(p, ref)).reshape(2 * Q, N)
     assert rel[:, ok].max() <= FP32_TOL, rel[:, ok].max()
+
+
+@pytest.mark.parametrize("lat", [oracle.D2Q9, oracle.D3Q27])
+def test_fp64_edm_dispersed_parity(lat):
+    """The paper's forcing (exact difference method, NCI on the dispersed phase only):
+    FP64 per-step parity with the oracle, NCI active."""
+    if lat == oracle.D2Q9:
+        p = oracle.make_params(lattice=lat, nx=96, ny=48, wall_y=1, tau=0.9, A_s=0.01, beta=0.7, A_h=0.05,
+                               force=(1e-5, 2e-6, 0), forcing=1)
+        fl = inputs.channel_emulsion_2d(96, 48, seed=5, r_lo=8, r_hi=10)
+        steps = [1, 10, 100]
+    else:
+        p = oracle.make_params(lattice=lat, nx=40, ny=22, nz=17, wall_y=1, wall_z=1, tau=0.9, A_s=0.01,
+                               beta=0.7, A_h=0.03, force=(2e-6, 0, 1e-6), forcing=1)
+        fl = _duct_fields(40, 22, 17, seed=11)
+        steps = [1, 10]
+    out, fields = _run_pair(p, fl.rho1, fl.rho2, steps)
+    for n, got, ref in out:
+        err = _max_rel(p, got, ref)
+        assert err <= FP64_RTOL, f"step {n}: max rel err {err:.3e}"
+    of = oracle.fields(p, out[-1][2])
+    assert np.array_equal(fields["hit"], of["hit"]) and (of["hit"] > 0).sum() > 0
+
+
+def test_fp32_edm_one_step():
+    p = oracle.make_params(lattice=oracle.D2Q9, nx=96, ny=48, wall_y=1, tau=0.9, A_s=0.01, beta=0.7, A_h=0.05,
+                           force=(1e-5, 0, 0), forcing=1)
+    fl = inputs.channel_emulsion_2d(96, 48, seed=5, r_lo=8, r_hi=10)
+    f0 = oracle.step(p, oracle.init(p, fl.rho1, fl.rho2), 20).astype(np.float32).astype(np.float64)
+    with lbnci.Sim(_cfg(p, lbnci.LB_FP32)) as sim:
+        sim.set_populations(f0)
+        fields = sim.fields()
+        sim.step(1)
+        got = sim.get_populations()
+    ref = oracle.step(p, f0, 1)
+    of = oracle.fields(p, f0)
+    ok = fields["hit"] == of["hit"]
+    rel = (np.abs(got - ref) / _scale(p, ref)).reshape(18, 96 * 48)
+    assert ok.mean() > 0.99 and rel[:, ok].max() <= FP32_TOL

@@ -416,3 +416,56 @@ def test_nci_films_far_and_near():
         assert abs(fy[yy] + fy[mirror]) < 1e-15
     # the force on the lower film's upper face points down (away from the other film)
     assert fy[27:31].min() < 0 and fy[27:31].max() <= 0.0
+
+
+# --------------------------------------------------------------------------- EDM forcing
+@pytest.mark.parametrize("lat", [oracle.D2Q9, oracle.D3Q27])
+def test_edm_site_invariants(lat):
+    """Exact difference method (the paper's insertion of the near-contact force): each
+    component's mass is kept, the mixture gains exactly F = G + F_rep of momentum, and the
+    continuous phase (component 2) is untouched by F_rep: it feels only its mass share
+    of the body force."""
+    rng = np.random.default_rng(5)
+    c, w, _ = oracle.lattice(lat)
+    Q = len(w)
+    D = 2 if lat == oracle.D2Q9 else 3
+    cf = c[:, :D].astype(float)
+    fin = rng.uniform(0.02, 0.1, size=2 * Q) * np.concatenate([w, w]) * 9
+    grad = np.zeros(3)
+    grad[:D] = rng.normal(size=D) * 0.3
+    G = np.zeros(3)
+    G[:D] = rng.normal(size=D) * 1e-4
+    Frep = np.zeros(3)
+    Frep[:D] = rng.normal(size=D) * 1e-3
+    p = oracle.make_params(lattice=lat, nx=1, ny=1, nz=1, tau=0.8, A_s=0.01, beta=0.7, force=tuple(G), forcing=1)
+    out = oracle.collide_site(p, fin, grad, G + Frep)
+    r1, r2 = fin[:Q].sum(), fin[Q:].sum()
+    assert abs(out[:Q].sum() - r1) < 1e-14 and abs(out[Q:].sum() - r2) < 1e-14
+    j_in = cf.T @ (fin[:Q] + fin[Q:])
+    assert np.allclose(cf.T @ (out[:Q] + out[Q:]) - j_in, (G + Frep)[:D], atol=1e-16 * 50)
+    # component 2 does not see F_rep
+    out0 = oracle.collide_site(p, fin, grad, G)
+    assert np.allclose(out[Q:], out0[Q:], atol=1e-16 * 10)
+    assert not np.allclose(out[:Q], out0[:Q], atol=1e-9)
+    # the added populations are f_eq(rho_k, u + dU_k) - f_eq(rho_k, u): zero without force
+    pz = oracle.make_params(lattice=lat, nx=1, ny=1, nz=1, tau=0.8, A_s=0.01, beta=0.7, forcing=1)
+    pg = oracle.make_params(lattice=lat, nx=1, ny=1, nz=1, tau=0.8, A_s=0.01, beta=0.7, forcing=0)
+    assert np.allclose(oracle.collide_site(pz, fin, grad, np.zeros(3))[Q:],
+                       oracle.collide_site(pg, fin, grad, np.zeros(3))[Q:], atol=1e-16)
+
+
+def test_edm_poiseuille_second_order():
+    """Single-phase channel driven by G with the exact difference method: the parabolic
+    profile is reached with second-order convergence in H."""
+    errs = []
+    for H in (8, 16):
+        tau = 1.0
+        p = oracle.make_params(nx=2, ny=H, wall_y=1, tau=tau, force=(1e-6, 0, 0), forcing=1)
+        fl = inputs.uniform(2, H, 1, psi0=-1.0)
+        f = oracle.step(p, oracle.init(p, fl.rho1, fl.rho2), int(12 * H * H / ((tau - 0.5) / 3)))
+        u = oracle.fields(p, f)["u"][0].reshape(H, 2)[:, 0]
+        nu = (tau - 0.5) / 3
+        y = np.arange(H)
+        ua = 1e-6 / (2 * nu) * (y + 0.5) * (H - 0.5 - y)
+        errs.append(np.sqrt(((u - ua) ** 2).sum() / (ua ** 2).sum()))
+    assert errs[1] < 2e-3 and 3.5 < errs[0] / errs[1] < 4.5, errs
