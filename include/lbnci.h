@@ -165,7 +165,7 @@ long long lb_kernel_launches(const lb_sim* sim);
  * Ensembles: n independent D2Q9 lattices of different sizes and parameters (each a
  * full lb_config: size, walls, tau, A_s, beta, A_h, h_min, h_max, g_th, force) stepped
  * together, one batched kernel launch per step for all members, replayed from a CUDA
- * graph. This serves the paper's parameter studies (flow rate against the driving
+ * graph. All members share the precision and the forcing scheme. This serves the paper's parameter studies (flow rate against the driving
  * force and the near-contact strength, "Results": Figs. 2-3) as one job. All members
  * must share the precision. The work runs on cfgs[0].stream, or on a stream of the
  * ensemble's own when that is NULL (graph capture needs a non-default stream).

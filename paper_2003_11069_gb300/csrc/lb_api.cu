@@ -146,6 +146,9 @@ lb_status validate(const lb_config* c, HostParams* p, Layout* lay, long long* nb
   p->smax = smax;
   p->forcing = c->forcing;
   p->num_sms = 1;
+  // D3Q27 collision kernel: LBNCI_D3_KERNEL=march (z-marching, default) or tiled.
+  p->d3_kernel = 0;
+  if (const char* e = std::getenv("LBNCI_D3_KERNEL")) p->d3_kernel = std::strcmp(e, "tiled") == 0 ? 1 : 0;
   // Tile of the fused D2Q9 kernel: LBNCI_FUSED_SPT=2 (32x16, the default) or 4 (32x32).
   p->spt = 2;
   if (const char* e = std::getenv("LBNCI_FUSED_SPT")) p->spt = std::atoi(e) == 4 ? 4 : 2;
@@ -219,6 +222,9 @@ lb_status lb_create(const lb_config* cfg, lb_sim** out) {
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return fail(nullptr, LB_ECUDA, "no CUDA device: %s", cudaGetErrorString(e));
   const Launchers* L = launchers_for(cfg);
+  int nsm = 0;
+  if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && nsm > 0) p.num_sms = nsm;
+  cudaGetLastError();
   lb_sim* s = new (std::nothrow) lb_sim();
   if (!s) return fail(nullptr, LB_ENOMEM, "host allocation failed");
   s->cfg = *cfg;
@@ -606,7 +612,8 @@ lb_status ens_layout(lb_ensemble* e) {
 }
 
 cudaError_t ens_launch(lb_ensemble* e, int parity) {
-  return e->L->batch_step(e->d_members, e->d_tile0, e->n, e->total_tiles, parity, e->spt, e->smax_max, e->stream);
+  return e->L->batch_step(e->d_members, e->d_tile0, e->n, e->total_tiles, parity, e->spt, e->smax_max,
+                          e->members[0]->p.forcing == LB_FORCE_EDM_DISPERSED, e->stream);
 }
 
 }  // namespace
@@ -621,6 +628,8 @@ lb_status lb_ensemble_create(const lb_config* cfgs, int n, lb_ensemble** out) {
     if (cfgs[m].lattice != LB_D2Q9) return efail(nullptr, LB_EUNSUPPORTED, "ensembles are D2Q9 only (member %d)", m);
     if (cfgs[m].precision != cfgs[0].precision)
       return efail(nullptr, LB_EINVAL, "all members need the same precision (member %d)", m);
+    if (cfgs[m].forcing != cfgs[0].forcing)
+      return efail(nullptr, LB_EINVAL, "all members need the same forcing scheme (member %d)", m);
   }
   std::vector<size_t> ws(n);
   size_t total = 0;

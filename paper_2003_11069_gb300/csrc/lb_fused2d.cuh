@@ -34,7 +34,7 @@ constexpr int fused2d_min_blocks() {
 }
 
 // One 32 x (8*SPT) tile with origin (x0, y0) of a lattice; the whole block calls it.
-template <typename ST, int SPT>
+template <typename ST, int SPT, bool EDM>
 __device__ __forceinline__ void fused2d_tile(const typename ST::Reader& f, const typename ST::Writer& fout,
                                              const StepT<typename ST::Compute>& p, int x0, int y0,
                                              unsigned char* smem_raw) {
@@ -155,15 +155,15 @@ __device__ __forceinline__ void fused2d_tile(const typename ST::Reader& f, const
 #pragma unroll
     for (int a = 0; a < 3; ++a) u[a] = M<T>::div(j[a] + T(0.5) * F[a], rho);
     const T m[3] = {-n0, -n1, T(0)};
-    collide_store<0, T>(fin[s], rho1, rho2, j, u, F, g, m, p, fout, idx);
+    collide_store<0, T, typename ST::Writer, EDM>(fin[s], rho1, rho2, j, u, F, g, m, p, fout, idx);
   }
 }
 
-template <typename ST, int SPT>
+template <typename ST, int SPT, bool EDM>
 __global__ void __launch_bounds__(256, (fused2d_min_blocks<ST, SPT>()))
 fused2d_kernel(typename ST::Reader f, typename ST::Writer fout, StepT<typename ST::Compute> p) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  fused2d_tile<ST, SPT>(f, fout, p, blockIdx.x * kFusedTX, blockIdx.y * (kFusedThreadsY * SPT), smem_raw);
+  fused2d_tile<ST, SPT, EDM>(f, fout, p, blockIdx.x * kFusedTX, blockIdx.y * (kFusedThreadsY * SPT), smem_raw);
 }
 
 // One lattice of an ensemble: its step parameters, its two state buffers and the
@@ -178,7 +178,7 @@ struct BatchMember {
 // The D2Q9 step of every member of an ensemble in one launch: block b finds its member
 // by binary search over the tile offsets, then steps one tile of it with the member's
 // own parameters, reading buf[parity] and writing buf[1 - parity].
-template <typename ST, int SPT>
+template <typename ST, int SPT, bool EDM>
 __global__ void __launch_bounds__(256, (fused2d_min_blocks<ST, SPT>()))
 fused2d_batch_kernel(const BatchMember<typename ST::Compute>* __restrict__ members, const int* __restrict__ tile0,
                      int nmembers, int parity) {
@@ -195,7 +195,7 @@ fused2d_batch_kernel(const BatchMember<typename ST::Compute>* __restrict__ membe
   const int t = b - tile0[lo];
   const int by = t / mb.ntx, bx = t - by * mb.ntx;
   const unsigned N = (unsigned)p.N;
-  fused2d_tile<ST, SPT>(ST::reader(mb.buf[parity], N), ST::writer(const_cast<void*>(mb.buf[1 - parity]), N), p,
+  fused2d_tile<ST, SPT, EDM>(ST::reader(mb.buf[parity], N), ST::writer(const_cast<void*>(mb.buf[1 - parity]), N), p,
                         bx * kFusedTX, by * (kFusedThreadsY * SPT), smem_raw);
 }
 

@@ -3,6 +3,7 @@
 #pragma once
 
 #include "lb_fused2d.cuh"
+#include "lb_march3d.cuh"
 #include "lb_kernels.cuh"
 #include "lb_launch.h"
 
@@ -53,17 +54,29 @@ cudaError_t allow_smem(K kernel, size_t bytes, size_t* configured) {
 }
 
 // Sites per thread of the fused D2Q9 kernel (2: 32x16 tiles, 4: 32x32 tiles).
-template <typename ST, int SPT>
-cudaError_t launch_fused2d(const void* fa, void* fb, const StepT<typename ST::Compute>& p, cudaStream_t s) {
+// FP32 kernels come in a Guo and an EDM build; FP64 has one (it checks p.edm itself).
+template <typename ST>
+constexpr bool edm_build_exists() { return !std::is_same<typename ST::Compute, double>::value; }
+
+template <typename ST, int SPT, bool EDM>
+cudaError_t launch_fused2d_v(const void* fa, void* fb, const StepT<typename ST::Compute>& p, cudaStream_t s) {
   using T = typename ST::Compute;
   static size_t configured = 0;
   const size_t sm = fused2d_smem_bytes<T>(p.smax, SPT);
-  cudaError_t e = allow_smem(fused2d_kernel<ST, SPT>, sm, &configured);
+  cudaError_t e = allow_smem(fused2d_kernel<ST, SPT, EDM>, sm, &configured);
   if (e != cudaSuccess) return e;
   const dim3 grid((p.nx + kFusedTX - 1) / kFusedTX, (p.ny + kFusedThreadsY * SPT - 1) / (kFusedThreadsY * SPT), 1);
-  fused2d_kernel<ST, SPT><<<grid, dim3(kFusedTX, kFusedThreadsY, 1), sm, s>>>(
+  fused2d_kernel<ST, SPT, EDM><<<grid, dim3(kFusedTX, kFusedThreadsY, 1), sm, s>>>(
       ST::reader(fa, (unsigned)p.N), ST::writer(fb, (unsigned)p.N), p);
   return cudaGetLastError();
+}
+
+template <typename ST, int SPT>
+cudaError_t launch_fused2d(const void* fa, void* fb, const StepT<typename ST::Compute>& p, cudaStream_t s) {
+  if constexpr (edm_build_exists<ST>()) {
+    if (p.edm) return launch_fused2d_v<ST, SPT, true>(fa, fb, p, s);
+  }
+  return launch_fused2d_v<ST, SPT, false>(fa, fb, p, s);
 }
 
 template <int LAT, typename ST>
@@ -74,33 +87,74 @@ cudaError_t l_init(void* f, const double* r1, const double* r2, const double* u,
   return cudaGetLastError();
 }
 
-template <int LAT, typename ST, bool FIELDS>
-cudaError_t launch_tiled(const void* f, void* fout, const void* psi, const HostParams& h,
-                         const StepT<typename ST::Compute>& p, const FieldOut& fo, cudaStream_t s) {
+template <int LAT, typename ST, bool FIELDS, bool EDM = false>
+cudaError_t launch_tiled_v(const void* f, void* fout, const void* psi, const HostParams& h,
+                           const StepT<typename ST::Compute>& p, const FieldOut& fo, cudaStream_t s) {
   using T = typename ST::Compute;
   static size_t configured = 0;
   const size_t sm = tiled_smem_bytes<LAT, T>(p.smax);
-  cudaError_t e = allow_smem(tiled_kernel<LAT, ST, FIELDS>, sm, &configured);
+  cudaError_t e = allow_smem(tiled_kernel<LAT, ST, FIELDS, EDM>, sm, &configured);
   if (e != cudaSuccess) return e;
   typename ST::Writer w = FIELDS ? typename ST::Writer{} : ST::writer(fout, (unsigned)p.N);
-  tiled_kernel<LAT, ST, FIELDS><<<tiled_grid<LAT>(h), tiled_block<LAT>(), sm, s>>>(
+  tiled_kernel<LAT, ST, FIELDS, EDM><<<tiled_grid<LAT>(h), tiled_block<LAT>(), sm, s>>>(
       ST::reader(f, (unsigned)p.N), w, (const T*)psi, p, fo);
   return cudaGetLastError();
+}
+
+template <int LAT, typename ST, bool FIELDS>
+cudaError_t launch_tiled(const void* f, void* fout, const void* psi, const HostParams& h,
+                         const StepT<typename ST::Compute>& p, const FieldOut& fo, cudaStream_t s) {
+  if constexpr (!FIELDS && edm_build_exists<ST>()) {
+    if (p.edm) return launch_tiled_v<LAT, ST, false, true>(f, fout, psi, h, p, fo, s);
+  }
+  return launch_tiled_v<LAT, ST, FIELDS, false>(f, fout, psi, h, p, fo, s);
+}
+
+// D3Q27 collision marching along z (after moments_kernel has written psi).
+template <typename ST, bool EDM>
+cudaError_t launch_march3d_v(const void* fa, void* fb, const void* psi, const HostParams& h,
+                             const StepT<typename ST::Compute>& p, cudaStream_t s) {
+  using T = typename ST::Compute;
+  static size_t configured = 0;
+  const size_t sm = march3d_smem_bytes<T>(p.smax);
+  cudaError_t e = allow_smem(march3d_kernel<ST, EDM>, sm, &configured);
+  if (e != cudaSuccess) return e;
+  const int bx = (p.nx + kMarchTX - 1) / kMarchTX, by = (p.ny + kMarchTY - 1) / kMarchTY;
+  const int per_sm = sizeof(T) == 4 ? 2 : 1;
+  // enough z segments to give every SM its resident blocks, one plane at least each
+  int nseg = (h.num_sms * per_sm + bx * by - 1) / (bx * by);
+  nseg = nseg < 1 ? 1 : (nseg > p.nz ? p.nz : nseg);
+  const int seg_len = (p.nz + nseg - 1) / nseg;
+  nseg = (p.nz + seg_len - 1) / seg_len;
+  march3d_kernel<ST, EDM><<<dim3(bx, by, nseg), dim3(kMarchTX, kMarchTY, 1), sm, s>>>(
+      ST::reader(fa, (unsigned)p.N), ST::writer(fb, (unsigned)p.N), (const T*)psi, p, seg_len);
+  return cudaGetLastError();
+}
+
+template <typename ST>
+cudaError_t launch_march3d(const void* fa, void* fb, const void* psi, const HostParams& h,
+                           const StepT<typename ST::Compute>& p, cudaStream_t s) {
+  if constexpr (edm_build_exists<ST>()) {
+    if (p.edm) return launch_march3d_v<ST, true>(fa, fb, psi, h, p, s);
+  }
+  return launch_march3d_v<ST, false>(fa, fb, psi, h, p, s);
 }
 
 template <int LAT, typename ST>
 cudaError_t l_step(const void* fa, void* fb, void* psi, const HostParams& h, cudaStream_t s, int* nk) {
   using T = typename ST::Compute;
   const StepT<T> p = convert<T>(h);
-  if (LAT == 0) {
+  if constexpr (LAT == 0) {
     *nk = 1;
     return h.spt == 4 ? launch_fused2d<ST, 4>(fa, fb, p, s) : launch_fused2d<ST, 2>(fa, fb, p, s);
+  } else {
+    moments_kernel<LAT, ST><<<blocks_for(p.N, 256), 256, 0, s>>>(ST::reader(fa, (unsigned)p.N), (T*)psi, p);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    *nk = 2;
+    if (h.d3_kernel == 1) return launch_tiled<LAT, ST, false>(fa, fb, psi, h, p, FieldOut{}, s);
+    return launch_march3d<ST>(fa, fb, psi, h, p, s);
   }
-  moments_kernel<LAT, ST><<<blocks_for(p.N, 256), 256, 0, s>>>(ST::reader(fa, (unsigned)p.N), (T*)psi, p);
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
-  *nk = 2;
-  return launch_tiled<LAT, ST, false>(fa, fb, psi, h, p, FieldOut{}, s);
 }
 
 template <int LAT, typename ST>
@@ -143,24 +197,37 @@ int l_batch_tiles(const HostParams& h, int spt) {
   return ((h.nx + kFusedTX - 1) / kFusedTX) * ((h.ny + ty - 1) / ty);
 }
 
-template <typename ST, int SPT>
-cudaError_t launch_batch(const void* members, const int* tile0, int n, int total_tiles, int parity, int smax_max,
-                         cudaStream_t s) {
+template <typename ST, int SPT, bool EDM>
+cudaError_t launch_batch_v(const void* members, const int* tile0, int n, int total_tiles, int parity,
+                           int smax_max, cudaStream_t s) {
   static size_t configured = 0;
   const size_t sm = fused2d_smem_bytes<typename ST::Compute>(smax_max, SPT);
-  cudaError_t e = allow_smem(fused2d_batch_kernel<ST, SPT>, sm, &configured);
+  cudaError_t e = allow_smem(fused2d_batch_kernel<ST, SPT, EDM>, sm, &configured);
   if (e != cudaSuccess) return e;
-  fused2d_batch_kernel<ST, SPT><<<total_tiles, dim3(kFusedTX, kFusedThreadsY, 1), sm, s>>>(
+  fused2d_batch_kernel<ST, SPT, EDM><<<total_tiles, dim3(kFusedTX, kFusedThreadsY, 1), sm, s>>>(
       (const BatchMember<typename ST::Compute>*)members, tile0, n, parity);
   return cudaGetLastError();
 }
 
+// All members of an ensemble share the forcing scheme (checked at creation).
+template <typename ST, int SPT>
+cudaError_t launch_batch(const void* members, const int* tile0, int n, int total_tiles, int parity, int smax_max,
+                         int edm, cudaStream_t s) {
+  if constexpr (edm_build_exists<ST>()) {
+    if (edm) return launch_batch_v<ST, SPT, true>(members, tile0, n, total_tiles, parity, smax_max, s);
+  }
+  return launch_batch_v<ST, SPT, false>(members, tile0, n, total_tiles, parity, smax_max, s);
+}
+
 template <int LAT, typename ST>
 cudaError_t l_batch_step(const void* members, const int* tile0, int n, int total_tiles, int parity, int spt,
-                         int smax_max, cudaStream_t s) {
-  if (LAT != 0) return cudaErrorNotSupported;
-  return spt == 4 ? launch_batch<ST, 4>(members, tile0, n, total_tiles, parity, smax_max, s)
-                  : launch_batch<ST, 2>(members, tile0, n, total_tiles, parity, smax_max, s);
+                         int smax_max, int edm, cudaStream_t s) {
+  if constexpr (LAT != 0) {
+    return cudaErrorNotSupported;
+  } else {
+    return spt == 4 ? launch_batch<ST, 4>(members, tile0, n, total_tiles, parity, smax_max, edm, s)
+                    : launch_batch<ST, 2>(members, tile0, n, total_tiles, parity, smax_max, edm, s);
+  }
 }
 
 template <int LAT, typename ST>

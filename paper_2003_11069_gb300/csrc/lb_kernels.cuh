@@ -202,10 +202,6 @@ __device__ __forceinline__ void momentum(const T fin[2][Lattice<LAT>::Q], T j[3]
   });
 }
 
-// BGK relaxation towards f_eq(rho, u) with the Guo source, plus the perturbation
-// (A_s/2)|grad psi| [w_i (c_i.m)^2 - w_i/3] of each component, on the total
-// population; then recolouring f^1 = (rho1/rho) f* + beta rho1 rho2/rho w_i cos(theta_i),
-// f^2 = (rho2/rho) f* - same, cos(theta_i) = c_i.m/|c_i|. m = grad psi/|grad psi|.
 // f_eq of the second-order lattice BGK model, c_s^2 = 1/3, for direction i.
 template <int LAT, int I, typename T>
 __device__ __forceinline__ T feq_dir(T rho, const T v[3]) {
@@ -283,12 +279,15 @@ __device__ __forceinline__ void collide_exact(const T fin[2][Lattice<LAT>::Q], T
 // (A_s/2)|grad psi| [w_i (c_i.m)^2 - w_i/3] of each component, on the total
 // population; then recolouring f^1 = (rho1/rho) f* + beta rho1 rho2/rho w_i cos(theta_i),
 // f^2 = (rho2/rho) f* - same, cos(theta_i) = c_i.m/|c_i|. m = grad psi/|grad psi|.
-template <int LAT, typename T, typename WR>
+// EDM: the kernel variant built for the exact-difference-method forcing. FP64 always
+// takes the term-by-term path (which checks p.edm itself); FP32 kernels are built twice,
+// so the common Guo path keeps its register budget.
+template <int LAT, typename T, typename WR, bool EDM = false>
 __device__ __forceinline__ void collide_store(const T fin[2][Lattice<LAT>::Q], T rho1, T rho2, const T j[3],
                                               const T u[3], const T F[3], T g, const T m[3], const StepT<T>& p,
                                               const WR& fout, int idx) {
   constexpr int Q = Lattice<LAT>::Q;
-  if (std::is_same<T, double>::value || p.edm) {
+  if constexpr (std::is_same<T, double>::value || EDM) {
     collide_exact<LAT, T, WR>(fin, rho1, rho2, j, u, F, g, m, p, fout, idx);
     return;
   }
@@ -368,7 +367,7 @@ size_t tiled_smem_bytes(int smax) {
 
 // Gradient, NCI and collision from a psi array: the psi tile and its halo of radius
 // smax+1 are staged in shared memory; probes recompute the gradient there.
-template <int LAT, typename ST, bool FIELDS>
+template <int LAT, typename ST, bool FIELDS, bool EDM = false>
 __global__ void __launch_bounds__(256)
 tiled_kernel(typename ST::Reader f, typename ST::Writer fout, const typename ST::Compute* __restrict__ psi,
              StepT<typename ST::Compute> p, FieldOut fo) {
@@ -479,7 +478,7 @@ tiled_kernel(typename ST::Reader f, typename ST::Writer fout, const typename ST:
       red[9] = bad ? 1.0 : 0.0;
     } else {
       const T m[3] = {-n[0], -n[1], -n[2]};
-      collide_store<LAT, T>(fin, rho1, rho2, j, u, F, g, m, p, fout, idx);
+      collide_store<LAT, T, typename ST::Writer, EDM>(fin, rho1, rho2, j, u, F, g, m, p, fout, idx);
     }
   }
 

@@ -15,6 +15,7 @@ struct HostParams {
   int spt;      // sites per thread of the fused D2Q9 kernel (2 or 4)
   int num_sms;  // multiprocessors of the device
   int forcing;  // 0: Guo, 1: exact difference method on the dispersed phase
+  int d3_kernel;  // D3Q27 collision: 0 marching along z (default), 1 tiled
   double tau, A_s, beta, A_h, h_min, h_max, g_th, G[3];
 };
 
@@ -36,7 +37,7 @@ struct Launchers {
   void (*batch_fill)(void* dst, const HostParams& p, const void* buf0, const void* buf1);
   int (*batch_tiles)(const HostParams& p, int spt);
   cudaError_t (*batch_step)(const void* members, const int* tile0, int n, int total_tiles, int parity, int spt,
-                            int smax_max, cudaStream_t s);
+                            int smax_max, int edm, cudaStream_t s);
 };
 
 const Launchers* launchers_fp64(int lattice);

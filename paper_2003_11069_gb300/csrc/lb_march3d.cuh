@@ -1,0 +1,161 @@
+// lb_march3d.cuh -- the collision half of the D3Q27 step, marching along z.
+//
+// A block owns a 32 x 8 column of sites and walks it through a z segment. Shared memory
+// holds two rings of planes:
+//   psi ring     3 planes of psi on the column plus a halo of smax + 1 (from the psi
+//                array written by moments_kernel; the plane beyond a z wall holds the
+//                mirror of the wall plane);
+//   (n, g) ring  2 smax + 1 planes of the unit normal n = -grad psi/|grad psi| and
+//                |grad psi| on the column plus a halo of smax, each computed once.
+// Iteration q loads psi plane q, computes (n, g) of plane q - 1, and collides plane
+// q - smax - 1, whose NCI rays find every probe's (n, g) in the ring. The psi array is
+// read about three times per site instead of once per halo cell of a 3-D tile, and no
+// gradient is recomputed along a ray. Arithmetic is that of the other step kernels
+// (same helpers and expression order), so FP64 rounds like the oracle.
+#pragma once
+
+#include "lb_kernels.cuh"
+
+namespace lbnci {
+
+constexpr int kMarchTX = 32, kMarchTY = 8;
+
+template <typename T>
+size_t march3d_smem_bytes(int smax) {
+  const int R = smax + 1;
+  const size_t psi = 3 * (size_t)(kMarchTX + 2 * R) * (kMarchTY + 2 * R);
+  const size_t ng = (size_t)(2 * smax + 1) * 4 * (kMarchTX + 2 * smax) * (kMarchTY + 2 * smax);
+  return sizeof(T) * (psi + ng);
+}
+
+// Isotropic D3Q27 gradient of the cell c of a psi plane, with the planes below and
+// above it in separate buffers (same direction order as grad_smem).
+template <typename T>
+__device__ __forceinline__ void grad_ring(const T* __restrict__ pm, const T* __restrict__ p0,
+                                          const T* __restrict__ pp, int RX, int c, T g[3]) {
+  g[0] = T(0); g[1] = T(0); g[2] = T(0);
+  static_for<27>([&](auto I) {
+    constexpr int i = decltype(I)::value;
+    if constexpr (i > 0) {
+      constexpr T wx = T(Lattice<1>::w(i) * cc(i, 0));
+      constexpr T wy = T(Lattice<1>::w(i) * cc(i, 1));
+      constexpr T wz = T(Lattice<1>::w(i) * cc(i, 2));
+      const T* pl = cc(i, 2) < 0 ? pm : (cc(i, 2) > 0 ? pp : p0);
+      const T v = pl[c + cc(i, 0) + RX * cc(i, 1)];
+      if constexpr (cc(i, 0) != 0) g[0] += wx * v;
+      if constexpr (cc(i, 1) != 0) g[1] += wy * v;
+      if constexpr (cc(i, 2) != 0) g[2] += wz * v;
+    }
+  });
+  g[0] = T(3) * g[0];
+  g[1] = T(3) * g[1];
+  g[2] = T(3) * g[2];
+}
+
+template <typename ST, bool EDM>
+__global__ void __launch_bounds__(kMarchTX * kMarchTY, (sizeof(typename ST::Compute) == 4 ? 2 : 1))
+march3d_kernel(typename ST::Reader f, typename ST::Writer fout, const typename ST::Compute* __restrict__ psi,
+               StepT<typename ST::Compute> p, int seg_len) {
+  using T = typename ST::Compute;
+  constexpr int Q = 27, TX = kMarchTX, TY = kMarchTY, NT = TX * TY;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int S = p.smax, R = S + 1, W = 2 * S + 1;
+  const int RX = TX + 2 * R, RY = TY + 2 * R, RXY = RX * RY;
+  const int GX = TX + 2 * S, GY = TY + 2 * S, GXY = GX * GY;
+  T* s_psi = reinterpret_cast<T*>(smem_raw);  // [3][RXY]
+  T* s_ng = s_psi + 3 * RXY;                   // [W][4][GXY]: n_x, n_y, n_z, |grad psi|
+  const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
+  const int zs = blockIdx.z * seg_len;
+  const int ze = min(zs + seg_len, p.nz);
+  const int tx = threadIdx.x, ty = threadIdx.y, tid = tx + TX * ty;
+  const int x = x0 + tx, y = y0 + ty;
+  const bool col_active = x < p.nx && y < p.ny;
+  auto ring3 = [](int q) { int r = q % 3; return r < 0 ? r + 3 : r; };
+  auto ringW = [W](int q) { int r = q % W; return r < 0 ? r + W : r; };
+
+  for (int q = zs - R; q < ze + R; ++q) {
+    // psi plane q (beyond a z wall only the first plane is read: the mirror of the wall plane)
+    const bool q_needed = !p.wall_z || (q >= -1 && q <= p.nz);
+    if (q_needed) {
+      const int gz = p.wall_z ? clampc(q, p.nz) : wrapn(q, p.nz);
+      T* dst = s_psi + ring3(q) * RXY;
+      for_region(tid, NT, RX, RY, 1, [&](int c, int lx, int ly, int) {
+        const int gx = wrapn(x0 - R + lx, p.nx);
+        const int gy = p.wall_y ? clampc(y0 - R + ly, p.ny) : wrapn(y0 - R + ly, p.ny);
+        dst[c] = psi[gx + p.nx * (gy + p.ny * gz)];
+      });
+    }
+    __syncthreads();
+    // (n, |grad psi|) of plane q - 1 on the column and a halo of smax
+    const int qg = q - 1;
+    if (qg >= zs - S && qg < ze + S && (!p.wall_z || (qg >= 0 && qg < p.nz))) {
+      const T* pm = s_psi + ring3(qg - 1) * RXY;
+      const T* p0 = s_psi + ring3(qg) * RXY;
+      const T* pp = s_psi + ring3(qg + 1) * RXY;
+      T* dst = s_ng + ringW(qg) * 4 * GXY;
+      for_region(tid, NT, GX, GY, 1, [&](int c, int lx, int ly, int) {
+        T grad[3], n[3];
+        grad_ring<T>(pm, p0, pp, RX, (lx + 1) + RX * (ly + 1), grad);
+        const T gn = M<T>::unit(grad, n);
+        dst[c] = n[0];
+        dst[GXY + c] = n[1];
+        dst[2 * GXY + c] = n[2];
+        dst[3 * GXY + c] = gn;
+      });
+    }
+    __syncthreads();
+    // collide plane z = q - R
+    const int z = q - R;
+    if (z >= zs && col_active) {
+      const int idx = x + p.nx * (y + p.ny * z);
+      T fin[2][Q];
+      pull_any<1, T>(f, x, y, z, p, fin);
+      T rho1, rho2;
+      psi_of<Q, T>(fin, &rho1, &rho2);
+      const T rho = rho1 + rho2;
+      T j[3];
+      momentum<1, T>(fin, j);
+      const int c = (tx + S) + GX * (ty + S);
+      const T* own = s_ng + ringW(z) * 4 * GXY;
+      const T n0 = own[c], n1 = own[GXY + c], n2 = own[2 * GXY + c], g = own[3 * GXY + c];
+      T frep[3] = {T(0), T(0), T(0)};
+      if (S > 0 && g > p.g_th) {
+        int hit = 0;
+        static_for<kMaxProbe>([&](auto I) {
+          constexpr int st = decltype(I)::value + 1;
+          if (hit != 0 || st > S) return;  // found, stopped at a wall, or past h_max
+          const int dx = round_probe<st, T>(T(st) * n0);
+          const int dy = round_probe<st, T>(T(st) * n1);
+          const int dz = round_probe<st, T>(T(st) * n2);
+          const int py = y + dy, pz = z + dz;
+          if ((p.wall_y && (py < 0 || py >= p.ny)) || (p.wall_z && (pz < 0 || pz >= p.nz))) {
+            hit = -1;
+            return;
+          }
+          const T* pl = s_ng + ringW(pz) * 4 * GXY;
+          const int cp = c + dx + GX * dy;
+          if (!(pl[3 * GXY + cp] > p.g_th)) return;
+          T dot = pl[cp] * n0 + pl[GXY + cp] * n1;
+          dot += pl[2 * GXY + cp] * n2;
+          if (dot < T(0)) hit = st;
+        });
+        if (hit > 0) {
+          const T A = p.Ah[hit];
+          const T deltaI = T(0.5) * g;
+          frep[0] = -A * n0 * deltaI;
+          frep[1] = -A * n1 * deltaI;
+          frep[2] = -A * n2 * deltaI;
+        }
+      }
+      T F[3], u[3];
+#pragma unroll
+      for (int a = 0; a < 3; ++a) F[a] = p.G[a] + frep[a];
+#pragma unroll
+      for (int a = 0; a < 3; ++a) u[a] = M<T>::div(j[a] + T(0.5) * F[a], rho);
+      const T m[3] = {-n0, -n1, -n2};
+      collide_store<1, T, typename ST::Writer, EDM>(fin, rho1, rho2, j, u, F, g, m, p, fout, idx);
+    }
+  }
+}
+
+}  // namespace lbnci

@@ -14,11 +14,11 @@ SIZES = [(64, 24, 1, 1.0, 0.05, 2e-5), (37, 19, 1, 0.8, 0.1, 1e-5), (96, 40, 0, 
          (32, 16, 1, 1.0, 0.03, 1e-4), (130, 33, 1, 0.7, 0.07, 5e-6)]
 
 
-def _cfgs(precision):
+def _cfgs(precision, forcing=lbnci.LB_FORCE_GUO):
     cfgs, fields = [], []
     for k, (nx, ny, wall, tau, ah, g) in enumerate(SIZES):
         cfgs.append(lbnci.lb_config_make(nx=nx, ny=ny, wall_y=wall, tau=tau, A_s=0.01, beta=0.7, A_h=ah,
-                                         force=(g, 0.0, 0.0), precision=precision))
+                                         force=(g, 0.0, 0.0), precision=precision, forcing=forcing))
         fields.append(inputs.channel_emulsion_2d(nx, ny, seed=100 + k, r_lo=5, r_hi=7, film=0.5))
     return cfgs, fields
 
@@ -28,9 +28,10 @@ def _lib():
     lbnci.load()
 
 
-@pytest.mark.parametrize("precision", [lbnci.LB_FP64, lbnci.LB_FP32, lbnci.LB_FP16DEV])
-def test_members_match_standalone(precision):
-    cfgs, fields = _cfgs(precision)
+@pytest.mark.parametrize("precision,forcing", [(lbnci.LB_FP64, 0), (lbnci.LB_FP32, 0), (lbnci.LB_FP16DEV, 0),
+                                               (lbnci.LB_FP64, 1), (lbnci.LB_FP32, 1)])
+def test_members_match_standalone(precision, forcing):
+    cfgs, fields = _cfgs(precision, forcing)
     with lbnci.Ensemble(cfgs) as ens:
         for m, fl in zip(ens.members, fields):
             m.init_fields(fl.rho1, fl.rho2)

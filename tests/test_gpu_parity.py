@@ -99,8 +99,11 @@ def _duct_fields(nx, ny, nz, seed):
     return inputs.duct_emulsion_3d(nx, ny, nz, seed=seed, radius=5.0, volume_fraction=0.5)
 
 
+@pytest.mark.parametrize("kernel", ["march", "tiled"])
 @pytest.mark.parametrize("walls", [(1, 1), (0, 1), (0, 0)])
-def test_fp64_d3q27_parity(walls):
+def test_fp64_d3q27_parity(walls, kernel, monkeypatch):
+    """Both D3Q27 collision kernels (z-marching, default; 3-D tiles)."""
+    monkeypatch.setenv("LBNCI_D3_KERNEL", kernel)
     nx, ny, nz = 40, 22, 17  # ragged against the 32x4x2 tile
     p = oracle.make_params(lattice=oracle.D3Q27, nx=nx, ny=ny, nz=nz, wall_y=walls[0], wall_z=walls[1],
                            tau=0.9, A_s=0.01, beta=0.7, A_h=0.03, force=(2e-6, 0, 1e-6))
