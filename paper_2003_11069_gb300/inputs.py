@@ -234,3 +234,18 @@ def ensemble_channels(n: int, seed: int, nx_range=(512, 2048), ny_range=(64, 256
         fl.meta["target_area_fraction"] = af
         out.append(Member(nx, ny, g, ah, fl))
     return out
+
+
+def unet_params(shapes, seed: int, bias_scale: float = 0.0) -> list:
+    """Seeded initial parameters of a convolutional network: for each weight shape
+    [C_out, ..., C_in] a He-normal weight (standard deviation sqrt(2 / fan_in), fan_in =
+    the product of all but the first dimension) and a bias drawn from N(0, bias_scale^2).
+    Values are rounded to FP32 so that both sides start from the same numbers."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for _, shape in shapes:
+        fan_in = int(np.prod(shape[1:]))
+        w = rng.normal(0.0, math.sqrt(2.0 / fan_in), size=shape).astype(np.float32).astype(np.float64)
+        b = (rng.normal(0.0, 1.0, size=shape[0]) * bias_scale).astype(np.float32).astype(np.float64)
+        out.append((w, b))
+    return out
