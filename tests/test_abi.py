@@ -5,6 +5,8 @@ import ctypes
 import os
 import re
 
+import numpy as np
+
 import pytest
 
 from paper_2003_11069_gb300 import lbnci
@@ -89,3 +91,32 @@ def test_no_gpu_fails_loudly():
     with pytest.raises(lbnci.LBError) as ei:
         lbnci.lb_create(lbnci.lb_config_make())
     assert ei.value.status == lbnci.LB_ECUDA
+
+
+def _unet_header_functions():
+    txt = open(os.path.join(ROOT, "include", "lbnci_unet.h")).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(lbu_[a-z_0-9]+)\s*\(", txt)))
+
+
+def test_unet_library_exports_and_layer_table():
+    """The U-Net entry points exist, and the library's layer table (a host function) has
+    the oracle's shapes in the oracle's order."""
+    from oracle import unet_oracle as U
+    from paper_2003_11069_gb300 import unet
+    lib = unet.load()
+    names = _unet_header_functions()
+    assert set(names) == set(unet.EXPORTS)
+    for n in names:
+        assert hasattr(lib, n), n
+    for levels in (2, 3, 4):
+        cfg = unet.make_config(levels=levels)
+        lib_shapes = unet.layer_shapes(cfg)
+        ora = U.layer_shapes(levels, 32, 5, 3)
+        assert len(lib_shapes) == len(ora)
+        for (co, kh, kw, ci), (_, ws) in zip(lib_shapes, ora):
+            assert ws == ((co, kh, kw, ci) if kh == 3 else (co, ci))
+        assert unet.param_count(cfg) == sum(int(np.prod(ws)) + ws[0] for _, ws in ora)
+    for bad in (dict(levels=1), dict(base=48), dict(in_ch=33), dict(out_ch=9), dict(H=60), dict(max_batch=0)):
+        with pytest.raises(lbnci.LBError):
+            unet.param_count(unet.make_config(**bad))
