@@ -63,6 +63,12 @@ WORKLOADS = {
                          gen=lambda nx, ny, nz, seed: inputs.duct_emulsion_3d(nx, ny, nz, seed=seed),
                          desc="D3Q27 packed-emulsion square duct 256x64x64 (profiling size), walls y,z, FCC "
                               "droplets R 10, G=2e-6, A_h=0.03"),
+    "warmstart": dict(lattice=0, nx=0, ny=0, nz=1, wall_y=1, wall_z=0, tau=1.0, A_s=0.01, beta=0.7,
+                      A_h=0.0, force=(0.0, 0.0, 0.0), gen=None,
+                      desc="U-Net warm start: D2Q9 packed-emulsion channels, length 512-1024, width 64-96, "
+                           "area fraction 0.7-0.9 target, A_h 0-0.01, Poiseuille velocity 2e-3..2e-2 "
+                           "(log-uniform); network 4 levels, base 32, BF16, trained on LB snapshots "
+                           "resampled to 64x256; held-out channels run cold, cold-perturbed and warm"),
     "droplet2d": dict(lattice=0, nx=128, ny=128, nz=1, wall_y=0, wall_z=0, tau=1.0, A_s=0.01, beta=0.7,
                       A_h=0.05, force=(0.0, 0.0, 0.0),
                       gen=lambda nx, ny, nz, seed: inputs.droplet(nx, ny, radius=30),
@@ -219,7 +225,19 @@ def run_reference(args, w):
     if rank != 0:
         return 0
     cores = os.cpu_count() or 1
+    if w is WORKLOADS["warmstart"]:
+        cpu = unet_cpu_baseline()
+        line = {"impl": "reference", "metric": "U-Net training throughput (FP64 oracle)", "value": cpu["value"],
+                "unit": cpu["unit"], "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": None, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "f64", "data": "synthetic", "config": {"workload": w["desc"], "sample": cpu["sample"]},
+                "cpu_baseline": cpu,
+                "e2e": {"value": cpu["value"], "unit": cpu["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(line), flush=True)
+        return 0
     import oracle
+    if w["nx"] == 0:  # the ensemble: one 1024 x 128 member stands in for the sample
+        w = dict(w, nx=1024, ny=128)
     nx, ny, nz = w["nx"], w["ny"], w["nz"]
     sites = nx * ny * nz
     # each step: one full oracle step on a bounded sample of the workload
@@ -324,6 +342,9 @@ def main(argv=None):
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=12.0)
+    ap.add_argument("--ws-train", type=int, default=768, help="warmstart: training channels")
+    ap.add_argument("--ws-test", type=int, default=64, help="warmstart: held-out channels")
+    ap.add_argument("--ws-horizon", type=int, default=60000, help="warmstart: lattice steps per run")
     ap.add_argument("--flush-mb", type=int, default=L2_FLUSH_BYTES >> 20,
                     help="L2 flush buffer written before every timed step (MB)")
     args = ap.parse_args(argv)
@@ -347,6 +368,8 @@ def main(argv=None):
     lbnci.load()
     if args.workload == "ensemble":
         return main_ensemble(args, w, lbnci, torch, ws, rank, local, dist)
+    if args.workload == "warmstart":
+        return main_warmstart(args, w, torch, ws, rank, local, dist)
     stream = torch.cuda.Stream()
     prec = {"fp32": lbnci.LB_FP32, "fp64": lbnci.LB_FP64, "fp16dev": lbnci.LB_FP16DEV}[args.precision]
     nx, ny, nz = w["nx"], w["ny"], w["nz"]
@@ -485,6 +508,122 @@ def main_ensemble(args, w, lbnci, torch, ws, rank, local, dist):
     }
     print(json.dumps(line), flush=True)
     return 0
+
+
+def unet_train_flops_per_sample(H=64, W=256, levels=4, base=32, in_ch=5, out_ch=3) -> float:
+    """Algorithmic FLOPs of one training sample (forward + data gradient + weight gradient;
+    the first layer needs no data gradient): 2 MACs per weight use per pixel."""
+    fwd = first = 0.0
+    C = [base << l for l in range(levels)]
+    for l in range(levels):
+        P = (H >> l) * (W >> l)
+        cin = in_ch if l == 0 else C[l - 1]
+        fwd += 2 * P * C[l] * 9 * (cin + C[l])
+        if l == 0:
+            first = 2 * P * C[l] * 9 * cin
+    for l in range(levels - 1):
+        P = (H >> l) * (W >> l)
+        fwd += 2 * P * C[l] * 9 * (C[l + 1] + 2 * C[l] + C[l])
+    fwd += 2 * H * W * out_ch * base
+    return 3 * fwd - first
+
+
+def main_warmstart(args, w, torch, ws_, rank, local, dist):
+    """Time to steady state of held-out channels started warm from the trained surrogate,
+    against cold starts; one JSON line. Replicas under torchrun (each rank its own study)."""
+    from paper_2003_11069_gb300 import unet
+    from paper_2003_11069_gb300 import warmstart as wst
+    stream = torch.cuda.Stream()
+    train = wst.channels(args.ws_train, seed=100 + rank, ah_range=(0.0, 0.01))
+    test = wst.channels(args.ws_test, seed=999 + rank, ah_range=(0.0, 0.01))
+    every = 200
+    horizon = args.ws_horizon
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    with ClockSampler(local) as clk:
+        res = wst.experiment(train, test, steps=horizon, every=every, snap_from=int(0.72 * horizon) // 2000 * 2000,
+                             snap_every=2000, epochs=30, batch=32, lr=1e-3, stream=stream.cuda_stream,
+                             log=lambda m: print(m, file=sys.stderr))
+    wall = max_over_ranks(time.perf_counter() - t0, dist, "cuda")
+    # the surrogate's training step alone, timed with CUDA events on its stream
+    cfg = unet.make_config(max_batch=32, stream=stream.cuda_stream)
+    net = unet.Net(cfg)
+    X = torch.randn(64, 64, 256, 5, device="cuda")
+    T = torch.randn(64, 64, 256, 3, device="cuda")
+    idx = torch.arange(32, dtype=torch.int32, device="cuda")
+    torch.cuda.synchronize()
+    for _ in range(args.warmup):
+        net.train_step(X, T, idx=idx, batch=32, lr=1e-4)
+    s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    n = 20
+    l0 = net.launches()
+    s.record(stream)
+    for _ in range(n):
+        net.train_step(X, T, idx=idx, batch=32, lr=1e-4)
+    e.record(stream)
+    torch.cuda.synchronize()
+    step_ms = s.elapsed_time(e) / n
+    launches = (net.launches() - l0) // n
+    net.close()
+    if dist:
+        dist.destroy_process_group()
+    if rank != 0:
+        return 0
+    flops = unet_train_flops_per_sample() * 32
+    with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+        pk = json.load(fh)
+    peak = float(pk.get("bf16_tflops", 1900.0))
+    achieved = flops / (step_ms * 1e-3) / 1e12
+    sm = res["summary"]
+    cpu = None
+    if not args.no_cpu_baseline:
+        cpu = unet_cpu_baseline()
+    line = {
+        "metric": "time-to-steady-state speedup (median over held-out channels, warm vs cold start, flow rate "
+                  "within 1%)",
+        "value": sm["median_speedup_warm"], "unit": "x", "n_gpus": ws_, "steps": horizon, "warmup": args.warmup,
+        "ms_per_step": None, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "bf16 network (f32 accumulate), f32 lattice Boltzmann", "data": "synthetic",
+        "config": {"workload": w["desc"], "train_channels": len(train), "test_channels": len(test),
+                   "snapshots": res["snapshots"], "horizon_steps": horizon, "record_every": every,
+                   "window_steps": res["window_steps"], "l2": "not applicable (whole pipeline)",
+                   "wall_seconds": round(wall, 1), "data_seconds": round(res["data_seconds"], 1),
+                   "train_seconds": round(res["train_seconds"], 1), "train_steps": res["train_steps"],
+                   "test_lb_seconds": round(res["lb_seconds_test"], 1)},
+        "summary": sm,
+        "roofline": {"bound": "tensor", "achieved": round(achieved, 1), "peak": peak, "unit": "TFLOP/s",
+                     "frac": round(achieved / peak, 4), "traffic": None,
+                     "peak_source": "measured (MEASURED_PEAKS.json bf16_tflops, burst)",
+                     "kernel": "U-Net training step (batch 32, 64x256, all kernels)",
+                     "flops_per_step": flops, "ms_per_train_step": round(step_ms, 4)},
+        "cpu_baseline": cpu, "e2e": None, "gpu_launches": int(launches),
+        "gpu_launches_note": "kernel launches of one U-Net training step",
+        "clocks": clk.summary(),
+    }
+    print(json.dumps(line, default=float), flush=True)
+    return 0
+
+
+def unet_cpu_baseline(budget_s: float = 15.0) -> dict:
+    """The FP64 U-Net oracle (numpy) on the host: forward + backward of single 64x256 samples."""
+    from oracle import unet_oracle as U
+    shapes = U.layer_shapes(4, 32, 5, 3)
+    params = inputs.unet_params(shapes, 0)
+    rng = np.random.default_rng(0)
+    x = rng.normal(size=(1, 64, 256, 5))
+    t = rng.normal(size=(1, 64, 256, 3))
+    n, t0 = 0, time.perf_counter()
+    while True:
+        U.loss_and_grads(params, x, t, levels=4)
+        n += 1
+        if time.perf_counter() - t0 > budget_s or n >= 50:
+            break
+    el = time.perf_counter() - t0
+    return {"value": round(unet_train_flops_per_sample() * n / el / 1e12, 5), "unit": "TFLOP/s",
+            "cores": os.cpu_count() or 1, "kind": "oracle",
+            "sample": f"{n} single-sample forward+backward passes of the 4-level U-Net oracle (numpy FP64)"}
 
 
 if __name__ == "__main__":
