@@ -161,6 +161,15 @@ const char* lb_last_error(const lb_sim* sim);
 /* Step kernels launched by this sim since lb_create (for launch accounting). */
 long long lb_kernel_launches(const lb_sim* sim);
 
+/* Which kernel lb_step runs for this sim (no paper counterpart; reporting only):
+ *   LB_PATH_FUSED2D  one-pass fused D2Q9 kernel (FP64, FP16-dev, FP32 when nx % 4 != 0
+ *                    or LBNCI_FUSED=classic is set in the environment),
+ *   LB_PATH_TMA2D    persistent TMA-fed D2Q9 FP32 kernel,
+ *   LB_PATH_D3Q27    D3Q27 moments + collision kernels.
+ * Returns -1 for a NULL sim. */
+enum { LB_PATH_FUSED2D = 0, LB_PATH_TMA2D = 1, LB_PATH_D3Q27 = 2 };
+int lb_step_path(const lb_sim* sim);
+
 /* ------------------------------------------------------------------------------
  * Ensembles: n independent D2Q9 lattices of different sizes and parameters (each a
  * full lb_config: size, walls, tau, A_s, beta, A_h, h_min, h_max, g_th, force) stepped

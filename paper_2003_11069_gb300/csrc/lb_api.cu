@@ -63,6 +63,9 @@ struct lb_sim {
   cudaStream_t stream;
   void* fa;        // current state
   void* fb;        // back buffer (also staging between steps)
+  void* buf_a;     // the state buffer that fa points to at creation
+  TmaMaps maps;    // tensor maps of both state buffers (p.tma)
+  int* errflag;    // device word: bit 0 set when a kernel's bounded wait expired
   void* psi;       // order parameter of the streamed state
   double* partials;
   double* result;  // kRedSlots doubles
@@ -95,6 +98,10 @@ lb_status cuda_fail(lb_sim* s, cudaError_t e, const char* what) {
 }
 
 size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
+
+// The result area holds 16 doubles: the kRedSlots reductions, then, in slot
+// kErrSlot, the kernels' error word (an int).
+constexpr int kErrSlot = 12;
 
 struct Layout {
   size_t fa, fb, psi, partials, result, total;
@@ -152,6 +159,13 @@ lb_status validate(const lb_config* c, HostParams* p, Layout* lay, long long* nb
   // Tile of the fused D2Q9 kernel: LBNCI_FUSED_SPT=2 (32x16, the default) or 4 (32x32).
   p->spt = 2;
   if (const char* e = std::getenv("LBNCI_FUSED_SPT")) p->spt = std::atoi(e) == 4 ? 4 : 2;
+  // D2Q9 FP32 step: the persistent TMA-fed kernel (its tensor maps need nx % 4 == 0),
+  // unless LBNCI_FUSED=classic selects the one-pass fused kernel.
+  p->tma = c->lattice == LB_D2Q9 && c->precision == LB_FP32 && c->nx % 4 == 0 ? 1 : 0;
+  if (const char* e = std::getenv("LBNCI_FUSED"))
+    if (std::strcmp(e, "classic") == 0) p->tma = 0;
+  p->tma_stages = 1;
+  if (const char* e = std::getenv("LBNCI_TMA_STAGES")) p->tma_stages = std::atoi(e) == 2 ? 2 : 1;
   const int Q = c->lattice == LB_D2Q9 ? 9 : 27;
   (void)Q;
   const Launchers* L = launchers_for(c);
@@ -188,10 +202,14 @@ lb_status run_fields(lb_sim* s, const FieldOut& outs) {
   if (e != cudaSuccess) return cuda_fail(s, e, "fields launch");
   e = reduce_partials(s->partials, s->nblocks, s->result, s->stream);
   if (e != cudaSuccess) return cuda_fail(s, e, "reduce launch");
-  e = cudaMemcpyAsync(s->host_result, s->result, kRedSlots * sizeof(double), cudaMemcpyDeviceToHost, s->stream);
+  e = cudaMemcpyAsync(s->host_result, s->result, 16 * sizeof(double), cudaMemcpyDeviceToHost, s->stream);
   if (e != cudaSuccess) return cuda_fail(s, e, "result copy");
   e = cudaStreamSynchronize(s->stream);
   if (e != cudaSuccess) return cuda_fail(s, e, "stream synchronize");
+  int flag = 0;
+  std::memcpy(&flag, &s->host_result[kErrSlot], sizeof(flag));
+  if (flag != 0)
+    return fail(s, LB_ECUDA, "a step kernel gave up waiting for its TMA copies (flag %d); the state is invalid", flag);
   return LB_OK;
 }
 
@@ -259,9 +277,17 @@ lb_status lb_create(const lb_config* cfg, lb_sim** out) {
   }
   s->fa = base + lay.fa;
   s->fb = base + lay.fb;
+  s->buf_a = s->fa;
   s->psi = base + lay.psi;
   s->partials = (double*)(base + lay.partials);
   s->result = (double*)(base + lay.result);
+  s->errflag = (int*)(s->result + kErrSlot);
+  if (s->p.tma) {
+    // tensor maps of both state buffers; without the driver's tensor-map encoder the
+    // step falls back to the one-pass fused kernel
+    if (!tma2d_supported(s->p) || tma2d_prepare(&s->maps, s->fa, s->fb, s->p) != cudaSuccess) s->p.tma = 0;
+    cudaGetLastError();
+  }
   e = cudaMallocHost((void**)&s->host_result, 16 * sizeof(double));
   if (e != cudaSuccess) {
     if (s->owns) cudaFree(s->base);
@@ -269,6 +295,7 @@ lb_status lb_create(const lb_config* cfg, lb_sim** out) {
     return fail(nullptr, LB_ECUDA, "pinned allocation failed: %s", cudaGetErrorString(e));
   }
   e = cudaMemsetAsync(s->fa, 0, lay.psi, s->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(s->result, 0, 16 * sizeof(double), s->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
   if (e != cudaSuccess) {
     lb_destroy(s);
@@ -312,7 +339,13 @@ lb_status lb_step(lb_sim* s, long long nsteps) {
   if (s->in_ensemble) return fail(s, LB_EINVAL, "an ensemble member is stepped by lb_ensemble_step");
   for (long long t = 0; t < nsteps; ++t) {
     int nk = 0;
-    cudaError_t e = s->L->step(s->fa, s->fb, s->psi, s->p, s->stream, &nk);
+    cudaError_t e;
+    if (s->p.tma) {
+      e = tma2d_step(s->maps, s->fa == s->buf_a ? 0 : 1, s->fa, s->fb, s->errflag, s->p, s->stream);
+      nk = 1;
+    } else {
+      e = s->L->step(s->fa, s->fb, s->psi, s->p, s->stream, &nk);
+    }
     s->launches += nk;
     if (e != cudaSuccess) return cuda_fail(s, e, "step launch");
     std::swap(s->fa, s->fb);
@@ -455,6 +488,12 @@ void lb_destroy(lb_sim* s) {
 const char* lb_last_error(const lb_sim* s) { return s ? s->err : g_err; }
 
 long long lb_kernel_launches(const lb_sim* s) { return s ? s->launches : 0; }
+
+int lb_step_path(const lb_sim* s) {
+  if (!s) return -1;
+  if (s->cfg.lattice == LB_D3Q27) return LB_PATH_D3Q27;
+  return s->p.tma ? LB_PATH_TMA2D : LB_PATH_FUSED2D;
+}
 
 }  // extern "C"
 

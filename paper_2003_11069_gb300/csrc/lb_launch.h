@@ -16,6 +16,8 @@ struct HostParams {
   int num_sms;  // multiprocessors of the device
   int forcing;  // 0: Guo, 1: exact difference method on the dispersed phase
   int d3_kernel;  // D3Q27 collision: 0 marching along z (default), 1 tiled
+  int tma;        // 1: D2Q9 FP32 steps run the persistent TMA-fed kernel
+  int tma_stages; // its population stages: 1 (two CTAs per SM, default) or 2 (one CTA per SM)
   double tau, A_s, beta, A_h, h_min, h_max, g_th, G[3];
 };
 
@@ -39,6 +41,17 @@ struct Launchers {
   cudaError_t (*batch_step)(const void* members, const int* tile0, int n, int total_tiles, int parity, int spt,
                             int smax_max, int edm, cudaStream_t s);
 };
+
+// Persistent TMA-fed D2Q9 FP32 step (lb_tma2d.cu), tiles of kTmaTX x kTmaTY sites.
+constexpr int kTmaTX = 32, kTmaTY = 16;
+struct TmaMaps {
+  alignas(64) unsigned char bytes[2 * 128];  // tensor maps of state buffer A and B
+};
+bool tma2d_supported(const HostParams& h);
+cudaError_t tma2d_prepare(TmaMaps* m, const void* fa, const void* fb, const HostParams& h);
+// One step from state `from` (0: buffer A, 1: buffer B) into the other buffer.
+cudaError_t tma2d_step(const TmaMaps& m, int from, const void* fa, void* fb, int* err, const HostParams& h,
+                       cudaStream_t s);
 
 const Launchers* launchers_fp64(int lattice);
 const Launchers* launchers_fp32(int lattice);

@@ -1,0 +1,469 @@
+// lb_tma2d.cu -- persistent, TMA-fed D2Q9 step for FP32 populations
+// (arXiv:2003.11069, "Materials and Methods": the colour-gradient step
+// Omega = Omega^(3)[Omega^(1) + Omega^(2)] with the near-contact force of Eq. (near_c);
+// the per-site arithmetic is that of lb_kernels.cuh).
+//
+// One CTA of 512 threads per SM walks 32 x 16 tiles, tile = blockIdx.x + k gridDim.x,
+// one thread per site. The gradient of psi and the NCI ray search at a site read psi
+// up to R = smax + 1 = 5 sites away, and psi at a site is a sum of the 18 populations
+// streamed into it, so a tile needs the populations of its 48 x 28 neighbourhood
+// (x0-8..x0+39, y0-6..y0+21; the x range is widened to keep TMA coordinates 16-byte
+// aligned). For an interior ("fast") tile one elected thread loads that box, all 18
+// population planes, with a single TMA copy into a double-buffered shared-memory
+// stage one tile ahead, so the copy of the next tile overlaps the arithmetic of this
+// one and costs no load instructions. Everything the step reads then comes from
+// shared memory:
+//   phase 1: pull the own site (kept in registers) and every halo cell from the box,
+//            psi into shared memory;
+//   phase 2: unit normal and |grad psi| of the own site (registers) and of the ring of
+//            width smax around the tile, stored as probe normals (zero where
+//            |grad psi| <= g_th, so a probe needs one load and one sign test);
+//   phase 3: NCI ray search, Guo velocity, BGK + source + perturbation, recolouring,
+//            coalesced stores of the 18 new populations.
+// Tiles whose neighbourhood wraps around the lattice (the first and last tile columns,
+// the first and last tile rows of a periodic y axis) or that are ragged take a slow
+// path with the same phases 2-3 but pulls from global memory.
+//
+// Every wait on an mbarrier is bounded (about one second); on expiry the kernel
+// records a flag that the host reports, waits (bounded again) for its own copies
+// in flight, and returns.
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <cudaTypedefs.h>
+
+#include "lb_kernels.cuh"
+#include "lb_launch.h"
+
+namespace lbnci {
+namespace {
+
+constexpr int TX = kTmaTX, TY = kTmaTY, NT = TX * TY;  // 32 x 16 tile, one thread per site
+constexpr int kQ = 9;
+// population box: 18 planes x 28 rows (y0-6..y0+21) x 48 columns (x0-8..x0+39)
+constexpr int kBX = 48, kBY = 28, kBOX = 8, kBOY = 6, kBPlane = kBX * kBY;
+constexpr int kBoxFloats = 2 * kQ * kBPlane;
+constexpr unsigned kBoxBytes = kBoxFloats * 4;
+constexpr int kBoxStride = (kBoxBytes + 1023) / 1024 * 1024;
+
+// Shared-memory layout (bytes from a 1024-aligned base): STAGES population boxes,
+// psi of the tile and its halo, probe normals, two mbarriers.
+constexpr int kRmax = kMaxProbe + 1;
+constexpr int kPsiBytes = (TX + 2 * kRmax) * (TY + 2 * kRmax) * 4;           // (32+10) x (16+10) floats
+constexpr int kPBytes = (TX + 2 * kMaxProbe) * (TY + 2 * kMaxProbe) * 8;     // (32+8) x (16+8) float2
+template <int STAGES> __host__ __device__ constexpr int off_psi() { return STAGES * kBoxStride; }
+template <int STAGES> __host__ __device__ constexpr int off_P() { return off_psi<STAGES>() + kPsiBytes; }
+template <int STAGES> __host__ __device__ constexpr int off_bar() { return off_P<STAGES>() + kPBytes; }
+template <int STAGES> __host__ __device__ constexpr int smem_bytes() { return off_bar<STAGES>() + 16 + 1024; }  // + alignment slack
+static_assert(smem_bytes<2>() <= 227 * 1024, "shared memory (two stages, one CTA per SM)");
+static_assert(2 * (smem_bytes<1>() + 1024) <= 228 * 1024, "shared memory (one stage, two CTAs per SM)");
+
+constexpr unsigned long long kWaitLimitNs = 1000000000ull;
+
+// ------------------------------------------------------------------ PTX helpers
+__device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ unsigned long long globaltimer() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long* bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Wait for phase `parity` of an mbarrier for at most kWaitLimitNs; false on expiry.
+__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned parity) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const unsigned long long t0 = globaltimer();
+  while (!mbar_try_wait(bar, parity))
+    if (globaltimer() - t0 > kWaitLimitNs) return false;
+  return true;
+}
+
+__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, int x, int y, int z,
+                                            unsigned long long* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
+      "[%5];" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<unsigned long long>(map)), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
+      : "memory");
+}
+
+// Probe offset of the NCI ray: round(s n_a) to the nearest integer (ties to even),
+// returned as the float's bit pattern b with round(s n_a) = b - kMagicBits; adding
+// 1.5 2^23 leaves the integer in the low mantissa bits (|s n_a| <= 4 here). The FP64
+// kernels round half away from zero; the two differ only when s n_a is exactly a
+// half-integer, a tie at which the FP32 path may take either side.
+constexpr float kMagic = 12582912.0f;
+constexpr unsigned kMagicBits = 0x4B400000u;
+__device__ __forceinline__ unsigned probe_bits(float s, float v) { return __float_as_uint(fmaf(s, v, kMagic)); }
+
+// Halo cell h of a ring of width W around the 32 x 16 tile, in region coordinates
+// (region = (32 + 2W) x (16 + 2W)): two bands of W full rows, then the W-wide sides.
+template <int W>
+__device__ __forceinline__ void ring_cell(int h, int& lx, int& ly) {
+  constexpr int RX = TX + 2 * W, nband = W * RX;
+  if (h < 2 * nband) {
+    const int hb = h < nband ? h : h - nband;
+    const int row = hb / RX;
+    lx = hb - row * RX;
+    ly = h < nband ? row : W + TY + row;
+  } else {
+    const int hs = h - 2 * nband;
+    const int row = hs / (2 * W);
+    const int col = hs - row * (2 * W);
+    lx = col < W ? col : col + TX;
+    ly = W + row;
+  }
+}
+
+// True when the tile is full and its population box needs no periodic wrap (walls
+// may cut it: rows beyond a wall are never read as sources).
+__device__ __forceinline__ bool fast_tile(int x0, int y0, const StepT<float>& p) {
+  if (x0 < TX || x0 + kBX - kBOX > p.nx) return false;
+  if (p.wall_y) return y0 + TY <= p.ny;
+  return y0 >= kBOY && y0 + kBY - kBOY <= p.ny;
+}
+
+// Pull the 2 Q populations of the site at box position c (plane offsets kBPlane);
+// bounce-back at walls from the site itself.
+__device__ __forceinline__ void pull_box(const float* __restrict__ bx, int c, bool bym, bool byp,
+                                         float fin[2][kQ]) {
+  if (!(bym || byp)) {
+    static_for<kQ>([&](auto I) {
+      constexpr int i = decltype(I)::value;
+      constexpr int off = -cc(i, 1) * kBX - cc(i, 0);
+      fin[0][i] = bx[i * kBPlane + c + off];
+      fin[1][i] = bx[(kQ + i) * kBPlane + c + off];
+    });
+  } else {
+    static_for<kQ>([&](auto I) {
+      constexpr int i = decltype(I)::value;
+      constexpr int cy = cc(i, 1);
+      constexpr int off = -cy * kBX - cc(i, 0);
+      const bool bounce = (cy == 1 && bym) || (cy == -1 && byp);
+      fin[0][i] = bounce ? bx[opposite(i) * kBPlane + c] : bx[i * kBPlane + c + off];
+      fin[1][i] = bounce ? bx[(kQ + opposite(i)) * kBPlane + c] : bx[(kQ + i) * kBPlane + c + off];
+    });
+  }
+}
+
+struct TmaArgs {
+  int* err;  // bit 0: a TMA wait expired
+  int ntx, ntiles;
+};
+
+// STAGES = 2: one CTA per SM (128 registers a thread), the next tile's box is loaded
+// into the other stage while this tile is computed. STAGES = 1: two CTAs per SM (64
+// registers), the next tile's box is loaded as soon as this tile's phase 1 has read
+// the stage, and the other CTA computes meanwhile.
+template <int S, bool EDM, int STAGES>
+__global__ void __launch_bounds__(NT, 3 - STAGES)
+tma2d_kernel(const __grid_constant__ CUtensorMap map_pop, Plain<0, float>::Reader f, Plain<0, float>::Writer fout,
+             StepT<float> p, TmaArgs a) {
+  constexpr int R = S + 1;  // psi halo
+  constexpr int RX = TX + 2 * R, RY = TY + 2 * R;
+  constexpr int GX = TX + 2 * S, GY = TY + 2 * S;
+  constexpr int NHALO = RX * RY - NT, NRING = GX * GY - NT;
+  extern __shared__ unsigned char smem_dyn[];
+  unsigned char* sm = reinterpret_cast<unsigned char*>(
+      (reinterpret_cast<uintptr_t>(smem_dyn) + 1023) & ~static_cast<uintptr_t>(1023));
+  auto box = [&](int b) { return reinterpret_cast<float*>(sm + b * kBoxStride); };
+  float* s_psi = reinterpret_cast<float*>(sm + off_psi<STAGES>());
+  float2* s_P = reinterpret_cast<float2*>(sm + off_P<STAGES>());
+  unsigned long long* bar = reinterpret_cast<unsigned long long*>(sm + off_bar<STAGES>());
+
+  const int tid = threadIdx.x;
+  const int tx = tid & (TX - 1), ty = tid >> 5;
+  const bool walls = p.wall_y != 0;
+  const int nx = p.nx, ny = p.ny;
+
+  if (tid == 0) {
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<unsigned long long>(&map_pop)) : "memory");
+  }
+  __syncthreads();
+
+  auto origin = [&](int tile, int& x0, int& y0) {
+    const int by = tile / a.ntx;
+    x0 = (tile - by * a.ntx) * TX;
+    y0 = by * TY;
+  };
+  auto issue = [&](int tile, int b) {  // one thread: TMA load of a fast tile's box into stage b
+    int x0, y0;
+    origin(tile, x0, y0);
+    mbar_expect_tx(&bar[b], kBoxBytes);
+    tma_load_3d(box(b), &map_pop, x0 - kBOX, y0 - kBOY, 0, &bar[b]);
+  };
+  auto tile_fast = [&](int tile) {
+    int x0, y0;
+    origin(tile, x0, y0);
+    return fast_tile(x0, y0, p);
+  };
+
+  unsigned phase = 0;    // bit b: parity of the next completion of bar[b]
+  unsigned pending = 0;  // bit b: a TMA load into stage b is in flight
+  if ((int)blockIdx.x < a.ntiles && tile_fast(blockIdx.x)) {
+    if (tid == 0) issue(blockIdx.x, 0);
+    pending |= 1u;
+  }
+
+  int k = 0;
+  for (int tile = blockIdx.x; tile < a.ntiles; tile += gridDim.x, ++k) {
+    const int b = STAGES == 2 ? (k & 1) : 0;
+    int x0, y0;
+    origin(tile, x0, y0);
+    const bool fast = fast_tile(x0, y0, p);
+    const int next = tile + gridDim.x;
+    const bool next_fast = next < a.ntiles && tile_fast(next);
+    if (STAGES == 2 && next_fast) {  // stage b^1 was last read before this tile
+      if (tid == 0) issue(next, b ^ 1);
+      pending |= 2u >> b;
+    }
+    const int x = x0 + tx, y = y0 + ty;
+    const bool act = x < nx && y < ny;
+    float fin[2][kQ];
+    float rho1 = 0.f, rho2 = 0.f;
+
+    // ---- phase 1: own populations (registers) and psi of the tile and its halo
+    if (fast) {
+      const bool ok = mbar_wait(&bar[b], (phase >> b) & 1u);
+      if (__syncthreads_or(!ok)) {
+        if (tid == 0) atomicOr(a.err, 1);
+        for (int q = 0; q < 2; ++q)  // wait (bounded) for every copy still in flight
+          if ((pending >> q) & 1u) mbar_wait(&bar[q], (phase >> q) & 1u);
+        return;
+      }
+      phase ^= 1u << b;
+      pending &= ~(1u << b);
+      const float* bx = box(b);
+      pull_box(bx, (ty + kBOY) * kBX + (tx + kBOX), walls && y == 0, walls && y == ny - 1, fin);
+      s_psi[(tx + R) + RX * (ty + R)] = psi_of<kQ, float>(fin, &rho1, &rho2);
+      for (int h = tid; h < NHALO; h += NT) {
+        int lx, ly;
+        ring_cell<R>(h, lx, ly);
+        int gy = y0 - R + ly;
+        if (walls) {
+          if (gy < -1 || gy > ny) continue;  // beyond a wall only the mirror row is read
+          gy = clampc(gy, ny);
+        }
+        float hf[2][kQ];
+        pull_box(bx, (gy - y0 + kBOY) * kBX + (lx - R + kBOX), walls && gy == 0, walls && gy == ny - 1,
+                 hf);
+        s_psi[lx + RX * ly] = psi_of<kQ, float>(hf);
+      }
+    } else {
+      if (act) {
+        pull_any<0, float>(f, x, y, 0, p, fin);
+        s_psi[(tx + R) + RX * (ty + R)] = psi_of<kQ, float>(fin, &rho1, &rho2);
+      } else {  // an own position beyond a ragged edge holds the psi of the site it wraps to
+        const int gx = wrapn(x, nx);
+        const int gy = walls ? clampc(y, ny) : wrapn(y, ny);
+        float h2[2][kQ];
+        pull_site<0, float>(f, gx, gy, 0, p, h2);
+        s_psi[(tx + R) + RX * (ty + R)] = psi_of<kQ, float>(h2);
+      }
+      for (int h = tid; h < NHALO; h += NT) {
+        int lx, ly;
+        ring_cell<R>(h, lx, ly);
+        int gy = y0 - R + ly;
+        if (walls && (gy < -1 || gy > ny)) continue;
+        const int gx = wrapn(x0 - R + lx, nx);
+        gy = walls ? clampc(gy, ny) : wrapn(gy, ny);
+        float hf[2][kQ];
+        pull_any<0, float>(f, gx, gy, 0, p, hf);
+        s_psi[lx + RX * ly] = psi_of<kQ, float>(hf);
+      }
+    }
+    __syncthreads();
+    if (STAGES == 1 && next_fast) {  // the stage has been read: load the next tile into it
+      if (tid == 0) issue(next, 0);
+      pending |= 1u;
+    }
+
+    // ---- phase 2: unit normal and |grad psi|; own site in registers, every cell
+    // within S of the tile as a probe normal (zero where |grad psi| <= g_th)
+    float n0, n1, g;
+    {
+      float grad[3], n[3];
+      grad_smem<0, float>(s_psi, RX, 0, (tx + R) + RX * (ty + R), grad);
+      g = M<float>::unit(grad, n);
+      n0 = n[0];
+      n1 = n[1];
+      if constexpr (S > 0) s_P[(tx + S) + GX * (ty + S)] = g > p.g_th ? make_float2(n0, n1) : make_float2(0.f, 0.f);
+    }
+    if constexpr (S > 0) {
+      for (int h = tid; h < NRING; h += NT) {
+        int lx, ly;
+        ring_cell<S>(h, lx, ly);
+        const int gy = y0 - S + ly;
+        if (walls && (gy < 0 || gy >= ny)) continue;  // probes stop at walls
+        float grad[3], n[3];
+        grad_smem<0, float>(s_psi, RX, 0, (lx + 1) + RX * (ly + 1), grad);
+        const float gg = M<float>::unit(grad, n);
+        s_P[lx + GX * ly] = gg > p.g_th ? make_float2(n[0], n[1]) : make_float2(0.f, 0.f);
+      }
+    }
+    __syncthreads();
+
+    // ---- phase 3: NCI ray search, forcing, collision, recolouring, store
+    if (act) {
+      const float rho = rho1 + rho2;
+      float j[3];
+      momentum<0, float>(fin, j);
+      float frep0 = 0.f, frep1 = 0.f;
+      if (S > 0 && g > p.g_th) {
+        // g > g_th > = 0 implies a finite normal with |n_a| <= 1, so |probe offset| <= s
+        const bool near_wall = walls && (y0 < S || y0 + TY + S > ny);
+        int hit = 0;
+        float A = 0.f;  // A_h(h) of the hit (indexed at compile time: no local copy of p)
+        const float2* Pc = s_P + (tx + S) + GX * (ty + S);
+        static_for<(S > 0 ? S : 1)>([&](auto I) {
+          constexpr int st = decltype(I)::value + 1;
+          if (hit != 0 || st > p.smax) return;
+          const unsigned bxu = probe_bits(float(st), n0), byu = probe_bits(float(st), n1);
+          if (near_wall) {
+            const int py = y + (int)(byu - kMagicBits);
+            if (py < 0 || py >= ny) { hit = -1; return; }
+          }
+          const int off = (int)(bxu + (unsigned)GX * byu - (unsigned)(GX + 1) * kMagicBits);
+          const float2 q = Pc[off];
+          if (q.x * n0 + q.y * n1 < 0.f) { hit = st; A = p.Ah[st]; }
+        });
+        if (hit > 0) {
+          const float deltaI = 0.5f * g;
+          frep0 = -A * n0 * deltaI;
+          frep1 = -A * n1 * deltaI;
+        }
+      }
+      const float F[3] = {p.G[0] + frep0, p.G[1] + frep1, p.G[2]};
+      float u[3];
+#pragma unroll
+      for (int c = 0; c < 3; ++c) u[c] = __fdividef(j[c] + 0.5f * F[c], rho);
+      const float m[3] = {-n0, -n1, 0.f};
+      collide_store<0, float, Plain<0, float>::Writer, EDM>(fin, rho1, rho2, j, u, F, g, m, p, fout, x + nx * y);
+    }
+  }
+}
+
+StepT<float> to_step(const HostParams& h) {
+  StepT<float> p;
+  p.nx = h.nx; p.ny = h.ny; p.nz = h.nz; p.wall_y = h.wall_y; p.wall_z = h.wall_z;
+  p.N = h.N; p.smax = h.smax;
+  p.edm = h.forcing == 1;
+  p.omega = 1.0f / float(h.tau);
+  p.guo = 1.0f - 0.5f * p.omega;
+  p.pamp = 2.0f * (0.5f * float(h.A_s));
+  p.beta = float(h.beta);
+  p.g_th = float(h.g_th);
+  for (int a = 0; a < 3; ++a) p.G[a] = float(h.G[a]);
+  for (int k = 0; k < 8; ++k) {
+    const float hd = float(k), hmin = float(h.h_min), hmax = float(h.h_max), A = float(h.A_h);
+    if (k == 0) p.Ah[k] = 0.0f;
+    else if (hd <= hmin) p.Ah[k] = A;
+    else if (hd <= hmax) { const float r = hmin / hd; p.Ah[k] = A * (r * r * r); }
+    else p.Ah[k] = 0.0f;
+  }
+  return p;
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    void* ptr = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &ptr, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(ptr);
+    cudaGetLastError();
+  }
+  return fn;
+}
+
+// Populations of one state as a 3-D tensor (x, y, plane) of floats, box 48 x 28 x 18.
+bool encode_pop(CUtensorMap* m, const void* base, const HostParams& h) {
+  auto fn = encode_fn();
+  if (!fn) return false;
+  const cuuint64_t dims[3] = {(cuuint64_t)h.nx, (cuuint64_t)h.ny, 2 * kQ};
+  const cuuint64_t strides[2] = {(cuuint64_t)h.nx * 4, (cuuint64_t)h.N * 4};
+  const cuuint32_t box[3] = {kBX, kBY, 2 * kQ};
+  const cuuint32_t es[3] = {1, 1, 1};
+  return fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<void*>(base), dims, strides, box, es,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+template <int S, bool EDM, int STAGES>
+cudaError_t launch_v(const CUtensorMap& map, const void* fa, void* fb, int* err, const StepT<float>& p, int num_sms,
+                     cudaStream_t s) {
+  static bool configured = false;
+  constexpr int smem = smem_bytes<STAGES>();
+  if (!configured) {
+    cudaError_t e =
+        cudaFuncSetAttribute(tma2d_kernel<S, EDM, STAGES>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    configured = true;
+  }
+  TmaArgs a;
+  a.err = err;
+  a.ntx = (p.nx + TX - 1) / TX;
+  a.ntiles = a.ntx * ((p.ny + TY - 1) / TY);
+  const int slots = num_sms * (3 - STAGES);  // resident CTAs
+  const int grid = a.ntiles < slots ? a.ntiles : slots;
+  tma2d_kernel<S, EDM, STAGES><<<grid, NT, smem, s>>>(map, Plain<0, float>::reader(fa, (unsigned)p.N),
+                                                      Plain<0, float>::writer(fb, (unsigned)p.N), p, a);
+  return cudaGetLastError();
+}
+
+template <int S, bool EDM>
+cudaError_t launch_s(const CUtensorMap& map, const void* fa, void* fb, int* err, const StepT<float>& p, int num_sms,
+                     int stages, cudaStream_t s) {
+  return stages == 2 ? launch_v<S, EDM, 2>(map, fa, fb, err, p, num_sms, s)
+                     : launch_v<S, EDM, 1>(map, fa, fb, err, p, num_sms, s);
+}
+
+}  // namespace
+
+bool tma2d_supported(const HostParams& h) { return h.nx % 4 == 0 && h.nz == 1 && encode_fn() != nullptr; }
+
+cudaError_t tma2d_prepare(TmaMaps* m, const void* fa, const void* fb, const HostParams& h) {
+  static_assert(sizeof(CUtensorMap) == 128, "tensor map size");
+  CUtensorMap* maps = reinterpret_cast<CUtensorMap*>(m->bytes);
+  return encode_pop(&maps[0], fa, h) && encode_pop(&maps[1], fb, h) ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+cudaError_t tma2d_step(const TmaMaps& m, int from, const void* fa, void* fb, int* err, const HostParams& h,
+                       cudaStream_t s) {
+  const StepT<float> p = to_step(h);
+  const CUtensorMap& map = reinterpret_cast<const CUtensorMap*>(m.bytes)[from];
+  const bool edm = h.forcing == 1;
+  const int st = h.tma_stages;
+  if (h.smax == 0)
+    return edm ? launch_s<0, true>(map, fa, fb, err, p, h.num_sms, st, s)
+               : launch_s<0, false>(map, fa, fb, err, p, h.num_sms, st, s);
+  return edm ? launch_s<kMaxProbe, true>(map, fa, fb, err, p, h.num_sms, st, s)
+             : launch_s<kMaxProbe, false>(map, fa, fb, err, p, h.num_sms, st, s);
+}
+
+}  // namespace lbnci

@@ -24,7 +24,7 @@ STATUS = {0: "LB_OK", 1: "LB_EINVAL", 2: "LB_ENOMEM", 3: "LB_ECUDA", 4: "LB_ENUM
 # Every symbol include/lbnci.h declares.
 EXPORTS = ("lb_workspace_size", "lb_create", "lb_init_fields", "lb_step", "lb_observables",
            "lb_fields", "lb_get_populations", "lb_set_populations", "lb_destroy",
-           "lb_last_error", "lb_kernel_launches", "lb_observables_noalloc",
+           "lb_last_error", "lb_kernel_launches", "lb_step_path", "lb_observables_noalloc",
            "lb_ensemble_create", "lb_ensemble_member", "lb_ensemble_step", "lb_ensemble_tune",
            "lb_ensemble_tune_times", "lb_ensemble_launches", "lb_ensemble_last_error", "lb_ensemble_destroy")
 
@@ -100,6 +100,8 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
     lib.lb_last_error.restype = ctypes.c_char_p
     lib.lb_kernel_launches.argtypes = [simp]
     lib.lb_kernel_launches.restype = ctypes.c_longlong
+    lib.lb_step_path.argtypes = [simp]
+    lib.lb_step_path.restype = ctypes.c_int
     lib.lb_observables_noalloc.argtypes = [cfgp, vp, ctypes.POINTER(lb_obs)]
     lib.lb_ensemble_create.argtypes = [cfgp, ctypes.c_int, ctypes.POINTER(ctypes.c_void_p)]
     lib.lb_ensemble_member.argtypes = [simp, ctypes.c_int, ctypes.POINTER(ctypes.c_void_p)]
@@ -246,6 +248,13 @@ def lb_kernel_launches(sim) -> int:
     return int(load().lb_kernel_launches(sim))
 
 
+LB_PATH_FUSED2D, LB_PATH_TMA2D, LB_PATH_D3Q27 = 0, 1, 2
+
+
+def lb_step_path(sim) -> int:
+    return int(load().lb_step_path(sim))
+
+
 def lb_observables_noalloc(cfg: lb_config, f, allow_numeric=False) -> dict:
     """Observables of device populations f (a CUDA tensor of the storage dtype) with no
     allocation inside the library; see include/lbnci.h for its limits."""
@@ -325,6 +334,9 @@ class Sim:
 
     def launches(self) -> int:
         return lb_kernel_launches(self.h)
+
+    def step_path(self) -> int:
+        return lb_step_path(self.h)
 
 
 def _echeck(st: int, ens=None) -> int:
