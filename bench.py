@@ -6,8 +6,9 @@ crystal channel, D2Q9, 2048 x 256 sites, walls at top and bottom, periodic in x,
 packed droplets (radius 12-16, hexagonal rows, area fraction 0.8 target), body force
 1e-5, A_h = 0.05, FP32 storage and arithmetic. Metric: MLUPS (million lattice-site
 updates per second), whole job. The 2048 x 256 lattice fits in L2, so L2 is flushed
-(a 512 MB write) before every timed step and each step is timed alone with CUDA
-events on the library's stream.
+before every timed step (a 512 MB write, then a 256 MB read so that the write's dirty
+lines go back to memory before, not during, the step) and each step is timed alone
+with CUDA events on the library's stream.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
                   [--workload channel2d|duct3d|droplet2d] [--precision fp32|fp64]
@@ -74,6 +75,12 @@ WORKLOADS = {
                       gen=lambda nx, ny, nz, seed: inputs.droplet(nx, ny, radius=30),
                       desc="D2Q9 periodic 128x128, one droplet R 30, A_h=0.05"),
 }
+
+# The kernels lb_step launches, by lb_step_path().
+STEP_KERNELS = {0: "fused2d_kernel (one-pass D2Q9 step)",
+                1: "tma2d_kernel (persistent TMA-fed D2Q9 step, one launch per step)",
+                2: "moments_kernel + march3d_kernel (D3Q27 step, two launches)"}
+
 
 # Bytes of state moved per site update (1 read + 1 write): FP64/FP32 populations are
 # 2 components x Q values; FP16-dev stores Q half2 deviations plus a float2 of
@@ -398,11 +405,15 @@ def main(argv=None):
             for k in range(args.steps):
                 if args.flush_mb > 0:
                     flush.fill_(k & 0xFF)  # evict the lattice from L2 before each timed step
+                    # then read half of it back: the write left L2 full of the flush's dirty
+                    # lines, whose write-back would otherwise land in the timed step
+                    flush[: flush.numel() // 2].max()
                 starts[k].record(stream)
                 sim.step(1)
                 ends[k].record(stream)
             torch.cuda.synchronize()
         launches = sim.launches() - launches0
+        path = sim.step_path()
         step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
         total_ms = max_over_ranks(float(sum(step_ms)), dist, "cuda")
         if dist:
@@ -458,8 +469,10 @@ def main(argv=None):
         "dtype": {"fp32": "f32", "fp64": "f64", "fp16dev": "f16 storage / f32 compute"}[args.precision],
         "data": "synthetic",
         "config": {"workload": w["desc"], "sites": N, "precision": args.precision,
-                   "l2": (f"flushed ({args.flush_mb} MB write) before every timed step; each step timed alone"
-                          if args.flush_mb > 0 else "not flushed"),
+                   "l2": (f"flushed before every timed step ({args.flush_mb} MB write, then a "
+                          f"{args.flush_mb // 2} MB read so the flush's dirty lines are written back "
+                          f"before the step); each step timed alone" if args.flush_mb > 0 else "not flushed"),
+                   "step_kernel": STEP_KERNELS.get(path, "?"),
                    "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU",
                    "droplets": fl.meta.get("droplets"),
                    "fraction": fl.meta.get("area_fraction", fl.meta.get("volume_fraction"))},
@@ -467,7 +480,7 @@ def main(argv=None):
                      "frac": round(achieved / peak, 4), "traffic": traffic,
                      "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured"
                      else "fallback 6.8 TB/s",
-                     "kernel": "one lattice step (all step kernels)", "alg_bytes_per_site": bpsite},
+                     "kernel": STEP_KERNELS.get(path, "?"), "alg_bytes_per_site": bpsite},
         "cpu_baseline": cpu,
         "e2e": e2e,
         "gpu_launches": int(launches),

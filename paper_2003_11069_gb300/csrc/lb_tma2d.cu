@@ -204,40 +204,70 @@ tma2d_kernel(const __grid_constant__ CUtensorMap map_pop, Plain<0, float>::Reade
   }
   __syncthreads();
 
-  auto origin = [&](int tile, int& x0, int& y0) {
-    const int by = tile / a.ntx;
-    x0 = (tile - by * a.ntx) * TX;
-    y0 = by * TY;
-  };
-  auto issue = [&](int tile, int b) {  // one thread: TMA load of a fast tile's box into stage b
-    int x0, y0;
-    origin(tile, x0, y0);
+  auto issue = [&](int x0, int y0, int b) {  // one thread: TMA load of a fast tile's box into stage b
     mbar_expect_tx(&bar[b], kBoxBytes);
     tma_load_3d(box(b), &map_pop, x0 - kBOX, y0 - kBOY, 0, &bar[b]);
   };
-  auto tile_fast = [&](int tile) {
-    int x0, y0;
-    origin(tile, x0, y0);
-    return fast_tile(x0, y0, p);
+
+  // This thread's halo cells (tid, tid + NT) and ring cell (tid) are the same in every
+  // tile. Each is packed once into one word: offset in the psi region (or, for the
+  // ring cell, in the probe region) | offset in the population box (or psi region) << 11
+  // | (row relative to the tile + 8) << 22.
+  static_assert(RX * RY <= 2048 && kBPlane <= 2048 && GX * GY <= 2048, "packed offsets");
+  unsigned hcell[2] = {0u, 0u};
+#pragma unroll
+  for (int q = 0; q < 2; ++q) {
+    const int h = tid + q * NT;
+    if (h < NHALO) {
+      int lx, ly;
+      ring_cell<R>(h, lx, ly);
+      hcell[q] = (unsigned)(lx + RX * ly) | ((unsigned)((ly - R + kBOY) * kBX + (lx - R + kBOX)) << 11) |
+                 ((unsigned)(ly - R + 8) << 22);
+    }
+  }
+  unsigned rcell = 0u;
+  if constexpr (S > 0) {
+    if (tid < NRING) {
+      int lx, ly;
+      ring_cell<S>(tid, lx, ly);
+      rcell = (unsigned)(lx + GX * ly) | ((unsigned)((lx + 1) + RX * (ly + 1)) << 11) | ((unsigned)(ly - S + 8) << 22);
+    }
+  }
+  auto lo11 = [](unsigned v) { return (int)(v & 2047u); };
+  auto mid11 = [](unsigned v) { return (int)((v >> 11) & 2047u); };
+  auto row8 = [](unsigned v) { return (int)(v >> 22) - 8; };
+
+  // tiles tile = blockIdx.x + k gridDim.x, row-major over ntx columns, walked with
+  // incremental coordinates (no division in the loop)
+  const int step_x = (int)gridDim.x % a.ntx, step_y = (int)gridDim.x / a.ntx;
+  int bxt = (int)blockIdx.x % a.ntx, byt = (int)blockIdx.x / a.ntx;
+  auto advance = [&](int& bx_, int& by_) {
+    bx_ += step_x;
+    by_ += step_y;
+    if (bx_ >= a.ntx) { bx_ -= a.ntx; ++by_; }
   };
+  int nbx = bxt, nby = byt;
+  advance(nbx, nby);
 
   unsigned phase = 0;    // bit b: parity of the next completion of bar[b]
   unsigned pending = 0;  // bit b: a TMA load into stage b is in flight
-  if ((int)blockIdx.x < a.ntiles && tile_fast(blockIdx.x)) {
-    if (tid == 0) issue(blockIdx.x, 0);
+  if ((int)blockIdx.x < a.ntiles && fast_tile(bxt * TX, byt * TY, p)) {
+    if (tid == 0) issue(bxt * TX, byt * TY, 0);
     pending |= 1u;
   }
 
   int k = 0;
   for (int tile = blockIdx.x; tile < a.ntiles; tile += gridDim.x, ++k) {
     const int b = STAGES == 2 ? (k & 1) : 0;
-    int x0, y0;
-    origin(tile, x0, y0);
+    const int x0 = bxt * TX, y0 = byt * TY;
     const bool fast = fast_tile(x0, y0, p);
-    const int next = tile + gridDim.x;
-    const bool next_fast = next < a.ntiles && tile_fast(next);
+    const int nx0 = nbx * TX, ny0 = nby * TY;
+    const bool next_fast = tile + (int)gridDim.x < a.ntiles && fast_tile(nx0, ny0, p);
+    bxt = nbx;
+    byt = nby;
+    advance(nbx, nby);
     if (STAGES == 2 && next_fast) {  // stage b^1 was last read before this tile
-      if (tid == 0) issue(next, b ^ 1);
+      if (tid == 0) issue(nx0, ny0, b ^ 1);
       pending |= 2u >> b;
     }
     const int x = x0 + tx, y = y0 + ty;
@@ -259,18 +289,25 @@ tma2d_kernel(const __grid_constant__ CUtensorMap map_pop, Plain<0, float>::Reade
       const float* bx = box(b);
       pull_box(bx, (ty + kBOY) * kBX + (tx + kBOX), walls && y == 0, walls && y == ny - 1, fin);
       s_psi[(tx + R) + RX * (ty + R)] = psi_of<kQ, float>(fin, &rho1, &rho2);
-      for (int h = tid; h < NHALO; h += NT) {
-        int lx, ly;
-        ring_cell<R>(h, lx, ly);
-        int gy = y0 - R + ly;
-        if (walls) {
+      // the halo reaches a wall (or the mirror row beyond it) only in the first and last
+      // tile rows of a walled channel
+      const bool wall_halo = walls && (y0 < R + 1 || y0 + TY + R + 1 > ny);
+#pragma unroll
+      for (int q = 0; q < 2; ++q) {
+        if (tid + q * NT >= NHALO) continue;
+        int bo = mid11(hcell[q]);
+        bool bym = false, byp = false;
+        if (wall_halo) {
+          const int gy = y0 + row8(hcell[q]);
           if (gy < -1 || gy > ny) continue;  // beyond a wall only the mirror row is read
-          gy = clampc(gy, ny);
+          const int gyc = clampc(gy, ny);
+          bo += (gyc - gy) * kBX;
+          bym = gyc == 0;
+          byp = gyc == ny - 1;
         }
         float hf[2][kQ];
-        pull_box(bx, (gy - y0 + kBOY) * kBX + (lx - R + kBOX), walls && gy == 0, walls && gy == ny - 1,
-                 hf);
-        s_psi[lx + RX * ly] = psi_of<kQ, float>(hf);
+        pull_box(bx, bo, bym, byp, hf);
+        s_psi[lo11(hcell[q])] = psi_of<kQ, float>(hf);
       }
     } else {
       if (act) {
@@ -283,21 +320,22 @@ tma2d_kernel(const __grid_constant__ CUtensorMap map_pop, Plain<0, float>::Reade
         pull_site<0, float>(f, gx, gy, 0, p, h2);
         s_psi[(tx + R) + RX * (ty + R)] = psi_of<kQ, float>(h2);
       }
-      for (int h = tid; h < NHALO; h += NT) {
-        int lx, ly;
-        ring_cell<R>(h, lx, ly);
-        int gy = y0 - R + ly;
+#pragma unroll
+      for (int q = 0; q < 2; ++q) {
+        if (tid + q * NT >= NHALO) continue;
+        const int sp = lo11(hcell[q]);
+        int gy = y0 + row8(hcell[q]);
         if (walls && (gy < -1 || gy > ny)) continue;
-        const int gx = wrapn(x0 - R + lx, nx);
+        const int gx = wrapn(x0 + sp % RX - R, nx);
         gy = walls ? clampc(gy, ny) : wrapn(gy, ny);
         float hf[2][kQ];
         pull_any<0, float>(f, gx, gy, 0, p, hf);
-        s_psi[lx + RX * ly] = psi_of<kQ, float>(hf);
+        s_psi[sp] = psi_of<kQ, float>(hf);
       }
     }
     __syncthreads();
     if (STAGES == 1 && next_fast) {  // the stage has been read: load the next tile into it
-      if (tid == 0) issue(next, 0);
+      if (tid == 0) issue(nx0, ny0, 0);
       pending |= 1u;
     }
 
@@ -313,15 +351,12 @@ tma2d_kernel(const __grid_constant__ CUtensorMap map_pop, Plain<0, float>::Reade
       if constexpr (S > 0) s_P[(tx + S) + GX * (ty + S)] = g > p.g_th ? make_float2(n0, n1) : make_float2(0.f, 0.f);
     }
     if constexpr (S > 0) {
-      for (int h = tid; h < NRING; h += NT) {
-        int lx, ly;
-        ring_cell<S>(h, lx, ly);
-        const int gy = y0 - S + ly;
-        if (walls && (gy < 0 || gy >= ny)) continue;  // probes stop at walls
+      const int gy = y0 + row8(rcell);
+      if (tid < NRING && !(walls && (gy < 0 || gy >= ny))) {  // probes stop at walls
         float grad[3], n[3];
-        grad_smem<0, float>(s_psi, RX, 0, (lx + 1) + RX * (ly + 1), grad);
+        grad_smem<0, float>(s_psi, RX, 0, mid11(rcell), grad);
         const float gg = M<float>::unit(grad, n);
-        s_P[lx + GX * ly] = gg > p.g_th ? make_float2(n[0], n[1]) : make_float2(0.f, 0.f);
+        s_P[lo11(rcell)] = gg > p.g_th ? make_float2(n[0], n[1]) : make_float2(0.f, 0.f);
       }
     }
     __syncthreads();
