@@ -66,6 +66,8 @@ struct lb_sim {
   void* buf_a;     // the state buffer that fa points to at creation
   TmaMaps maps;    // tensor maps of both state buffers (p.tma)
   int* errflag;    // device word: bit 0 set when a kernel's bounded wait expired
+  int* tile_counter;  // two device ints: tile counters of the TMA step kernel
+  long long tma_launches;
   void* psi;       // order parameter of the streamed state
   double* partials;
   double* result;  // kRedSlots doubles
@@ -100,7 +102,8 @@ lb_status cuda_fail(lb_sim* s, cudaError_t e, const char* what) {
 size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
 
 // The result area holds 16 doubles: the kRedSlots reductions, then, in slot
-// kErrSlot, the kernels' error word (an int).
+// kErrSlot, the kernels' error word (an int), and in slot kErrSlot + 1 the two tile
+// counters of the TMA step kernel (ints).
 constexpr int kErrSlot = 12;
 
 struct Layout {
@@ -164,8 +167,6 @@ lb_status validate(const lb_config* c, HostParams* p, Layout* lay, long long* nb
   p->tma = c->lattice == LB_D2Q9 && c->precision == LB_FP32 && c->nx % 4 == 0 ? 1 : 0;
   if (const char* e = std::getenv("LBNCI_FUSED"))
     if (std::strcmp(e, "classic") == 0) p->tma = 0;
-  p->tma_stages = 1;
-  if (const char* e = std::getenv("LBNCI_TMA_STAGES")) p->tma_stages = std::atoi(e) == 2 ? 2 : 1;
   const int Q = c->lattice == LB_D2Q9 ? 9 : 27;
   (void)Q;
   const Launchers* L = launchers_for(c);
@@ -282,6 +283,7 @@ lb_status lb_create(const lb_config* cfg, lb_sim** out) {
   s->partials = (double*)(base + lay.partials);
   s->result = (double*)(base + lay.result);
   s->errflag = (int*)(s->result + kErrSlot);
+  s->tile_counter = (int*)(s->result + kErrSlot + 1);
   if (s->p.tma) {
     // tensor maps of both state buffers; without the driver's tensor-map encoder the
     // step falls back to the one-pass fused kernel
@@ -341,7 +343,8 @@ lb_status lb_step(lb_sim* s, long long nsteps) {
     int nk = 0;
     cudaError_t e;
     if (s->p.tma) {
-      e = tma2d_step(s->maps, s->fa == s->buf_a ? 0 : 1, s->fa, s->fb, s->errflag, s->p, s->stream);
+      e = tma2d_step(s->maps, s->fa == s->buf_a ? 0 : 1, s->fa, s->fb, s->errflag, s->tile_counter,
+                     s->tma_launches++, s->p, s->stream);
       nk = 1;
     } else {
       e = s->L->step(s->fa, s->fb, s->psi, s->p, s->stream, &nk);

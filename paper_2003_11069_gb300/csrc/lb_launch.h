@@ -17,7 +17,6 @@ struct HostParams {
   int forcing;  // 0: Guo, 1: exact difference method on the dispersed phase
   int d3_kernel;  // D3Q27 collision: 0 marching along z (default), 1 tiled
   int tma;        // 1: D2Q9 FP32 steps run the persistent TMA-fed kernel
-  int tma_stages; // its population stages: 1 (two CTAs per SM, default) or 2 (one CTA per SM)
   double tau, A_s, beta, A_h, h_min, h_max, g_th, G[3];
 };
 
@@ -49,9 +48,11 @@ struct TmaMaps {
 };
 bool tma2d_supported(const HostParams& h);
 cudaError_t tma2d_prepare(TmaMaps* m, const void* fa, const void* fb, const HostParams& h);
-// One step from state `from` (0: buffer A, 1: buffer B) into the other buffer.
-cudaError_t tma2d_step(const TmaMaps& m, int from, const void* fa, void* fb, int* err, const HostParams& h,
-                       cudaStream_t s);
+// One step from state `from` (0: buffer A, 1: buffer B) into the other buffer. counter:
+// two device ints, zero at first use, reserved for this kernel; launch: a count of
+// this sim's launches of it (alternate launches use alternate counters).
+cudaError_t tma2d_step(const TmaMaps& m, int from, const void* fa, void* fb, int* err, int* counter,
+                       long long launch, const HostParams& h, cudaStream_t s);
 
 const Launchers* launchers_fp64(int lattice);
 const Launchers* launchers_fp32(int lattice);

@@ -3,16 +3,21 @@
 // Omega = Omega^(3)[Omega^(1) + Omega^(2)] with the near-contact force of Eq. (near_c);
 // the per-site arithmetic is that of lb_kernels.cuh).
 //
-// One CTA of 512 threads per SM walks 32 x 16 tiles, tile = blockIdx.x + k gridDim.x,
+// Persistent CTAs of 512 threads walk 32 x 16 tiles, tile = blockIdx.x + k gridDim.x,
 // one thread per site. The gradient of psi and the NCI ray search at a site read psi
 // up to R = smax + 1 = 5 sites away, and psi at a site is a sum of the 18 populations
 // streamed into it, so a tile needs the populations of its 48 x 28 neighbourhood
 // (x0-8..x0+39, y0-6..y0+21; the x range is widened to keep TMA coordinates 16-byte
-// aligned). For an interior ("fast") tile one elected thread loads that box, all 18
-// population planes, with a single TMA copy into a double-buffered shared-memory
-// stage one tile ahead, so the copy of the next tile overlaps the arithmetic of this
-// one and costs no load instructions. Everything the step reads then comes from
-// shared memory:
+// aligned). One elected thread loads that box, all 18 population planes, with a
+// single TMA copy into the CTA's shared-memory stage; two CTAs share an SM, and a CTA
+// issues its next tile's copy as soon as this tile has read the stage, so copies
+// overlap the other CTA's arithmetic and cost no load instructions. After its first two
+// tiles a CTA takes tiles from an atomic counter, which evens out tiles of uneven cost
+// (interface density, periodic edges) across CTAs. Box cells
+// beyond the lattice along a periodic axis arrive as zeros and are replaced by their
+// periodic images with plain loads (first and last tile columns, and the first and
+// last tile rows without walls). Everything the step reads then comes from shared
+// memory:
 //   phase 1: pull the own site (kept in registers) and every halo cell from the box,
 //            psi into shared memory;
 //   phase 2: unit normal and |grad psi| of the own site (registers) and of the ring of
@@ -20,9 +25,8 @@
 //            |grad psi| <= g_th, so a probe needs one load and one sign test);
 //   phase 3: NCI ray search, Guo velocity, BGK + source + perturbation, recolouring,
 //            coalesced stores of the 18 new populations.
-// Tiles whose neighbourhood wraps around the lattice (the first and last tile columns,
-// the first and last tile rows of a periodic y axis) or that are ragged take a slow
-// path with the same phases 2-3 but pulls from global memory.
+// Ragged tiles use the same path: an own position beyond the lattice holds the psi of
+// its periodic image (or, beyond a wall, of its mirror) and stores nothing.
 //
 // Every wait on an mbarrier is bounded (about one second); on expiry the kernel
 // records a flag that the host reports, waits (bounded again) for its own copies
@@ -45,17 +49,16 @@ constexpr int kBoxFloats = 2 * kQ * kBPlane;
 constexpr unsigned kBoxBytes = kBoxFloats * 4;
 constexpr int kBoxStride = (kBoxBytes + 1023) / 1024 * 1024;
 
-// Shared-memory layout (bytes from a 1024-aligned base): STAGES population boxes,
-// psi of the tile and its halo, probe normals, two mbarriers.
+// Shared-memory layout (bytes from a 1024-aligned base): the population box, psi of
+// the tile and its halo, probe normals, the mbarrier and the next tile's index.
 constexpr int kRmax = kMaxProbe + 1;
 constexpr int kPsiBytes = (TX + 2 * kRmax) * (TY + 2 * kRmax) * 4;           // (32+10) x (16+10) floats
 constexpr int kPBytes = (TX + 2 * kMaxProbe) * (TY + 2 * kMaxProbe) * 8;     // (32+8) x (16+8) float2
-template <int STAGES> __host__ __device__ constexpr int off_psi() { return STAGES * kBoxStride; }
-template <int STAGES> __host__ __device__ constexpr int off_P() { return off_psi<STAGES>() + kPsiBytes; }
-template <int STAGES> __host__ __device__ constexpr int off_bar() { return off_P<STAGES>() + kPBytes; }
-template <int STAGES> __host__ __device__ constexpr int smem_bytes() { return off_bar<STAGES>() + 16 + 1024; }  // + alignment slack
-static_assert(smem_bytes<2>() <= 227 * 1024, "shared memory (two stages, one CTA per SM)");
-static_assert(2 * (smem_bytes<1>() + 1024) <= 228 * 1024, "shared memory (one stage, two CTAs per SM)");
+constexpr int kOffPsi = kBoxStride;
+constexpr int kOffP = kOffPsi + kPsiBytes;
+constexpr int kOffBar = kOffP + kPBytes;
+constexpr int kSmemBytes = kOffBar + 16 + 1024;  // + alignment slack
+static_assert(2 * (kSmemBytes + 1024) <= 228 * 1024, "shared memory: two CTAs per SM");
 
 constexpr unsigned long long kWaitLimitNs = 1000000000ull;
 
@@ -116,6 +119,8 @@ constexpr float kMagic = 12582912.0f;
 constexpr unsigned kMagicBits = 0x4B400000u;
 __device__ __forceinline__ unsigned probe_bits(float s, float v) { return __float_as_uint(fmaf(s, v, kMagic)); }
 
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
 // Halo cell h of a ring of width W around the 32 x 16 tile, in region coordinates
 // (region = (32 + 2W) x (16 + 2W)): two bands of W full rows, then the W-wide sides.
 template <int W>
@@ -133,14 +138,6 @@ __device__ __forceinline__ void ring_cell(int h, int& lx, int& ly) {
     lx = col < W ? col : col + TX;
     ly = W + row;
   }
-}
-
-// True when the tile is full and its population box needs no periodic wrap (walls
-// may cut it: rows beyond a wall are never read as sources).
-__device__ __forceinline__ bool fast_tile(int x0, int y0, const StepT<float>& p) {
-  if (x0 < TX || x0 + kBX - kBOX > p.nx) return false;
-  if (p.wall_y) return y0 + TY <= p.ny;
-  return y0 >= kBOY && y0 + kBY - kBOY <= p.ny;
 }
 
 // Pull the 2 Q populations of the site at box position c (plane offsets kBPlane);
@@ -166,17 +163,29 @@ __device__ __forceinline__ void pull_box(const float* __restrict__ bx, int c, bo
   }
 }
 
+// Stores the collision's populations plane by plane: each plane's base address is
+// the same for all threads, so a store needs only the site's offset.
+struct PlaneWriter {
+  float* __restrict__ f;
+  unsigned N;
+  template <int I>
+  __device__ __forceinline__ void put(unsigned site, float a, float b, float, float) const {
+    (f + (size_t)I * N)[site] = a;
+    (f + (size_t)(kQ + I) * N)[site] = b;
+  }
+  __device__ __forceinline__ void put_rho(unsigned, float, float) const {}
+};
+
 struct TmaArgs {
-  int* err;  // bit 0: a TMA wait expired
+  int* err;      // bit 0: a TMA wait expired
+  int* counter;  // two tile counters, used by alternate launches (zero before first use)
+  int parity;    // this launch uses counter[parity] and zeroes counter[parity ^ 1]
   int ntx, ntiles;
 };
 
-// STAGES = 2: one CTA per SM (128 registers a thread), the next tile's box is loaded
-// into the other stage while this tile is computed. STAGES = 1: two CTAs per SM (64
-// registers), the next tile's box is loaded as soon as this tile's phase 1 has read
-// the stage, and the other CTA computes meanwhile.
-template <int S, bool EDM, int STAGES>
-__global__ void __launch_bounds__(NT, 3 - STAGES)
+// Two CTAs per SM (64 registers a thread).
+template <int S, bool EDM>
+__global__ void __launch_bounds__(NT, 2)
 tma2d_kernel(const __grid_constant__ CUtensorMap map_pop, Plain<0, float>::Reader f, Plain<0, float>::Writer fout,
              StepT<float> p, TmaArgs a) {
   constexpr int R = S + 1;  // psi halo
@@ -186,10 +195,11 @@ tma2d_kernel(const __grid_constant__ CUtensorMap map_pop, Plain<0, float>::Reade
   extern __shared__ unsigned char smem_dyn[];
   unsigned char* sm = reinterpret_cast<unsigned char*>(
       (reinterpret_cast<uintptr_t>(smem_dyn) + 1023) & ~static_cast<uintptr_t>(1023));
-  auto box = [&](int b) { return reinterpret_cast<float*>(sm + b * kBoxStride); };
-  float* s_psi = reinterpret_cast<float*>(sm + off_psi<STAGES>());
-  float2* s_P = reinterpret_cast<float2*>(sm + off_P<STAGES>());
-  unsigned long long* bar = reinterpret_cast<unsigned long long*>(sm + off_bar<STAGES>());
+  float* const bx = reinterpret_cast<float*>(sm);
+  float* s_psi = reinterpret_cast<float*>(sm + kOffPsi);
+  float2* s_P = reinterpret_cast<float2*>(sm + kOffP);
+  unsigned long long* bar = reinterpret_cast<unsigned long long*>(sm + kOffBar);
+  int* s_next = reinterpret_cast<int*>(sm + kOffBar + 8);
 
   const int tid = threadIdx.x;
   const int tx = tid & (TX - 1), ty = tid >> 5;
@@ -198,15 +208,16 @@ tma2d_kernel(const __grid_constant__ CUtensorMap map_pop, Plain<0, float>::Reade
 
   if (tid == 0) {
     mbar_init(&bar[0], 1);
-    mbar_init(&bar[1], 1);
+    if (blockIdx.x == 0) a.counter[a.parity ^ 1] = 0;  // the next launch's counter
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<unsigned long long>(&map_pop)) : "memory");
   }
   __syncthreads();
 
-  auto issue = [&](int x0, int y0, int b) {  // one thread: TMA load of a fast tile's box into stage b
-    mbar_expect_tx(&bar[b], kBoxBytes);
-    tma_load_3d(box(b), &map_pop, x0 - kBOX, y0 - kBOY, 0, &bar[b]);
+  auto issue = [&](int tile) {  // one thread: TMA load of a tile's box into the stage
+    const int by = tile / a.ntx;
+    mbar_expect_tx(&bar[0], kBoxBytes);
+    tma_load_3d(bx, &map_pop, (tile - by * a.ntx) * TX - kBOX, by * TY - kBOY, 0, &bar[0]);
   };
 
   // This thread's halo cells (tid, tid + NT) and ring cell (tid) are the same in every
@@ -237,106 +248,114 @@ tma2d_kernel(const __grid_constant__ CUtensorMap map_pop, Plain<0, float>::Reade
   auto mid11 = [](unsigned v) { return (int)((v >> 11) & 2047u); };
   auto row8 = [](unsigned v) { return (int)(v >> 22) - 8; };
 
-  // tiles tile = blockIdx.x + k gridDim.x, row-major over ntx columns, walked with
-  // incremental coordinates (no division in the loop)
-  const int step_x = (int)gridDim.x % a.ntx, step_y = (int)gridDim.x / a.ntx;
-  int bxt = (int)blockIdx.x % a.ntx, byt = (int)blockIdx.x / a.ntx;
-  auto advance = [&](int& bx_, int& by_) {
-    bx_ += step_x;
-    by_ += step_y;
-    if (bx_ >= a.ntx) { bx_ -= a.ntx; ++by_; }
-  };
-  int nbx = bxt, nby = byt;
-  advance(nbx, nby);
-
-  unsigned phase = 0;    // bit b: parity of the next completion of bar[b]
-  unsigned pending = 0;  // bit b: a TMA load into stage b is in flight
-  if ((int)blockIdx.x < a.ntiles && fast_tile(bxt * TX, byt * TY, p)) {
-    if (tid == 0) issue(bxt * TX, byt * TY, 0);
-    pending |= 1u;
+  unsigned phase = 0;  // parity of the next completion of the mbarrier
+  bool pending = false;  // a TMA load into the stage is in flight
+  int tile = blockIdx.x;
+  if (tile < a.ntiles) {
+    if (tid == 0) issue(tile);
+    pending = true;
   }
 
-  int k = 0;
-  for (int tile = blockIdx.x; tile < a.ntiles; tile += gridDim.x, ++k) {
-    const int b = STAGES == 2 ? (k & 1) : 0;
-    const int x0 = bxt * TX, y0 = byt * TY;
-    const bool fast = fast_tile(x0, y0, p);
-    const int nx0 = nbx * TX, ny0 = nby * TY;
-    const bool next_fast = tile + (int)gridDim.x < a.ntiles && fast_tile(nx0, ny0, p);
-    bxt = nbx;
-    byt = nby;
-    advance(nbx, nby);
-    if (STAGES == 2 && next_fast) {  // stage b^1 was last read before this tile
-      if (tid == 0) issue(nx0, ny0, b ^ 1);
-      pending |= 2u >> b;
+  // Thread 0 reserves tiles one iteration ahead, so the counter's round trip is never
+  // waited for: at each tile it publishes the tile reserved before (read by all after
+  // phase 1) and reserves the one after it. The first two tiles of a CTA are blockIdx.x
+  // and blockIdx.x + gridDim.x; the counter hands out tiles from 2 gridDim.x on.
+  int reserved = tile + (int)gridDim.x;  // the second tile is static, the counter starts at 2 gridDim.x
+  while (tile < a.ntiles) {
+    if (tid == 0) {
+      *s_next = reserved;
+      reserved = 2 * (int)gridDim.x + atomicAdd(&a.counter[a.parity], 1);
     }
+    const int by_ = tile / a.ntx;
+    const int x0 = (tile - by_ * a.ntx) * TX, y0 = by_ * TY;
     const int x = x0 + tx, y = y0 + ty;
     const bool act = x < nx && y < ny;
     float fin[2][kQ];
     float rho1 = 0.f, rho2 = 0.f;
 
+    // Box cells beyond the lattice along a periodic axis (always x; y without walls)
+    // arrive from the copy as zeros and are overwritten with their periodic images
+    // (plain loads, all 18 planes of a cell in flight together): out-of-range columns
+    // [0, cl) and [cr, kBX) (all rows), then out-of-range rows [0, rt) and [rb, kBY)
+    // (in-range columns). Beyond a wall nothing is read (bounce-back).
+    const int cl = x0 < kBOX ? kBOX - x0 : 0, cr = min(kBX, nx - x0 + kBOX);
+    const int rt = !walls && y0 < kBOY ? kBOY - y0 : 0, rb = walls ? kBY : min(kBY, ny - y0 + kBOY);
+    const int ncol = cl + (kBX - cr);
+    const int nfix = ncol * kBY + (rt + (kBY - rb)) * (cr - cl);
+    auto fix_cell = [&](int e, int& c, int& r) {  // row-major: neighbouring threads, neighbouring columns
+      if (e < ncol * kBY) {
+        r = e / ncol;
+        const int j = e - r * ncol;
+        c = j < cl ? j : cr + (j - cl);
+      } else {
+        const int e2 = e - ncol * kBY, w = cr - cl;
+        const int j = e2 / w;
+        c = cl + (e2 - j * w);
+        r = j < rt ? j : rb + (j - rt);
+      }
+    };
+    auto fix_load = [&](int c, int r, float v[2 * kQ]) {
+      const unsigned src = (unsigned)(wrapn(x0 - kBOX + c, nx) + nx * wrapn(y0 - kBOY + r, ny));
+      static_for<2 * kQ>([&](auto I) {
+        constexpr int pl = decltype(I)::value;
+        v[pl] = __ldg(f.f + (size_t)pl * f.N + src);
+      });
+    };
+
     // ---- phase 1: own populations (registers) and psi of the tile and its halo
-    if (fast) {
-      const bool ok = mbar_wait(&bar[b], (phase >> b) & 1u);
-      if (__syncthreads_or(!ok)) {
-        if (tid == 0) atomicOr(a.err, 1);
-        for (int q = 0; q < 2; ++q)  // wait (bounded) for every copy still in flight
-          if ((pending >> q) & 1u) mbar_wait(&bar[q], (phase >> q) & 1u);
-        return;
+    const bool ok = mbar_wait(&bar[0], phase);
+    if (__syncthreads_or(!ok)) {
+      if (tid == 0) atomicOr(a.err, 1);
+      if (pending) mbar_wait(&bar[0], phase);  // wait (bounded) for the copy still in flight
+      return;
+    }
+    phase ^= 1u;
+    pending = false;
+    if (nfix > 0) {
+      for (int e = tid; e < nfix; e += NT) {
+        int c, r;
+        fix_cell(e, c, r);
+        float v[2 * kQ];
+        fix_load(c, r, v);
+        static_for<2 * kQ>([&](auto I) {
+          constexpr int pl = decltype(I)::value;
+          bx[pl * kBPlane + r * kBX + c] = v[pl];
+        });
       }
-      phase ^= 1u << b;
-      pending &= ~(1u << b);
-      const float* bx = box(b);
-      pull_box(bx, (ty + kBOY) * kBX + (tx + kBOX), walls && y == 0, walls && y == ny - 1, fin);
+      fence_async_smem();  // these generic writes precede the next TMA write of the stage
+      __syncthreads();
+    }
+    {  // an own position beyond a ragged edge holds the psi of the site it wraps to (x,
+       // periodic y: the box holds the image) or of its mirror across the wall
+      const int gy = walls ? clampc(y, ny) : y;
+      pull_box(bx, (gy - y0 + kBOY) * kBX + (tx + kBOX), walls && gy == 0, walls && gy == ny - 1, fin);
       s_psi[(tx + R) + RX * (ty + R)] = psi_of<kQ, float>(fin, &rho1, &rho2);
-      // the halo reaches a wall (or the mirror row beyond it) only in the first and last
-      // tile rows of a walled channel
-      const bool wall_halo = walls && (y0 < R + 1 || y0 + TY + R + 1 > ny);
+    }
+    // the halo reaches a wall (or the mirror row beyond it) only in the first and last
+    // tile rows of a walled channel
+    const bool wall_halo = walls && (y0 < R + 1 || y0 + TY + R + 1 > ny);
 #pragma unroll
-      for (int q = 0; q < 2; ++q) {
-        if (tid + q * NT >= NHALO) continue;
-        int bo = mid11(hcell[q]);
-        bool bym = false, byp = false;
-        if (wall_halo) {
-          const int gy = y0 + row8(hcell[q]);
-          if (gy < -1 || gy > ny) continue;  // beyond a wall only the mirror row is read
-          const int gyc = clampc(gy, ny);
-          bo += (gyc - gy) * kBX;
-          bym = gyc == 0;
-          byp = gyc == ny - 1;
-        }
-        float hf[2][kQ];
-        pull_box(bx, bo, bym, byp, hf);
-        s_psi[lo11(hcell[q])] = psi_of<kQ, float>(hf);
+    for (int q = 0; q < 2; ++q) {
+      if (tid + q * NT >= NHALO) continue;
+      int bo = mid11(hcell[q]);
+      bool bym = false, byp = false;
+      if (wall_halo) {
+        const int gy = y0 + row8(hcell[q]);
+        if (gy < -1 || gy > ny) continue;  // beyond a wall only the mirror row is read
+        const int gyc = clampc(gy, ny);
+        bo += (gyc - gy) * kBX;
+        bym = gyc == 0;
+        byp = gyc == ny - 1;
       }
-    } else {
-      if (act) {
-        pull_any<0, float>(f, x, y, 0, p, fin);
-        s_psi[(tx + R) + RX * (ty + R)] = psi_of<kQ, float>(fin, &rho1, &rho2);
-      } else {  // an own position beyond a ragged edge holds the psi of the site it wraps to
-        const int gx = wrapn(x, nx);
-        const int gy = walls ? clampc(y, ny) : wrapn(y, ny);
-        float h2[2][kQ];
-        pull_site<0, float>(f, gx, gy, 0, p, h2);
-        s_psi[(tx + R) + RX * (ty + R)] = psi_of<kQ, float>(h2);
-      }
-#pragma unroll
-      for (int q = 0; q < 2; ++q) {
-        if (tid + q * NT >= NHALO) continue;
-        const int sp = lo11(hcell[q]);
-        int gy = y0 + row8(hcell[q]);
-        if (walls && (gy < -1 || gy > ny)) continue;
-        const int gx = wrapn(x0 + sp % RX - R, nx);
-        gy = walls ? clampc(gy, ny) : wrapn(gy, ny);
-        float hf[2][kQ];
-        pull_any<0, float>(f, gx, gy, 0, p, hf);
-        s_psi[sp] = psi_of<kQ, float>(hf);
-      }
+      float hf[2][kQ];
+      pull_box(bx, bo, bym, byp, hf);
+      s_psi[lo11(hcell[q])] = psi_of<kQ, float>(hf);
     }
     __syncthreads();
-    if (STAGES == 1 && next_fast) {  // the stage has been read: load the next tile into it
-      if (tid == 0) issue(nx0, ny0, 0);
-      pending |= 1u;
+    const int next = *s_next;
+    if (next < a.ntiles) {  // the stage has been read: load the next tile into it
+      if (tid == 0) issue(next);
+      pending = true;
     }
 
     // ---- phase 2: unit normal and |grad psi|; own site in registers, every cell
@@ -396,8 +415,10 @@ tma2d_kernel(const __grid_constant__ CUtensorMap map_pop, Plain<0, float>::Reade
 #pragma unroll
       for (int c = 0; c < 3; ++c) u[c] = __fdividef(j[c] + 0.5f * F[c], rho);
       const float m[3] = {-n0, -n1, 0.f};
-      collide_store<0, float, Plain<0, float>::Writer, EDM>(fin, rho1, rho2, j, u, F, g, m, p, fout, x + nx * y);
+      collide_store<0, float, PlaneWriter, EDM>(fin, rho1, rho2, j, u, F, g, m, p, PlaneWriter{fout.f, fout.N},
+                                                 x + nx * y);
     }
+    tile = next;
   }
 }
 
@@ -449,33 +470,27 @@ bool encode_pop(CUtensorMap* m, const void* base, const HostParams& h) {
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-template <int S, bool EDM, int STAGES>
-cudaError_t launch_v(const CUtensorMap& map, const void* fa, void* fb, int* err, const StepT<float>& p, int num_sms,
-                     cudaStream_t s) {
+template <int S, bool EDM>
+cudaError_t launch_v(const CUtensorMap& map, const void* fa, void* fb, int* err, int* counter, int parity,
+                     const StepT<float>& p, int num_sms, cudaStream_t s) {
   static bool configured = false;
-  constexpr int smem = smem_bytes<STAGES>();
   if (!configured) {
-    cudaError_t e =
-        cudaFuncSetAttribute(tma2d_kernel<S, EDM, STAGES>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    cudaError_t e = cudaFuncSetAttribute(tma2d_kernel<S, EDM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         kSmemBytes);
     if (e != cudaSuccess) return e;
     configured = true;
   }
   TmaArgs a;
   a.err = err;
+  a.counter = counter;
+  a.parity = parity & 1;
   a.ntx = (p.nx + TX - 1) / TX;
   a.ntiles = a.ntx * ((p.ny + TY - 1) / TY);
-  const int slots = num_sms * (3 - STAGES);  // resident CTAs
+  const int slots = 2 * num_sms;  // resident CTAs
   const int grid = a.ntiles < slots ? a.ntiles : slots;
-  tma2d_kernel<S, EDM, STAGES><<<grid, NT, smem, s>>>(map, Plain<0, float>::reader(fa, (unsigned)p.N),
-                                                      Plain<0, float>::writer(fb, (unsigned)p.N), p, a);
+  tma2d_kernel<S, EDM><<<grid, NT, kSmemBytes, s>>>(map, Plain<0, float>::reader(fa, (unsigned)p.N),
+                                                    Plain<0, float>::writer(fb, (unsigned)p.N), p, a);
   return cudaGetLastError();
-}
-
-template <int S, bool EDM>
-cudaError_t launch_s(const CUtensorMap& map, const void* fa, void* fb, int* err, const StepT<float>& p, int num_sms,
-                     int stages, cudaStream_t s) {
-  return stages == 2 ? launch_v<S, EDM, 2>(map, fa, fb, err, p, num_sms, s)
-                     : launch_v<S, EDM, 1>(map, fa, fb, err, p, num_sms, s);
 }
 
 }  // namespace
@@ -488,17 +503,17 @@ cudaError_t tma2d_prepare(TmaMaps* m, const void* fa, const void* fb, const Host
   return encode_pop(&maps[0], fa, h) && encode_pop(&maps[1], fb, h) ? cudaSuccess : cudaErrorInvalidValue;
 }
 
-cudaError_t tma2d_step(const TmaMaps& m, int from, const void* fa, void* fb, int* err, const HostParams& h,
-                       cudaStream_t s) {
+cudaError_t tma2d_step(const TmaMaps& m, int from, const void* fa, void* fb, int* err, int* counter,
+                       long long launch, const HostParams& h, cudaStream_t s) {
   const StepT<float> p = to_step(h);
   const CUtensorMap& map = reinterpret_cast<const CUtensorMap*>(m.bytes)[from];
   const bool edm = h.forcing == 1;
-  const int st = h.tma_stages;
+  const int par = (int)(launch & 1);
   if (h.smax == 0)
-    return edm ? launch_s<0, true>(map, fa, fb, err, p, h.num_sms, st, s)
-               : launch_s<0, false>(map, fa, fb, err, p, h.num_sms, st, s);
-  return edm ? launch_s<kMaxProbe, true>(map, fa, fb, err, p, h.num_sms, st, s)
-             : launch_s<kMaxProbe, false>(map, fa, fb, err, p, h.num_sms, st, s);
+    return edm ? launch_v<0, true>(map, fa, fb, err, counter, par, p, h.num_sms, s)
+               : launch_v<0, false>(map, fa, fb, err, counter, par, p, h.num_sms, s);
+  return edm ? launch_v<kMaxProbe, true>(map, fa, fb, err, counter, par, p, h.num_sms, s)
+             : launch_v<kMaxProbe, false>(map, fa, fb, err, counter, par, p, h.num_sms, s);
 }
 
 }  // namespace lbnci
