@@ -7,8 +7,10 @@
 //                mirror of the wall plane);
 //   (n, g) ring  2 smax + 1 planes of the unit normal n = -grad psi/|grad psi| and
 //                |grad psi| on the column plus a halo of smax, each computed once.
-// Iteration q loads psi plane q, computes (n, g) of plane q - 1, and collides plane
-// q - smax - 1, whose NCI rays find every probe's (n, g) in the ring. The psi array is
+// Iteration q computes (n, g) of plane q - 1 and collides plane q - smax - 1, whose NCI
+// rays find every probe's (n, g) in the ring; the loads of psi plane q + 1 are issued
+// at the start of iteration q and stored into the ring at its end, so their latency
+// overlaps the iteration's arithmetic. The psi array is
 // read about three times per site instead of once per halo cell of a 3-D tile, and no
 // gradient is recomputed along a ray. Arithmetic is that of the other step kernels
 // (same helpers and expression order), so FP64 rounds like the oracle.
@@ -73,19 +75,43 @@ march3d_kernel(typename ST::Reader f, typename ST::Writer fout, const typename S
   auto ring3 = [](int q) { int r = q % 3; return r < 0 ? r + 3 : r; };
   auto ringW = [W](int q) { int r = q % W; return r < 0 ? r + W : r; };
 
-  for (int q = zs - R; q < ze + R; ++q) {
-    // psi plane q (beyond a z wall only the first plane is read: the mirror of the wall plane)
-    const bool q_needed = !p.wall_z || (q >= -1 && q <= p.nz);
-    if (q_needed) {
-      const int gz = p.wall_z ? clampc(q, p.nz) : wrapn(q, p.nz);
-      T* dst = s_psi + ring3(q) * RXY;
-      for_region(tid, NT, RX, RY, 1, [&](int c, int lx, int ly, int) {
+  // psi plane q (beyond a z wall only the first plane is read: the mirror of the wall
+  // plane): this thread's cells c = tid + k NT, loaded into registers, then stored.
+  constexpr int kPsiPer = 4;  // cells of a psi plane per thread: RX RY <= kPsiPer NT for smax <= 4
+  auto psi_load = [&](int q, T v[kPsiPer]) {
+    if (p.wall_z && (q < -1 || q > p.nz)) return;
+    const int gz = p.wall_z ? clampc(q, p.nz) : wrapn(q, p.nz);
+#pragma unroll
+    for (int k = 0; k < kPsiPer; ++k) {
+      const int c = tid + k * NT;
+      if (c < RXY) {
+        const int ly = c / RX, lx = c - ly * RX;
         const int gx = wrapn(x0 - R + lx, p.nx);
         const int gy = p.wall_y ? clampc(y0 - R + ly, p.ny) : wrapn(y0 - R + ly, p.ny);
-        dst[c] = psi[gx + p.nx * (gy + p.ny * gz)];
-      });
+        v[k] = psi[gx + p.nx * (gy + p.ny * gz)];
+      }
     }
-    __syncthreads();
+  };
+  auto psi_store = [&](int q, const T v[kPsiPer]) {
+    if (p.wall_z && (q < -1 || q > p.nz)) return;
+    T* dst = s_psi + ring3(q) * RXY;
+#pragma unroll
+    for (int k = 0; k < kPsiPer; ++k) {
+      const int c = tid + k * NT;
+      if (c < RXY) dst[c] = v[k];
+    }
+  };
+  {
+    T v[kPsiPer];
+    psi_load(zs - R, v);
+    psi_store(zs - R, v);
+  }
+  __syncthreads();
+
+  for (int q = zs - R; q < ze + R; ++q) {
+    T vnext[kPsiPer];
+    const bool more = q + 1 < ze + R;
+    if (more) psi_load(q + 1, vnext);
     // (n, |grad psi|) of plane q - 1 on the column and a halo of smax
     const int qg = q - 1;
     if (qg >= zs - S && qg < ze + S && (!p.wall_z || (qg >= 0 && qg < p.nz))) {
@@ -155,6 +181,9 @@ march3d_kernel(typename ST::Reader f, typename ST::Writer fout, const typename S
       const T m[3] = {-n0, -n1, -n2};
       collide_store<1, T, typename ST::Writer, EDM>(fin, rho1, rho2, j, u, F, g, m, p, fout, idx);
     }
+    // plane q + 1 replaces plane q - 2, whose last reader was the (n, g) pass above
+    if (more) psi_store(q + 1, vnext);
+    __syncthreads();
   }
 }
 

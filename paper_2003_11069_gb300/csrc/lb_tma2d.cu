@@ -214,10 +214,35 @@ tma2d_kernel(const __grid_constant__ CUtensorMap map_pop, Plain<0, float>::Reade
   }
   __syncthreads();
 
+  // Tile numbering: the tiles of the first and last tile columns (whose boxes need
+  // periodic images patched in, the slowest tiles) come first, two per tile row, then
+  // the others row by row. The first tiles are the CTAs' static ones, so the counter's
+  // tiles even out the extra cost.
+  const int nty = a.ntiles / a.ntx;
+  const int nedge = a.ntx > 2 ? 2 * nty : 0;
+  const int rowlen = nedge > 0 ? a.ntx - 2 : a.ntx;  // tiles per row after the edge tiles
+  const float rrow = 1.0f / (float)rowlen;
+  auto origin = [&](int t, int& x0_, int& y0_) {
+    int bxx, byy;
+    if (t < nedge) {
+      byy = t >> 1;
+      bxx = (t & 1) ? a.ntx - 1 : 0;
+    } else {
+      // u / rowlen by a float reciprocal, corrected to the exact quotient (u < 2^24)
+      const int u = t - nedge;
+      byy = (int)((float)u * rrow);
+      if (byy * rowlen > u) --byy;
+      else if ((byy + 1) * rowlen <= u) ++byy;
+      bxx = (nedge > 0 ? 1 : 0) + (u - byy * rowlen);
+    }
+    x0_ = bxx * TX;
+    y0_ = byy * TY;
+  };
   auto issue = [&](int tile) {  // one thread: TMA load of a tile's box into the stage
-    const int by = tile / a.ntx;
+    int tx0, ty0;
+    origin(tile, tx0, ty0);
     mbar_expect_tx(&bar[0], kBoxBytes);
-    tma_load_3d(bx, &map_pop, (tile - by * a.ntx) * TX - kBOX, by * TY - kBOY, 0, &bar[0]);
+    tma_load_3d(bx, &map_pop, tx0 - kBOX, ty0 - kBOY, 0, &bar[0]);
   };
 
   // This thread's halo cells (tid, tid + NT) and ring cell (tid) are the same in every
@@ -266,8 +291,8 @@ tma2d_kernel(const __grid_constant__ CUtensorMap map_pop, Plain<0, float>::Reade
       *s_next = reserved;
       reserved = 2 * (int)gridDim.x + atomicAdd(&a.counter[a.parity], 1);
     }
-    const int by_ = tile / a.ntx;
-    const int x0 = (tile - by_ * a.ntx) * TX, y0 = by_ * TY;
+    int x0, y0;
+    origin(tile, x0, y0);
     const int x = x0 + tx, y = y0 + ty;
     const bool act = x < nx && y < ny;
     float fin[2][kQ];
