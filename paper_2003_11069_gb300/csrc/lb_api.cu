@@ -210,7 +210,9 @@ lb_status run_fields(lb_sim* s, const FieldOut& outs) {
   int flag = 0;
   std::memcpy(&flag, &s->host_result[kErrSlot], sizeof(flag));
   if (flag != 0)
-    return fail(s, LB_ECUDA, "a step kernel gave up waiting for its TMA copies (flag %d); the state is invalid", flag);
+    return fail(s, LB_ECUDA, "%s (flag %d); the state is invalid",
+                (flag & 1) ? "a step kernel gave up waiting for its TMA copies"
+                           : "a step kernel found its shared memory misaligned for TMA and did nothing", flag);
   return LB_OK;
 }
 

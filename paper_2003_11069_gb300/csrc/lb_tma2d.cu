@@ -29,8 +29,9 @@
 // its periodic image (or, beyond a wall, of its mirror) and stores nothing.
 //
 // Every wait on an mbarrier is bounded (about one second); on expiry the kernel
-// records a flag that the host reports, waits (bounded again) for its own copies
-// in flight, and returns.
+// records a flag (bit 0) that the host reports, waits (bounded again) for its own
+// copies in flight, and returns. A shared-memory base that is not 1024-byte aligned
+// sets bit 1 before any copy is issued.
 #include <cuda.h>
 #include <cuda_runtime.h>
 #include <cudaTypedefs.h>
@@ -57,8 +58,8 @@ constexpr int kPBytes = (TX + 2 * kMaxProbe) * (TY + 2 * kMaxProbe) * 8;     // 
 constexpr int kOffPsi = kBoxStride;
 constexpr int kOffP = kOffPsi + kPsiBytes;
 constexpr int kOffBar = kOffP + kPBytes;
-constexpr int kSmemBytes = kOffBar + 16 + 1024;  // + alignment slack
-static_assert(2 * (kSmemBytes + 1024) <= 228 * 1024, "shared memory: two CTAs per SM");
+constexpr int kSmemBytes = kOffBar + 16;
+static_assert(2 * (kSmemBytes + 1024) <= 228 * 1024, "shared memory: two CTAs per SM (1 KB reserved each)");
 
 constexpr unsigned long long kWaitLimitNs = 1000000000ull;
 
@@ -176,6 +177,60 @@ struct PlaneWriter {
   __device__ __forceinline__ void put_rho(unsigned, float, float) const {}
 };
 
+// The FP32 Guo collision of lb_kernels.cuh (BGK + source + perturbation, then
+// recolouring) for D2Q9, evaluated per pair of opposite directions (i, opposite(i)):
+// with c.u, c.F, c.m changing sign between the two, the bracket
+//   B_i = K0 + c.u (3 omega rho + 4.5 omega rho c.u + 9 guo c.F) + 3 guo c.F + pamp (c.m)^2
+// splits into a part even in c, E = K0 + 4.5 omega rho (c.u)^2 + 9 guo (c.u)(c.F) +
+// pamp (c.m)^2, and an odd part O = 3 omega rho c.u + 3 guo c.F, B = E + O and E - O,
+// and the recolouring term changes sign; each pair shares those products.
+template <typename WR>
+__device__ __forceinline__ void collide_pairs_d2q9(const float fin[2][kQ], float rho1, float rho2, const float j[3],
+                                                   const float u[3], const float F[3], float g, const float m[3],
+                                                   const StepT<float>& p, const WR& fout, unsigned idx) {
+  (void)j;
+  const float rho = rho1 + rho2;
+  const float uF = u[0] * F[0] + u[1] * F[1];
+  const float uu = u[0] * u[0] + u[1] * u[1];
+  const float seg = __fdividef(p.beta * rho1 * rho2, rho);
+  const float pamp = p.pamp * g;
+  const float c1 = __fdividef(rho1, rho);
+  const float orho = p.omega * rho;
+  const float K0 = orho * (1.0f - 1.5f * uu) - 3.0f * p.guo * uF - pamp * (1.0f / 3.0f);
+  const float a3 = 3.0f * orho, a45 = 4.5f * orho, g3 = 3.0f * p.guo, g9 = 9.0f * p.guo;
+  const float om1 = 1.0f - p.omega;
+  float s1 = 0.f, s2 = 0.f;
+  static_for<kQ>([&](auto I) {
+    constexpr int i = decltype(I)::value;
+    constexpr int o = opposite(i);
+    if constexpr (i > 0 && i < o) {
+      constexpr float w = float(Lattice<0>::w(i));
+      constexpr int ix = cc(i, 0), iy = cc(i, 1);
+      constexpr float wl = float(Lattice<0>::w(i) / (speed2(i) == 1 ? 1.0 : 1.4142135623730951));
+      auto dotc = [&](const float v[3]) {
+        float r = 0.f;
+        if constexpr (ix == 1) r += v[0]; else if constexpr (ix == -1) r -= v[0];
+        if constexpr (iy == 1) r += v[1]; else if constexpr (iy == -1) r -= v[1];
+        return r;
+      };
+      const float cu = dotc(u), cF = dotc(F), cm = dotc(m);
+      const float E = fmaf(pamp, cm * cm, fmaf(g9, cu * cF, fmaf(a45, cu * cu, K0)));
+      const float O = fmaf(g3, cF, a3 * cu);
+      const float fsp = fmaf(w, E + O, om1 * (fin[0][i] + fin[1][i]));
+      const float fsm = fmaf(w, E - O, om1 * (fin[0][o] + fin[1][o]));
+      const float rc = (seg * wl) * cm;
+      const float o1p = fmaf(c1, fsp, rc), o1m = fmaf(c1, fsm, -rc);
+      const float o2p = fsp - o1p, o2m = fsm - o1m;
+      s1 += o1p + o1m;
+      s2 += o2p + o2m;
+      fout.template put<i>(idx, o1p, o2p, rho1, rho2);
+      fout.template put<o>(idx, o1m, o2m, rho1, rho2);
+    }
+  });
+  fout.template put<0>(idx, rho1 - s1, rho2 - s2, rho1, rho2);
+  fout.put_rho(idx, rho1, rho2);
+}
+
 struct TmaArgs {
   int* err;      // bit 0: a TMA wait expired
   int* counter;  // two tile counters, used by alternate launches (zero before first use)
@@ -192,9 +247,10 @@ tma2d_kernel(const __grid_constant__ CUtensorMap map_pop, Plain<0, float>::Reade
   constexpr int RX = TX + 2 * R, RY = TY + 2 * R;
   constexpr int GX = TX + 2 * S, GY = TY + 2 * S;
   constexpr int NHALO = RX * RY - NT, NRING = GX * GY - NT;
-  extern __shared__ unsigned char smem_dyn[];
-  unsigned char* sm = reinterpret_cast<unsigned char*>(
-      (reinterpret_cast<uintptr_t>(smem_dyn) + 1023) & ~static_cast<uintptr_t>(1023));
+  // The dynamic shared memory starts the CTA's shared window (no static shared
+  // memory here), so it is 1024-byte aligned; checked below. Indexing it directly
+  // keeps every access a shared-memory access with 32-bit addresses.
+  extern __shared__ __align__(1024) unsigned char sm[];
   float* const bx = reinterpret_cast<float*>(sm);
   float* s_psi = reinterpret_cast<float*>(sm + kOffPsi);
   float2* s_P = reinterpret_cast<float2*>(sm + kOffP);
@@ -206,6 +262,10 @@ tma2d_kernel(const __grid_constant__ CUtensorMap map_pop, Plain<0, float>::Reade
   const bool walls = p.wall_y != 0;
   const int nx = p.nx, ny = p.ny;
 
+  if (smem_u32(sm) & 1023u) {  // TMA destinations need the alignment: report, do nothing
+    if (tid == 0) atomicOr(a.err, 2);
+    return;
+  }
   if (tid == 0) {
     mbar_init(&bar[0], 1);
     if (blockIdx.x == 0) a.counter[a.parity ^ 1] = 0;  // the next launch's counter
@@ -440,8 +500,11 @@ tma2d_kernel(const __grid_constant__ CUtensorMap map_pop, Plain<0, float>::Reade
 #pragma unroll
       for (int c = 0; c < 3; ++c) u[c] = __fdividef(j[c] + 0.5f * F[c], rho);
       const float m[3] = {-n0, -n1, 0.f};
-      collide_store<0, float, PlaneWriter, EDM>(fin, rho1, rho2, j, u, F, g, m, p, PlaneWriter{fout.f, fout.N},
-                                                 x + nx * y);
+      if constexpr (EDM)
+        collide_store<0, float, PlaneWriter, EDM>(fin, rho1, rho2, j, u, F, g, m, p, PlaneWriter{fout.f, fout.N},
+                                                   x + nx * y);
+      else
+        collide_pairs_d2q9(fin, rho1, rho2, j, u, F, g, m, p, PlaneWriter{fout.f, fout.N}, (unsigned)(x + nx * y));
     }
     tile = next;
   }
