@@ -294,6 +294,7 @@ def run_ensemble(args, w, lbnci, torch, prec, ws, rank, local, dist):
                                  stream=stream.cuda_stream) for m in members]
     N = sum(m.nx * m.ny for m in members)
     ens = lbnci.Ensemble(cfgs)
+    n_tma = sum(1 for mv in ens.members if mv.step_path() == lbnci.LB_PATH_TMA2D)
     for mv, m in zip(ens.members, members):
         mv.init_fields(m.fields.rho1, m.fields.rho2)
     spt = ens.tune()
@@ -333,7 +334,12 @@ def run_ensemble(args, w, lbnci, torch, prec, ws, rank, local, dist):
         for sm in sims:
             sm.close()
     ens.close()
-    return N, total_ms, launches, clk.summary(), obs, {"tile": f"32x{8 * spt}", "tune_ms_per_step":
+    kern = []
+    if n_tma:
+        kern.append(f"tma2d_kernel batched over {n_tma} members")
+    if n_tma < len(members):
+        kern.append(f"fused2d_batch_kernel over {len(members) - n_tma} members (tile 32x{8 * spt})")
+    return N, total_ms, launches, clk.summary(), obs, {"step_kernels": "; ".join(kern), "tune_ms_per_step":
                                                       {"32x16": round(t32x16, 4), "32x32": round(t32x32, 4)},
                                                       "one_launch_per_member_ms_per_step": seq_ms}
 
@@ -514,7 +520,7 @@ def main_ensemble(args, w, lbnci, torch, ws, rank, local, dist):
                    "speedup_vs_one_launch_per_member": round(seq / ms_per_step, 3) if seq else None},
         "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                      "frac": round(achieved / peak, 4), "traffic": None,
-                     "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)", "kernel": "fused2d_batch_kernel",
+                     "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)", "kernel": extra["step_kernels"],
                      "alg_bytes_per_site": bpsite},
         "cpu_baseline": None, "e2e": None, "gpu_launches": int(launches), "clocks": clocks,
         "flow_rate_disp": {"min": min(o["flow_rate_disp"] for o in obs), "max": max(o["flow_rate_disp"] for o in obs)},

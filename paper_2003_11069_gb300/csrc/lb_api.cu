@@ -67,7 +67,7 @@ struct lb_sim {
   TmaMaps maps;    // tensor maps of both state buffers (p.tma)
   int* errflag;    // device word: bit 0 set when a kernel's bounded wait expired
   int* tile_counter;  // two device ints: tile counters of the TMA step kernel
-  long long tma_launches;
+  const int* ens_flag;  // member of an ensemble stepped by the batched TMA kernel: its error word
   void* psi;       // order parameter of the streamed state
   double* partials;
   double* result;  // kRedSlots doubles
@@ -209,6 +209,12 @@ lb_status run_fields(lb_sim* s, const FieldOut& outs) {
   if (e != cudaSuccess) return cuda_fail(s, e, "stream synchronize");
   int flag = 0;
   std::memcpy(&flag, &s->host_result[kErrSlot], sizeof(flag));
+  if (s->ens_flag) {  // the batched step reports into its ensemble's word
+    int ef = 0;
+    e = cudaMemcpy(&ef, s->ens_flag, sizeof(ef), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(s, e, "ensemble flag copy");
+    flag |= ef;
+  }
   if (flag != 0)
     return fail(s, LB_ECUDA, "%s (flag %d); the state is invalid",
                 (flag & 1) ? "a step kernel gave up waiting for its TMA copies"
@@ -345,8 +351,8 @@ lb_status lb_step(lb_sim* s, long long nsteps) {
     int nk = 0;
     cudaError_t e;
     if (s->p.tma) {
-      e = tma2d_step(s->maps, s->fa == s->buf_a ? 0 : 1, s->fa, s->fb, s->errflag, s->tile_counter,
-                     s->tma_launches++, s->p, s->stream);
+      e = tma2d_step(s->maps, s->fa == s->buf_a ? 0 : 1, s->fa, s->fb, s->errflag, s->tile_counter, s->p,
+                     s->stream);
       nk = 1;
     } else {
       e = s->L->step(s->fa, s->fb, s->psi, s->p, s->stream, &nk);
@@ -613,9 +619,14 @@ struct lb_ensemble {
   bool own_stream;
   std::vector<lb_sim*> members;
   void* base;              // one allocation holding every member's workspace
-  std::vector<unsigned char> host_members;  // BatchMember records (host copy)
+  std::vector<int> cls;    // members stepped by the one-pass batch kernel (FP64, FP16-dev, nx % 4 != 0)
+  std::vector<int> tma;    // members stepped by the batched TMA kernel (FP32, nx % 4 == 0)
+  std::vector<unsigned char> host_members;  // BatchMember records of cls (host copy)
   void* d_members;         // device copy of the member records
-  int* d_tile0;            // first tile of every member, n + 1 entries
+  int* d_tile0;            // first tile of every cls member, cls.size() + 1 entries
+  void* d_tma;             // TmaMember records of tma (device)
+  int* d_tma_flags;        // batched TMA kernel: error word, two tile counters
+  int tma_tiles, tma_smax;
   int spt;                 // tile shape: 32 x (8 spt) sites per block
   int total_tiles;
   int smax_max;
@@ -645,19 +656,37 @@ lb_status ecuda(lb_ensemble* e, cudaError_t c, const char* what) {
 
 // Tile offsets for the current tile shape, uploaded to the device.
 lb_status ens_layout(lb_ensemble* e) {
-  std::vector<int> t0(e->n + 1, 0);
-  for (int m = 0; m < e->n; ++m) t0[m + 1] = t0[m] + e->L->batch_tiles(e->members[m]->p, e->spt);
-  e->total_tiles = t0[e->n];
-  cudaError_t c = cudaMemcpyAsync(e->d_tile0, t0.data(), sizeof(int) * (e->n + 1), cudaMemcpyHostToDevice, e->stream);
+  const int nc = (int)e->cls.size();
+  std::vector<int> t0(nc + 1, 0);
+  for (int k = 0; k < nc; ++k) t0[k + 1] = t0[k] + e->L->batch_tiles(e->members[e->cls[k]]->p, e->spt);
+  e->total_tiles = t0[nc];
+  cudaError_t c = cudaMemcpyAsync(e->d_tile0, t0.data(), sizeof(int) * (nc + 1), cudaMemcpyHostToDevice, e->stream);
   if (c == cudaSuccess) c = cudaStreamSynchronize(e->stream);
   if (c != cudaSuccess) return ecuda(e, c, "tile table upload");
   if (e->graph_ok) { cudaGraphExecDestroy(e->graph); e->graph_ok = false; }
   return LB_OK;
 }
 
-cudaError_t ens_launch(lb_ensemble* e, int parity) {
-  return e->L->batch_step(e->d_members, e->d_tile0, e->n, e->total_tiles, parity, e->spt, e->smax_max,
+// The one-pass batch kernel over the cls members (none: nothing launched).
+cudaError_t ens_launch_cls(lb_ensemble* e, int parity, int* nk) {
+  if (e->cls.empty()) return cudaSuccess;
+  ++*nk;
+  return e->L->batch_step(e->d_members, e->d_tile0, (int)e->cls.size(), e->total_tiles, parity, e->spt, e->smax_max,
                           e->members[0]->p.forcing == LB_FORCE_EDM_DISPERSED, e->stream);
+}
+
+// One step of every member: the batched TMA kernel over the tma members, the one-pass
+// batch kernel over the others.
+cudaError_t ens_launch(lb_ensemble* e, int parity, int* nk) {
+  if (!e->tma.empty()) {
+    ++*nk;
+    cudaError_t c = tma2d_batch_step(e->d_tma, (int)e->tma.size(), e->tma_tiles, parity, e->d_tma_flags,
+                                     e->d_tma_flags + 1, e->tma_smax,
+                                     e->members[0]->p.forcing == LB_FORCE_EDM_DISPERSED,
+                                     e->members[0]->p.num_sms, e->stream);
+    if (c != cudaSuccess) return c;
+  }
+  return ens_launch_cls(e, parity, nk);
 }
 
 }  // namespace
@@ -716,14 +745,34 @@ lb_status lb_ensemble_create(const lb_config* cfgs, int n, lb_ensemble** out) {
     e->members.push_back(s);
     e->smax_max = std::max(e->smax_max, s->p.smax);
   }
+  for (int m = 0; m < n; ++m) (e->members[m]->p.tma ? e->tma : e->cls).push_back(m);
   const size_t rec = e->L->batch_member_bytes;
-  e->host_members.resize(rec * n);
-  for (int m = 0; m < n; ++m)
-    e->L->batch_fill(e->host_members.data() + rec * m, e->members[m]->p, e->members[m]->fa, e->members[m]->fb);
-  c = cudaMalloc(&e->d_members, rec * n);
-  if (c == cudaSuccess) c = cudaMalloc((void**)&e->d_tile0, sizeof(int) * (n + 1));
+  const int nc = (int)e->cls.size(), nt = (int)e->tma.size();
+  e->host_members.resize(rec * (nc > 0 ? nc : 1));
+  for (int k = 0; k < nc; ++k) {
+    lb_sim* s = e->members[e->cls[k]];
+    e->L->batch_fill(e->host_members.data() + rec * k, s->p, s->fa, s->fb);
+  }
+  c = cudaMalloc(&e->d_members, rec * (nc > 0 ? nc : 1));
+  if (c == cudaSuccess) c = cudaMalloc((void**)&e->d_tile0, sizeof(int) * (nc + 1));
   if (c == cudaSuccess)
-    c = cudaMemcpyAsync(e->d_members, e->host_members.data(), rec * n, cudaMemcpyHostToDevice, e->stream);
+    c = cudaMemcpyAsync(e->d_members, e->host_members.data(), rec * (nc > 0 ? nc : 1), cudaMemcpyHostToDevice,
+                        e->stream);
+  if (c == cudaSuccess && nt > 0) {
+    const size_t trec = tma2d_member_bytes();
+    std::vector<unsigned char> ht(trec * nt);
+    for (int k = 0; k < nt; ++k) {
+      lb_sim* s = e->members[e->tma[k]];
+      e->tma_tiles += tma2d_member_fill(ht.data() + trec * k, s->maps, s->p, s->fa, s->fb, e->tma_tiles);
+      e->tma_smax = std::max(e->tma_smax, s->p.smax);
+    }
+    c = cudaMalloc(&e->d_tma, trec * nt);
+    if (c == cudaSuccess) c = cudaMalloc((void**)&e->d_tma_flags, 4 * sizeof(int));
+    if (c == cudaSuccess) c = cudaMemcpyAsync(e->d_tma, ht.data(), trec * nt, cudaMemcpyHostToDevice, e->stream);
+    if (c == cudaSuccess) c = cudaMemsetAsync(e->d_tma_flags, 0, 4 * sizeof(int), e->stream);
+    if (c == cudaSuccess) c = cudaStreamSynchronize(e->stream);
+    for (int k = 0; k < nt; ++k) e->members[e->tma[k]]->ens_flag = e->d_tma_flags;
+  }
   if (c != cudaSuccess) {
     cudaGetLastError();
     lb_ensemble_destroy(e);
@@ -747,10 +796,11 @@ lb_status lb_ensemble_step(lb_ensemble* e, long long nsteps) {
   if (nsteps < 0) return efail(e, LB_EINVAL, "nsteps must be >= 0");
   cudaError_t c;
   long long left = nsteps;
+  int nk = 0;  // kernels of one step
   if (left > 0 && e->parity == 1) {  // back to parity 0, where the two-step graph starts
-    c = ens_launch(e, 1);
+    c = ens_launch(e, 1, &nk);
     if (c != cudaSuccess) return ecuda(e, c, "ensemble step launch");
-    ++e->launches;
+    e->launches += nk;
     e->parity = 0;
     --left;
   }
@@ -758,8 +808,9 @@ lb_status lb_ensemble_step(lb_ensemble* e, long long nsteps) {
     cudaGraph_t g;
     c = cudaStreamBeginCapture(e->stream, cudaStreamCaptureModeThreadLocal);
     if (c == cudaSuccess) {
-      cudaError_t c1 = ens_launch(e, 0);
-      cudaError_t c2 = ens_launch(e, 1);
+      int nk2 = 0;
+      cudaError_t c1 = ens_launch(e, 0, &nk2);
+      cudaError_t c2 = ens_launch(e, 1, &nk2);
       c = cudaStreamEndCapture(e->stream, &g);
       if (c == cudaSuccess && (c1 != cudaSuccess || c2 != cudaSuccess)) c = c1 != cudaSuccess ? c1 : c2;
       if (c == cudaSuccess) {
@@ -770,15 +821,17 @@ lb_status lb_ensemble_step(lb_ensemble* e, long long nsteps) {
     if (c != cudaSuccess) return ecuda(e, c, "ensemble graph capture");
     e->graph_ok = true;
   }
+  const int per_step = (e->tma.empty() ? 0 : 1) + (e->cls.empty() ? 0 : 1);
   for (; left >= 2; left -= 2) {
     c = cudaGraphLaunch(e->graph, e->stream);
     if (c != cudaSuccess) return ecuda(e, c, "ensemble graph launch");
-    e->launches += 2;
+    e->launches += 2 * per_step;
   }
   if (left == 1) {
-    c = ens_launch(e, 0);
+    nk = 0;
+    c = ens_launch(e, 0, &nk);
     if (c != cudaSuccess) return ecuda(e, c, "ensemble step launch");
-    ++e->launches;
+    e->launches += nk;
     e->parity = 1;
   }
   // the members' current state buffer follows the parity
@@ -801,13 +854,21 @@ lb_status lb_ensemble_tune(lb_ensemble* e, int* spt_out) {
   if (c != cudaSuccess) return ecuda(e, c, "event creation");
   int best = e->spt;
   float best_ms = 1e30f;
+  if (e->cls.empty()) {  // every member runs the TMA kernel: no tile shape to choose
+    cudaEventDestroy(t0);
+    cudaEventDestroy(t1);
+    e->tune_ms[0] = e->tune_ms[1] = 0.f;
+    if (spt_out) *spt_out = e->spt;
+    return LB_OK;
+  }
   for (int k = 0; k < 2 && c == cudaSuccess; ++k) {
     e->spt = shapes[k];
     lb_status st = ens_layout(e);
     if (st != LB_OK) { cudaEventDestroy(t0); cudaEventDestroy(t1); return st; }
-    c = ens_launch(e, e->parity);  // warm-up
+    int nk = 0;
+    c = ens_launch_cls(e, e->parity, &nk);  // warm-up
     if (c == cudaSuccess) c = cudaEventRecord(t0, e->stream);
-    for (int r = 0; r < 5 && c == cudaSuccess; ++r) c = ens_launch(e, e->parity);
+    for (int r = 0; r < 5 && c == cudaSuccess; ++r) c = ens_launch_cls(e, e->parity, &nk);
     if (c == cudaSuccess) c = cudaEventRecord(t1, e->stream);
     if (c == cudaSuccess) c = cudaEventSynchronize(t1);
     float ms = 0.f;
@@ -843,6 +904,8 @@ void lb_ensemble_destroy(lb_ensemble* e) {
   if (e->graph_ok) cudaGraphExecDestroy(e->graph);
   for (lb_sim* s : e->members) lb_destroy(s);
   if (e->d_members) cudaFree(e->d_members);
+  if (e->d_tma) cudaFree(e->d_tma);
+  if (e->d_tma_flags) cudaFree(e->d_tma_flags);
   if (e->d_tile0) cudaFree(e->d_tile0);
   if (e->base) cudaFree(e->base);
   if (e->own_stream) cudaStreamDestroy(e->stream);

@@ -49,10 +49,18 @@ struct TmaMaps {
 bool tma2d_supported(const HostParams& h);
 cudaError_t tma2d_prepare(TmaMaps* m, const void* fa, const void* fb, const HostParams& h);
 // One step from state `from` (0: buffer A, 1: buffer B) into the other buffer. counter:
-// two device ints, zero at first use, reserved for this kernel; launch: a count of
-// this sim's launches of it (alternate launches use alternate counters).
+// two device ints, zero at first use, reserved for this sim's steps (alternate states
+// use alternate counters).
 cudaError_t tma2d_step(const TmaMaps& m, int from, const void* fa, void* fb, int* err, int* counter,
-                       long long launch, const HostParams& h, cudaStream_t s);
+                       const HostParams& h, cudaStream_t s);
+// Batched TMA step over the members of an ensemble: a device table of member records
+// (tma2d_member_bytes each, filled on the host by tma2d_member_fill, which returns the
+// member's tile count; tile0 = tiles of the members before it). Members read their
+// buffer `state` and write the other; counter as for tma2d_step, reserved for the batch.
+size_t tma2d_member_bytes();
+int tma2d_member_fill(void* dst, const TmaMaps& m, const HostParams& h, void* buf0, void* buf1, int tile0);
+cudaError_t tma2d_batch_step(const void* members, int nmem, int total_tiles, int state, int* err, int* counter,
+                             int smax_max, int edm, int num_sms, cudaStream_t s);
 
 const Launchers* launchers_fp64(int lattice);
 const Launchers* launchers_fp32(int lattice);

@@ -36,6 +36,8 @@
 #include <cuda_runtime.h>
 #include <cudaTypedefs.h>
 
+#include <cstring>
+
 #include "lb_kernels.cuh"
 #include "lb_launch.h"
 
@@ -58,7 +60,7 @@ constexpr int kPBytes = (TX + 2 * kMaxProbe) * (TY + 2 * kMaxProbe) * 8;     // 
 constexpr int kOffPsi = kBoxStride;
 constexpr int kOffP = kOffPsi + kPsiBytes;
 constexpr int kOffBar = kOffP + kPBytes;
-constexpr int kSmemBytes = kOffBar + 16;
+constexpr int kSmemBytes = kOffBar + 256;  // mbarrier, next tile (4 ints), 2 x StepT<float>
 static_assert(2 * (kSmemBytes + 1024) <= 228 * 1024, "shared memory: two CTAs per SM (1 KB reserved each)");
 
 constexpr unsigned long long kWaitLimitNs = 1000000000ull;
@@ -231,18 +233,61 @@ __device__ __forceinline__ void collide_pairs_d2q9(const float fin[2][kQ], float
   fout.put_rho(idx, rho1, rho2);
 }
 
+// One lattice of a batched step (device memory): its population-box maps for state
+// buffer 0 and 1, step parameters, the two buffers and its tiles' place in the batch.
+struct alignas(64) TmaMember {
+  CUtensorMap map[2];
+  StepT<float> p;
+  float* buf[2];
+  int ntx, ntiles, tile0;
+};
+
 struct TmaArgs {
-  int* err;      // bit 0: a TMA wait expired
+  int* err;      // bit 0: a TMA wait expired; bit 1: misaligned shared memory
   int* counter;  // two tile counters, used by alternate launches (zero before first use)
   int parity;    // this launch uses counter[parity] and zeroes counter[parity ^ 1]
   int ntx, ntiles;
+  const TmaMember* members;  // batched step: the member table
+  int nmem;
+  int state;     // batched step: members read buf[state] and write buf[state ^ 1]
 };
 
-// Two CTAs per SM (64 registers a thread).
-template <int S, bool EDM>
+// Tile t of a lattice with ntx tile columns and ntiles tiles -> its origin. Numbering:
+// the tiles of the first and last tile columns (whose boxes need periodic images
+// patched in, the slowest tiles) come first, two per tile row, then the others row by
+// row. The first tiles are the CTAs' static ones, so the counter's tiles even out the
+// extra cost.
+__device__ __forceinline__ void tile_origin(int t, int ntx, int ntiles, int& x0, int& y0) {
+  const int nty = ntiles / ntx;
+  const int nedge = ntx > 2 ? 2 * nty : 0;
+  int bxx, byy;
+  if (t < nedge) {
+    byy = t >> 1;
+    bxx = (t & 1) ? ntx - 1 : 0;
+  } else {
+    // u / rowlen by a float reciprocal, corrected to the exact quotient (u < 2^22)
+    const int rowlen = nedge > 0 ? ntx - 2 : ntx;
+    const int u = t - nedge;
+    byy = (int)((float)u * __frcp_rn((float)rowlen));
+    if (byy * rowlen > u) --byy;
+    else if ((byy + 1) * rowlen <= u) ++byy;
+    bxx = (nedge > 0 ? 1 : 0) + (u - byy * rowlen);
+  }
+  x0 = bxx * TX;
+  y0 = byy * TY;
+}
+
+// A tile's lattice (member of a batch; 0 for a single lattice) and origin.
+struct TileLoc {
+  int m, x0, y0;
+};
+
+// Two CTAs per SM (64 registers a thread). BATCH: tiles of all members of a batch,
+// each member's parameters copied into shared memory for its tiles.
+template <int S, bool EDM, bool BATCH>
 __global__ void __launch_bounds__(NT, 2)
-tma2d_kernel(const __grid_constant__ CUtensorMap map_pop, Plain<0, float>::Reader f, Plain<0, float>::Writer fout,
-             StepT<float> p, TmaArgs a) {
+tma2d_kernel(const __grid_constant__ CUtensorMap map_pop, Plain<0, float>::Reader f_one,
+             Plain<0, float>::Writer fout_one, StepT<float> p_one, TmaArgs a) {
   constexpr int R = S + 1;  // psi halo
   constexpr int RX = TX + 2 * R, RY = TY + 2 * R;
   constexpr int GX = TX + 2 * S, GY = TY + 2 * S;
@@ -255,12 +300,11 @@ tma2d_kernel(const __grid_constant__ CUtensorMap map_pop, Plain<0, float>::Reade
   float* s_psi = reinterpret_cast<float*>(sm + kOffPsi);
   float2* s_P = reinterpret_cast<float2*>(sm + kOffP);
   unsigned long long* bar = reinterpret_cast<unsigned long long*>(sm + kOffBar);
-  int* s_next = reinterpret_cast<int*>(sm + kOffBar + 8);
+  int* s_next = reinterpret_cast<int*>(sm + kOffBar + 8);  // next tile, its member and origin
+  StepT<float>* s_p = reinterpret_cast<StepT<float>*>(sm + kOffBar + 32);  // [2], BATCH
 
   const int tid = threadIdx.x;
   const int tx = tid & (TX - 1), ty = tid >> 5;
-  const bool walls = p.wall_y != 0;
-  const int nx = p.nx, ny = p.ny;
 
   if (smem_u32(sm) & 1023u) {  // TMA destinations need the alignment: report, do nothing
     if (tid == 0) atomicOr(a.err, 2);
@@ -270,39 +314,31 @@ tma2d_kernel(const __grid_constant__ CUtensorMap map_pop, Plain<0, float>::Reade
     mbar_init(&bar[0], 1);
     if (blockIdx.x == 0) a.counter[a.parity ^ 1] = 0;  // the next launch's counter
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<unsigned long long>(&map_pop)) : "memory");
+    if (!BATCH)
+      asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<unsigned long long>(&map_pop)) : "memory");
   }
   __syncthreads();
 
-  // Tile numbering: the tiles of the first and last tile columns (whose boxes need
-  // periodic images patched in, the slowest tiles) come first, two per tile row, then
-  // the others row by row. The first tiles are the CTAs' static ones, so the counter's
-  // tiles even out the extra cost.
-  const int nty = a.ntiles / a.ntx;
-  const int nedge = a.ntx > 2 ? 2 * nty : 0;
-  const int rowlen = nedge > 0 ? a.ntx - 2 : a.ntx;  // tiles per row after the edge tiles
-  const float rrow = 1.0f / (float)rowlen;
-  auto origin = [&](int t, int& x0_, int& y0_) {
-    int bxx, byy;
-    if (t < nedge) {
-      byy = t >> 1;
-      bxx = (t & 1) ? a.ntx - 1 : 0;
+  auto locate = [&](int t) {
+    TileLoc l{0, 0, 0};
+    if constexpr (BATCH) {
+      int lo = 0, hi = a.nmem - 1;
+      while (lo < hi) {  // last member whose first tile is <= t
+        const int mid = (lo + hi + 1) >> 1;
+        if (a.members[mid].tile0 <= t) lo = mid; else hi = mid - 1;
+      }
+      l.m = lo;
+      const TmaMember& mb = a.members[lo];
+      tile_origin(t - mb.tile0, mb.ntx, mb.ntiles, l.x0, l.y0);
     } else {
-      // u / rowlen by a float reciprocal, corrected to the exact quotient (u < 2^24)
-      const int u = t - nedge;
-      byy = (int)((float)u * rrow);
-      if (byy * rowlen > u) --byy;
-      else if ((byy + 1) * rowlen <= u) ++byy;
-      bxx = (nedge > 0 ? 1 : 0) + (u - byy * rowlen);
+      tile_origin(t, a.ntx, a.ntiles, l.x0, l.y0);
     }
-    x0_ = bxx * TX;
-    y0_ = byy * TY;
+    return l;
   };
-  auto issue = [&](int tile) {  // one thread: TMA load of a tile's box into the stage
-    int tx0, ty0;
-    origin(tile, tx0, ty0);
+  auto issue = [&](const TileLoc& l) {  // one thread: TMA load of a tile's box into the stage
+    const CUtensorMap* map = BATCH ? &a.members[l.m].map[a.state] : &map_pop;
     mbar_expect_tx(&bar[0], kBoxBytes);
-    tma_load_3d(bx, &map_pop, tx0 - kBOX, ty0 - kBOY, 0, &bar[0]);
+    tma_load_3d(bx, map, l.x0 - kBOX, l.y0 - kBOY, 0, &bar[0]);
   };
 
   // This thread's halo cells (tid, tid + NT) and ring cell (tid) are the same in every
@@ -333,11 +369,12 @@ tma2d_kernel(const __grid_constant__ CUtensorMap map_pop, Plain<0, float>::Reade
   auto mid11 = [](unsigned v) { return (int)((v >> 11) & 2047u); };
   auto row8 = [](unsigned v) { return (int)(v >> 22) - 8; };
 
-  unsigned phase = 0;  // parity of the next completion of the mbarrier
+  unsigned phase = 0;    // parity of the next completion of the mbarrier
   bool pending = false;  // a TMA load into the stage is in flight
   int tile = blockIdx.x;
+  TileLoc cur = locate(tile < a.ntiles ? tile : 0);
   if (tile < a.ntiles) {
-    if (tid == 0) issue(tile);
+    if (tid == 0) issue(cur);
     pending = true;
   }
 
@@ -345,47 +382,28 @@ tma2d_kernel(const __grid_constant__ CUtensorMap map_pop, Plain<0, float>::Reade
   // waited for: at each tile it publishes the tile reserved before (read by all after
   // phase 1) and reserves the one after it. The first two tiles of a CTA are blockIdx.x
   // and blockIdx.x + gridDim.x; the counter hands out tiles from 2 gridDim.x on.
-  int reserved = tile + (int)gridDim.x;  // the second tile is static, the counter starts at 2 gridDim.x
+  int reserved = tile + (int)gridDim.x;
+  int k = 0;
   while (tile < a.ntiles) {
     if (tid == 0) {
-      *s_next = reserved;
+      s_next[0] = reserved;
+      if (reserved < a.ntiles) {
+        const TileLoc l = locate(reserved);
+        s_next[1] = l.m;
+        s_next[2] = l.x0;
+        s_next[3] = l.y0;
+      }
       reserved = 2 * (int)gridDim.x + atomicAdd(&a.counter[a.parity], 1);
     }
-    int x0, y0;
-    origin(tile, x0, y0);
-    const int x = x0 + tx, y = y0 + ty;
-    const bool act = x < nx && y < ny;
+    const int slot = k & 1;
+    if constexpr (BATCH) {  // this tile's member parameters (read after the next barrier)
+      static_assert(sizeof(StepT<float>) % 4 == 0 && sizeof(StepT<float>) / 4 <= NT, "parameter copy");
+      if (tid < (int)(sizeof(StepT<float>) / 4))
+        reinterpret_cast<int*>(&s_p[slot])[tid] = reinterpret_cast<const int*>(&a.members[cur.m].p)[tid];
+    }
+    const int x0 = cur.x0, y0 = cur.y0;
     float fin[2][kQ];
     float rho1 = 0.f, rho2 = 0.f;
-
-    // Box cells beyond the lattice along a periodic axis (always x; y without walls)
-    // arrive from the copy as zeros and are overwritten with their periodic images
-    // (plain loads, all 18 planes of a cell in flight together): out-of-range columns
-    // [0, cl) and [cr, kBX) (all rows), then out-of-range rows [0, rt) and [rb, kBY)
-    // (in-range columns). Beyond a wall nothing is read (bounce-back).
-    const int cl = x0 < kBOX ? kBOX - x0 : 0, cr = min(kBX, nx - x0 + kBOX);
-    const int rt = !walls && y0 < kBOY ? kBOY - y0 : 0, rb = walls ? kBY : min(kBY, ny - y0 + kBOY);
-    const int ncol = cl + (kBX - cr);
-    const int nfix = ncol * kBY + (rt + (kBY - rb)) * (cr - cl);
-    auto fix_cell = [&](int e, int& c, int& r) {  // row-major: neighbouring threads, neighbouring columns
-      if (e < ncol * kBY) {
-        r = e / ncol;
-        const int j = e - r * ncol;
-        c = j < cl ? j : cr + (j - cl);
-      } else {
-        const int e2 = e - ncol * kBY, w = cr - cl;
-        const int j = e2 / w;
-        c = cl + (e2 - j * w);
-        r = j < rt ? j : rb + (j - rt);
-      }
-    };
-    auto fix_load = [&](int c, int r, float v[2 * kQ]) {
-      const unsigned src = (unsigned)(wrapn(x0 - kBOX + c, nx) + nx * wrapn(y0 - kBOY + r, ny));
-      static_for<2 * kQ>([&](auto I) {
-        constexpr int pl = decltype(I)::value;
-        v[pl] = __ldg(f.f + (size_t)pl * f.N + src);
-      });
-    };
 
     // ---- phase 1: own populations (registers) and psi of the tile and its halo
     const bool ok = mbar_wait(&bar[0], phase);
@@ -396,12 +414,46 @@ tma2d_kernel(const __grid_constant__ CUtensorMap map_pop, Plain<0, float>::Reade
     }
     phase ^= 1u;
     pending = false;
+    const StepT<float>& p = BATCH ? s_p[slot] : p_one;
+    Plain<0, float>::Reader f = f_one;
+    Plain<0, float>::Writer fout = fout_one;
+    if constexpr (BATCH) {
+      f = Plain<0, float>::reader(a.members[cur.m].buf[a.state], (unsigned)p.N);
+      fout = Plain<0, float>::writer(a.members[cur.m].buf[a.state ^ 1], (unsigned)p.N);
+    }
+    const bool walls = p.wall_y != 0;
+    const int nx = p.nx, ny = p.ny;
+    const int x = x0 + tx, y = y0 + ty;
+    const bool act = x < nx && y < ny;
+
+    // Box cells beyond the lattice along a periodic axis (always x; y without walls)
+    // arrive from the copy as zeros and are overwritten with their periodic images
+    // (plain loads, all 18 planes of a cell in flight together): out-of-range columns
+    // [0, cl) and [cr, kBX) (all rows), then out-of-range rows [0, rt) and [rb, kBY)
+    // (in-range columns). Beyond a wall nothing is read (bounce-back).
+    const int cl = x0 < kBOX ? kBOX - x0 : 0, cr = min(kBX, nx - x0 + kBOX);
+    const int rt = !walls && y0 < kBOY ? kBOY - y0 : 0, rb = walls ? kBY : min(kBY, ny - y0 + kBOY);
+    const int ncol = cl + (kBX - cr);
+    const int nfix = ncol * kBY + (rt + (kBY - rb)) * (cr - cl);
     if (nfix > 0) {
       for (int e = tid; e < nfix; e += NT) {
-        int c, r;
-        fix_cell(e, c, r);
+        int c, r;  // row-major: neighbouring threads, neighbouring columns
+        if (e < ncol * kBY) {
+          r = e / ncol;
+          const int j = e - r * ncol;
+          c = j < cl ? j : cr + (j - cl);
+        } else {
+          const int e2 = e - ncol * kBY, w = cr - cl;
+          const int j = e2 / w;
+          c = cl + (e2 - j * w);
+          r = j < rt ? j : rb + (j - rt);
+        }
+        const unsigned src = (unsigned)(wrapn(x0 - kBOX + c, nx) + nx * wrapn(y0 - kBOY + r, ny));
         float v[2 * kQ];
-        fix_load(c, r, v);
+        static_for<2 * kQ>([&](auto I) {
+          constexpr int pl = decltype(I)::value;
+          v[pl] = __ldg(f.f + (size_t)pl * f.N + src);
+        });
         static_for<2 * kQ>([&](auto I) {
           constexpr int pl = decltype(I)::value;
           bx[pl * kBPlane + r * kBX + c] = v[pl];
@@ -437,9 +489,11 @@ tma2d_kernel(const __grid_constant__ CUtensorMap map_pop, Plain<0, float>::Reade
       s_psi[lo11(hcell[q])] = psi_of<kQ, float>(hf);
     }
     __syncthreads();
-    const int next = *s_next;
+    const int next = s_next[0];
+    TileLoc nloc{0, 0, 0};
     if (next < a.ntiles) {  // the stage has been read: load the next tile into it
-      if (tid == 0) issue(next);
+      nloc = TileLoc{s_next[1], s_next[2], s_next[3]};
+      if (tid == 0) issue(nloc);
       pending = true;
     }
 
@@ -507,6 +561,8 @@ tma2d_kernel(const __grid_constant__ CUtensorMap map_pop, Plain<0, float>::Reade
         collide_pairs_d2q9(fin, rho1, rho2, j, u, F, g, m, p, PlaneWriter{fout.f, fout.N}, (unsigned)(x + nx * y));
     }
     tile = next;
+    cur = nloc;
+    ++k;
   }
 }
 
@@ -558,27 +614,32 @@ bool encode_pop(CUtensorMap* m, const void* base, const HostParams& h) {
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-template <int S, bool EDM>
-cudaError_t launch_v(const CUtensorMap& map, const void* fa, void* fb, int* err, int* counter, int parity,
-                     const StepT<float>& p, int num_sms, cudaStream_t s) {
+template <int S, bool EDM, bool BATCH>
+cudaError_t launch_v(const CUtensorMap& map, const void* fa, void* fb, const StepT<float>& p, TmaArgs a, int num_sms,
+                     cudaStream_t s) {
   static bool configured = false;
   if (!configured) {
-    cudaError_t e = cudaFuncSetAttribute(tma2d_kernel<S, EDM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = cudaFuncSetAttribute(tma2d_kernel<S, EDM, BATCH>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          kSmemBytes);
     if (e != cudaSuccess) return e;
     configured = true;
   }
-  TmaArgs a;
-  a.err = err;
-  a.counter = counter;
-  a.parity = parity & 1;
-  a.ntx = (p.nx + TX - 1) / TX;
-  a.ntiles = a.ntx * ((p.ny + TY - 1) / TY);
+  if (a.ntiles <= 0) return cudaSuccess;
   const int slots = 2 * num_sms;  // resident CTAs
   const int grid = a.ntiles < slots ? a.ntiles : slots;
-  tma2d_kernel<S, EDM><<<grid, NT, kSmemBytes, s>>>(map, Plain<0, float>::reader(fa, (unsigned)p.N),
-                                                    Plain<0, float>::writer(fb, (unsigned)p.N), p, a);
+  tma2d_kernel<S, EDM, BATCH><<<grid, NT, kSmemBytes, s>>>(map, Plain<0, float>::reader(fa, (unsigned)p.N),
+                                                           Plain<0, float>::writer(fb, (unsigned)p.N), p, a);
   return cudaGetLastError();
+}
+
+template <bool BATCH>
+cudaError_t launch_any(const CUtensorMap& map, const void* fa, void* fb, const StepT<float>& p, const TmaArgs& a,
+                       int smax, bool edm, int num_sms, cudaStream_t s) {
+  if (smax == 0)
+    return edm ? launch_v<0, true, BATCH>(map, fa, fb, p, a, num_sms, s)
+               : launch_v<0, false, BATCH>(map, fa, fb, p, a, num_sms, s);
+  return edm ? launch_v<kMaxProbe, true, BATCH>(map, fa, fb, p, a, num_sms, s)
+             : launch_v<kMaxProbe, false, BATCH>(map, fa, fb, p, a, num_sms, s);
 }
 
 }  // namespace
@@ -592,16 +653,50 @@ cudaError_t tma2d_prepare(TmaMaps* m, const void* fa, const void* fb, const Host
 }
 
 cudaError_t tma2d_step(const TmaMaps& m, int from, const void* fa, void* fb, int* err, int* counter,
-                       long long launch, const HostParams& h, cudaStream_t s) {
+                       const HostParams& h, cudaStream_t s) {
   const StepT<float> p = to_step(h);
   const CUtensorMap& map = reinterpret_cast<const CUtensorMap*>(m.bytes)[from];
-  const bool edm = h.forcing == 1;
-  const int par = (int)(launch & 1);
-  if (h.smax == 0)
-    return edm ? launch_v<0, true>(map, fa, fb, err, counter, par, p, h.num_sms, s)
-               : launch_v<0, false>(map, fa, fb, err, counter, par, p, h.num_sms, s);
-  return edm ? launch_v<kMaxProbe, true>(map, fa, fb, err, counter, par, p, h.num_sms, s)
-             : launch_v<kMaxProbe, false>(map, fa, fb, err, counter, par, p, h.num_sms, s);
+  TmaArgs a{};
+  a.err = err;
+  a.counter = counter;
+  a.parity = from & 1;  // the state alternates with every step, and so do the counters
+  a.ntx = (p.nx + TX - 1) / TX;
+  a.ntiles = a.ntx * ((p.ny + TY - 1) / TY);
+  return launch_any<false>(map, fa, fb, p, a, h.smax, h.forcing == 1, h.num_sms, s);
+}
+
+size_t tma2d_member_bytes() { return sizeof(TmaMember); }
+
+int tma2d_member_fill(void* dst, const TmaMaps& m, const HostParams& h, void* buf0, void* buf1, int tile0) {
+  TmaMember mb;
+  std::memset(&mb, 0, sizeof(mb));
+  std::memcpy(mb.map, m.bytes, sizeof(mb.map));
+  mb.p = to_step(h);
+  mb.buf[0] = (float*)buf0;
+  mb.buf[1] = (float*)buf1;
+  mb.ntx = (h.nx + TX - 1) / TX;
+  mb.ntiles = mb.ntx * ((h.ny + TY - 1) / TY);
+  mb.tile0 = tile0;
+  std::memcpy(dst, &mb, sizeof(mb));
+  return mb.ntiles;
+}
+
+cudaError_t tma2d_batch_step(const void* members, int nmem, int total_tiles, int state, int* err, int* counter,
+                             int smax_max, int edm, int num_sms, cudaStream_t s) {
+  TmaArgs a{};
+  a.err = err;
+  a.counter = counter;
+  a.parity = state & 1;
+  a.ntx = 1;
+  a.ntiles = total_tiles;
+  a.members = (const TmaMember*)members;
+  a.nmem = nmem;
+  a.state = state & 1;
+  StepT<float> none;
+  std::memset(&none, 0, sizeof(none));
+  CUtensorMap unused;
+  std::memset(&unused, 0, sizeof(unused));
+  return launch_any<true>(unused, nullptr, nullptr, none, a, smax_max, edm != 0, num_sms, s);
 }
 
 }  // namespace lbnci
