@@ -167,6 +167,10 @@ lb_status validate(const lb_config* c, HostParams* p, Layout* lay, long long* nb
   p->tma = c->lattice == LB_D2Q9 && c->precision == LB_FP32 && c->nx % 4 == 0 ? 1 : 0;
   if (const char* e = std::getenv("LBNCI_FUSED"))
     if (std::strcmp(e, "classic") == 0) p->tma = 0;
+  // Test of the failure path of the TMA kernel's bounded waits (never set in use):
+  // LBNCI_TMA_STALL_TEST=1 makes every CTA's first wait run out after about a second.
+  p->tma_stall_test = 0;
+  if (const char* e = std::getenv("LBNCI_TMA_STALL_TEST")) p->tma_stall_test = std::atoi(e) == 1 ? 1 : 0;
   const int Q = c->lattice == LB_D2Q9 ? 9 : 27;
   (void)Q;
   const Launchers* L = launchers_for(c);

@@ -17,6 +17,8 @@ struct HostParams {
   int forcing;  // 0: Guo, 1: exact difference method on the dispersed phase
   int d3_kernel;  // D3Q27 collision: 0 marching along z (default), 1 tiled
   int tma;        // 1: D2Q9 FP32 steps run the persistent TMA-fed kernel
+  int tma_stall_test;  // 1: its first copy is expected to bring 16 more bytes than it does,
+                       // so its bounded wait runs out (test of the failure path only)
   double tau, A_s, beta, A_h, h_min, h_max, g_th, G[3];
 };
 

@@ -250,6 +250,7 @@ struct TmaArgs {
   const TmaMember* members;  // batched step: the member table
   int nmem;
   int state;     // batched step: members read buf[state] and write buf[state ^ 1]
+  unsigned stall_bytes;  // failure-path test only: bytes expected on top of the first copy
 };
 
 // Tile t of a lattice with ntx tile columns and ntiles tiles -> its origin. Numbering:
@@ -335,9 +336,11 @@ tma2d_kernel(const __grid_constant__ CUtensorMap map_pop, Plain<0, float>::Reade
     }
     return l;
   };
+  unsigned extra = a.stall_bytes;  // nonzero only in the failure-path test: the wait runs out
   auto issue = [&](const TileLoc& l) {  // one thread: TMA load of a tile's box into the stage
     const CUtensorMap* map = BATCH ? &a.members[l.m].map[a.state] : &map_pop;
-    mbar_expect_tx(&bar[0], kBoxBytes);
+    mbar_expect_tx(&bar[0], kBoxBytes + extra);
+    extra = 0;
     tma_load_3d(bx, map, l.x0 - kBOX, l.y0 - kBOY, 0, &bar[0]);
   };
 
@@ -657,6 +660,7 @@ cudaError_t tma2d_step(const TmaMaps& m, int from, const void* fa, void* fb, int
   const StepT<float> p = to_step(h);
   const CUtensorMap& map = reinterpret_cast<const CUtensorMap*>(m.bytes)[from];
   TmaArgs a{};
+  a.stall_bytes = h.tma_stall_test ? 16u : 0u;
   a.err = err;
   a.counter = counter;
   a.parity = from & 1;  // the state alternates with every step, and so do the counters

@@ -163,3 +163,36 @@ def test_fp32_tma2d_tiny_and_ragged(nx, ny, walls):
     rel = (np.abs(got - ref) / _scale(p, ref)).reshape(18, nx * ny)
     assert (~near).mean() > 0.8
     assert rel[:, ~near].max() <= FP32_TOL, rel[:, ~near].max()
+
+
+def test_tma_wait_failure_is_reported_and_context_survives(monkeypatch):
+    """Failure path of the TMA kernel's bounded waits, without a GPU fault: with
+    LBNCI_TMA_STALL_TEST=1 every CTA expects 16 bytes more than its first copy brings, so
+    its mbarrier wait runs out after about a second; the kernel records the failure and
+    returns, lb_observables reports LB_ECUDA, and the context stays usable (a new sim
+    steps and matches the oracle)."""
+    import time
+    p = oracle.make_params(lattice=oracle.D2Q9, nx=64, ny=32, wall_y=1, tau=1.0, A_s=0.01, beta=0.7, A_h=0.05,
+                           force=(1e-5, 0, 0))
+    fl = inputs.channel_emulsion_2d(64, 32, seed=51, r_lo=6, r_hi=8)
+    monkeypatch.setenv("LBNCI_TMA_STALL_TEST", "1")
+    with lbnci.Sim(_cfg(p, lbnci.LB_FP32)) as sim:
+        sim.init_fields(fl.rho1, fl.rho2)
+        t0 = time.time()
+        sim.step(1)
+        with pytest.raises(lbnci.LBError) as ei:
+            sim.observables()
+        elapsed = time.time() - t0
+    assert ei.value.status == lbnci.LB_ECUDA and "gave up waiting" in str(ei.value)
+    assert 0.5 < elapsed < 30.0
+    monkeypatch.delenv("LBNCI_TMA_STALL_TEST")
+    f0 = oracle.init(p, fl.rho1, fl.rho2).astype(np.float32).astype(np.float64)
+    with lbnci.Sim(_cfg(p, lbnci.LB_FP32)) as sim:
+        sim.set_populations(f0)
+        sim.step(1)
+        got = sim.get_populations()
+        assert sim.observables()["n_bad"] == 0
+    ref = oracle.step(p, f0, 1)
+    near, _ = _near_tie_sites(p, f0)
+    rel = (np.abs(got - ref) / _scale(p, ref)).reshape(18, -1)
+    assert rel[:, ~near].max() <= FP32_TOL
