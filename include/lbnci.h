@@ -162,9 +162,9 @@ const char* lb_last_error(const lb_sim* sim);
 long long lb_kernel_launches(const lb_sim* sim);
 
 /* Which kernel lb_step runs for this sim (no paper counterpart; reporting only):
- *   LB_PATH_FUSED2D  one-pass fused D2Q9 kernel (FP64, FP16-dev, FP32 when nx % 4 != 0
+ *   LB_PATH_FUSED2D  one-pass fused D2Q9 kernel (FP64; FP32 and FP16-dev when nx % 4 != 0
  *                    or LBNCI_FUSED=classic is set in the environment),
- *   LB_PATH_TMA2D    persistent TMA-fed D2Q9 FP32 kernel,
+ *   LB_PATH_TMA2D    persistent TMA-fed D2Q9 kernel (FP32 and FP16-dev storage),
  *   LB_PATH_D3Q27    D3Q27 moments + collision kernels.
  * Returns -1 for a NULL sim. */
 enum { LB_PATH_FUSED2D = 0, LB_PATH_TMA2D = 1, LB_PATH_D3Q27 = 2 };

@@ -162,9 +162,10 @@ lb_status validate(const lb_config* c, HostParams* p, Layout* lay, long long* nb
   // Tile of the fused D2Q9 kernel: LBNCI_FUSED_SPT=2 (32x16, the default) or 4 (32x32).
   p->spt = 2;
   if (const char* e = std::getenv("LBNCI_FUSED_SPT")) p->spt = std::atoi(e) == 4 ? 4 : 2;
-  // D2Q9 FP32 step: the persistent TMA-fed kernel (its tensor maps need nx % 4 == 0),
+  // D2Q9 FP32 / FP16-dev step: the persistent TMA-fed kernel (its maps need nx % 4 == 0),
   // unless LBNCI_FUSED=classic selects the one-pass fused kernel.
-  p->tma = c->lattice == LB_D2Q9 && c->precision == LB_FP32 && c->nx % 4 == 0 ? 1 : 0;
+  p->tma = c->lattice == LB_D2Q9 && (c->precision == LB_FP32 || c->precision == LB_FP16DEV) && c->nx % 4 == 0 ? 1 : 0;
+  p->half = c->precision == LB_FP16DEV ? 1 : 0;
   if (const char* e = std::getenv("LBNCI_FUSED"))
     if (std::strcmp(e, "classic") == 0) p->tma = 0;
   // Test of the failure path of the TMA kernel's bounded waits (never set in use):
@@ -623,8 +624,8 @@ struct lb_ensemble {
   bool own_stream;
   std::vector<lb_sim*> members;
   void* base;              // one allocation holding every member's workspace
-  std::vector<int> cls;    // members stepped by the one-pass batch kernel (FP64, FP16-dev, nx % 4 != 0)
-  std::vector<int> tma;    // members stepped by the batched TMA kernel (FP32, nx % 4 == 0)
+  std::vector<int> cls;    // members stepped by the one-pass batch kernel (FP64, nx % 4 != 0)
+  std::vector<int> tma;    // members stepped by the batched TMA kernel (FP32 or FP16-dev, nx % 4 == 0)
   std::vector<unsigned char> host_members;  // BatchMember records of cls (host copy)
   void* d_members;         // device copy of the member records
   int* d_tile0;            // first tile of every cls member, cls.size() + 1 entries
@@ -687,7 +688,7 @@ cudaError_t ens_launch(lb_ensemble* e, int parity, int* nk) {
     cudaError_t c = tma2d_batch_step(e->d_tma, (int)e->tma.size(), e->tma_tiles, parity, e->d_tma_flags,
                                      e->d_tma_flags + 1, e->tma_smax,
                                      e->members[0]->p.forcing == LB_FORCE_EDM_DISPERSED,
-                                     e->members[0]->p.num_sms, e->stream);
+                                     e->members[0]->p.half, e->members[0]->p.num_sms, e->stream);
     if (c != cudaSuccess) return c;
   }
   return ens_launch_cls(e, parity, nk);

@@ -16,7 +16,8 @@ struct HostParams {
   int num_sms;  // multiprocessors of the device
   int forcing;  // 0: Guo, 1: exact difference method on the dispersed phase
   int d3_kernel;  // D3Q27 collision: 0 marching along z (default), 1 tiled
-  int tma;        // 1: D2Q9 FP32 steps run the persistent TMA-fed kernel
+  int tma;        // 1: D2Q9 FP32 / FP16-dev steps run the persistent TMA-fed kernel
+  int half;       // FP16-deviation storage
   int tma_stall_test;  // 1: its first copy is expected to bring 16 more bytes than it does,
                        // so its bounded wait runs out (test of the failure path only)
   double tau, A_s, beta, A_h, h_min, h_max, g_th, G[3];
@@ -43,10 +44,13 @@ struct Launchers {
                             int smax_max, int edm, cudaStream_t s);
 };
 
-// Persistent TMA-fed D2Q9 FP32 step (lb_tma2d.cu), tiles of kTmaTX x kTmaTY sites.
+// Persistent TMA-fed D2Q9 step (lb_tma2d.cu) for FP32 and FP16-dev storage, tiles of
+// kTmaTX x kTmaTY sites.
 constexpr int kTmaTX = 32, kTmaTY = 16;
 struct TmaMaps {
-  alignas(64) unsigned char bytes[2 * 128];  // tensor maps of state buffer A and B
+  // tensor maps: FP32: box of state buffer A, B; FP16-dev: deviations of A, B, then the
+  // reference densities of A, B
+  alignas(64) unsigned char bytes[4 * 128];
 };
 bool tma2d_supported(const HostParams& h);
 cudaError_t tma2d_prepare(TmaMaps* m, const void* fa, const void* fb, const HostParams& h);
@@ -62,7 +66,7 @@ cudaError_t tma2d_step(const TmaMaps& m, int from, const void* fa, void* fb, int
 size_t tma2d_member_bytes();
 int tma2d_member_fill(void* dst, const TmaMaps& m, const HostParams& h, void* buf0, void* buf1, int tile0);
 cudaError_t tma2d_batch_step(const void* members, int nmem, int total_tiles, int state, int* err, int* counter,
-                             int smax_max, int edm, int num_sms, cudaStream_t s);
+                             int smax_max, int edm, int half, int num_sms, cudaStream_t s);
 
 const Launchers* launchers_fp64(int lattice);
 const Launchers* launchers_fp32(int lattice);

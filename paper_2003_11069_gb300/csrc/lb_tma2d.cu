@@ -51,6 +51,11 @@ constexpr int kBX = 48, kBY = 28, kBOX = 8, kBOY = 6, kBPlane = kBX * kBY;
 constexpr int kBoxFloats = 2 * kQ * kBPlane;
 constexpr unsigned kBoxBytes = kBoxFloats * 4;
 constexpr int kBoxStride = (kBoxBytes + 1023) / 1024 * 1024;
+// FP16-deviation storage: 9 planes of half2 deviations (one 32-bit word per cell), then
+// the reference densities (float2 per cell) of the same 48 x 28 cells.
+constexpr unsigned kHalfDevBytes = kQ * kBPlane * 4, kHalfRhoBytes = kBPlane * 8;
+constexpr int kHalfRhoOff = (kHalfDevBytes + 1023) / 1024 * 1024;
+static_assert(kHalfRhoOff + (int)kHalfRhoBytes <= kBoxStride, "half boxes fit the stage");
 
 // Shared-memory layout (bytes from a 1024-aligned base): the population box, psi of
 // the tile and its halo, probe normals, the mbarrier and the next tile's index.
@@ -110,6 +115,15 @@ __device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, i
       "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
       "[%5];" ::"r"(smem_u32(dst)),
       "l"(reinterpret_cast<unsigned long long>(map)), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int x, int y,
+                                            unsigned long long* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], "
+      "[%4];" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<unsigned long long>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
       : "memory");
 }
 
@@ -233,14 +247,35 @@ __device__ __forceinline__ void collide_pairs_d2q9(const float fin[2][kQ], float
   fout.put_rho(idx, rho1, rho2);
 }
 
-// One lattice of a batched step (device memory): its population-box maps for state
-// buffer 0 and 1, step parameters, the two buffers and its tiles' place in the batch.
-struct alignas(64) TmaMember {
-  CUtensorMap map[2];
+// One lattice of a batched step (device memory): its tensor maps, step parameters, the
+// two state buffers and its tiles' place in the batch. (Aligned as CUtensorMap is.)
+struct TmaMember {
+  CUtensorMap map[4];  // plain: box of buffer 0, 1; FP16-dev: deviations 0, 1, densities 0, 1
   StepT<float> p;
   float* buf[2];
   int ntx, ntiles, tile0;
 };
+
+// pull_box for FP16-deviation storage: f_i^k = w_i rho_ref^k(src) + delta_i^k(src), the
+// reference densities of the cell the population comes from.
+__device__ __forceinline__ void pull_box_half(const unsigned char* __restrict__ bxb, int c, bool bym, bool byp,
+                                              float fin[2][kQ]) {
+  const __half2* dv = reinterpret_cast<const __half2*>(bxb);
+  const float2* rr = reinterpret_cast<const float2*>(bxb + kHalfRhoOff);
+  static_for<kQ>([&](auto I) {
+    constexpr int i = decltype(I)::value;
+    constexpr int cy = cc(i, 1);
+    constexpr int off = -cy * kBX - cc(i, 0);
+    constexpr float w = float(Lattice<0>::w(i));
+    const bool bounce = (cy == 1 && bym) || (cy == -1 && byp);
+    const int src = bounce ? c : c + off;
+    const int pl = bounce ? opposite(i) : i;
+    const float2 d = __half22float2(dv[pl * kBPlane + src]);
+    const float2 r = rr[src];
+    fin[0][i] = fmaf(w, r.x, d.x);
+    fin[1][i] = fmaf(w, r.y, d.y);
+  });
+}
 
 struct TmaArgs {
   int* err;      // bit 0: a TMA wait expired; bit 1: misaligned shared memory
@@ -284,11 +319,14 @@ struct TileLoc {
 };
 
 // Two CTAs per SM (64 registers a thread). BATCH: tiles of all members of a batch,
-// each member's parameters copied into shared memory for its tiles.
-template <int S, bool EDM, bool BATCH>
+// each member's parameters copied into shared memory for its tiles. ST: the storage
+// layout, Plain<0, float> (FP32) or HalfDev<0> (FP16 deviations, FP32 arithmetic);
+// map_rho is the reference-density map of the latter.
+template <int S, bool EDM, bool BATCH, typename ST>
 __global__ void __launch_bounds__(NT, 2)
-tma2d_kernel(const __grid_constant__ CUtensorMap map_pop, Plain<0, float>::Reader f_one,
-             Plain<0, float>::Writer fout_one, StepT<float> p_one, TmaArgs a) {
+tma2d_kernel(const __grid_constant__ CUtensorMap map_pop, const __grid_constant__ CUtensorMap map_rho,
+             typename ST::Reader f_one, typename ST::Writer fout_one, StepT<float> p_one, TmaArgs a) {
+  constexpr bool HALF = ST::kHalf;
   constexpr int R = S + 1;  // psi halo
   constexpr int RX = TX + 2 * R, RY = TY + 2 * R;
   constexpr int GX = TX + 2 * S, GY = TY + 2 * S;
@@ -339,9 +377,20 @@ tma2d_kernel(const __grid_constant__ CUtensorMap map_pop, Plain<0, float>::Reade
   unsigned extra = a.stall_bytes;  // nonzero only in the failure-path test: the wait runs out
   auto issue = [&](const TileLoc& l) {  // one thread: TMA load of a tile's box into the stage
     const CUtensorMap* map = BATCH ? &a.members[l.m].map[a.state] : &map_pop;
-    mbar_expect_tx(&bar[0], kBoxBytes + extra);
+    if constexpr (HALF) {
+      const CUtensorMap* mr = BATCH ? &a.members[l.m].map[2 + a.state] : &map_rho;
+      mbar_expect_tx(&bar[0], kHalfDevBytes + kHalfRhoBytes + extra);
+      tma_load_3d(bx, map, l.x0 - kBOX, l.y0 - kBOY, 0, &bar[0]);
+      tma_load_2d(sm + kHalfRhoOff, mr, 2 * (l.x0 - kBOX), l.y0 - kBOY, &bar[0]);
+    } else {
+      mbar_expect_tx(&bar[0], kBoxBytes + extra);
+      tma_load_3d(bx, map, l.x0 - kBOX, l.y0 - kBOY, 0, &bar[0]);
+    }
     extra = 0;
-    tma_load_3d(bx, map, l.x0 - kBOX, l.y0 - kBOY, 0, &bar[0]);
+  };
+  auto pull = [&](int c, bool bym, bool byp, float out[2][kQ]) {
+    if constexpr (HALF) pull_box_half(sm, c, bym, byp, out);
+    else pull_box(bx, c, bym, byp, out);
   };
 
   // This thread's halo cells (tid, tid + NT) and ring cell (tid) are the same in every
@@ -418,11 +467,11 @@ tma2d_kernel(const __grid_constant__ CUtensorMap map_pop, Plain<0, float>::Reade
     phase ^= 1u;
     pending = false;
     const StepT<float>& p = BATCH ? s_p[slot] : p_one;
-    Plain<0, float>::Reader f = f_one;
-    Plain<0, float>::Writer fout = fout_one;
+    typename ST::Reader f = f_one;
+    typename ST::Writer fout = fout_one;
     if constexpr (BATCH) {
-      f = Plain<0, float>::reader(a.members[cur.m].buf[a.state], (unsigned)p.N);
-      fout = Plain<0, float>::writer(a.members[cur.m].buf[a.state ^ 1], (unsigned)p.N);
+      f = ST::reader(a.members[cur.m].buf[a.state], (unsigned)p.N);
+      fout = ST::writer(a.members[cur.m].buf[a.state ^ 1], (unsigned)p.N);
     }
     const bool walls = p.wall_y != 0;
     const int nx = p.nx, ny = p.ny;
@@ -452,15 +501,31 @@ tma2d_kernel(const __grid_constant__ CUtensorMap map_pop, Plain<0, float>::Reade
           r = j < rt ? j : rb + (j - rt);
         }
         const unsigned src = (unsigned)(wrapn(x0 - kBOX + c, nx) + nx * wrapn(y0 - kBOY + r, ny));
-        float v[2 * kQ];
-        static_for<2 * kQ>([&](auto I) {
-          constexpr int pl = decltype(I)::value;
-          v[pl] = __ldg(f.f + (size_t)pl * f.N + src);
-        });
-        static_for<2 * kQ>([&](auto I) {
-          constexpr int pl = decltype(I)::value;
-          bx[pl * kBPlane + r * kBX + c] = v[pl];
-        });
+        if constexpr (HALF) {  // the cell's 9 deviation words and its reference densities
+          unsigned v[kQ];
+          const unsigned* dg = reinterpret_cast<const unsigned*>(f.d);
+          static_for<kQ>([&](auto I) {
+            constexpr int pl = decltype(I)::value;
+            v[pl] = __ldg(dg + (size_t)pl * f.N + src);
+          });
+          const float2 rv = __ldg(f.rho + src);
+          unsigned* db = reinterpret_cast<unsigned*>(sm);
+          static_for<kQ>([&](auto I) {
+            constexpr int pl = decltype(I)::value;
+            db[pl * kBPlane + r * kBX + c] = v[pl];
+          });
+          reinterpret_cast<float2*>(sm + kHalfRhoOff)[r * kBX + c] = rv;
+        } else {
+          float v[2 * kQ];
+          static_for<2 * kQ>([&](auto I) {
+            constexpr int pl = decltype(I)::value;
+            v[pl] = __ldg(f.f + (size_t)pl * f.N + src);
+          });
+          static_for<2 * kQ>([&](auto I) {
+            constexpr int pl = decltype(I)::value;
+            bx[pl * kBPlane + r * kBX + c] = v[pl];
+          });
+        }
       }
       fence_async_smem();  // these generic writes precede the next TMA write of the stage
       __syncthreads();
@@ -468,7 +533,7 @@ tma2d_kernel(const __grid_constant__ CUtensorMap map_pop, Plain<0, float>::Reade
     {  // an own position beyond a ragged edge holds the psi of the site it wraps to (x,
        // periodic y: the box holds the image) or of its mirror across the wall
       const int gy = walls ? clampc(y, ny) : y;
-      pull_box(bx, (gy - y0 + kBOY) * kBX + (tx + kBOX), walls && gy == 0, walls && gy == ny - 1, fin);
+      pull((gy - y0 + kBOY) * kBX + (tx + kBOX), walls && gy == 0, walls && gy == ny - 1, fin);
       s_psi[(tx + R) + RX * (ty + R)] = psi_of<kQ, float>(fin, &rho1, &rho2);
     }
     // the halo reaches a wall (or the mirror row beyond it) only in the first and last
@@ -488,7 +553,7 @@ tma2d_kernel(const __grid_constant__ CUtensorMap map_pop, Plain<0, float>::Reade
         byp = gyc == ny - 1;
       }
       float hf[2][kQ];
-      pull_box(bx, bo, bym, byp, hf);
+      pull(bo, bym, byp, hf);
       s_psi[lo11(hcell[q])] = psi_of<kQ, float>(hf);
     }
     __syncthreads();
@@ -557,11 +622,18 @@ tma2d_kernel(const __grid_constant__ CUtensorMap map_pop, Plain<0, float>::Reade
 #pragma unroll
       for (int c = 0; c < 3; ++c) u[c] = __fdividef(j[c] + 0.5f * F[c], rho);
       const float m[3] = {-n0, -n1, 0.f};
-      if constexpr (EDM)
-        collide_store<0, float, PlaneWriter, EDM>(fin, rho1, rho2, j, u, F, g, m, p, PlaneWriter{fout.f, fout.N},
-                                                   x + nx * y);
-      else
-        collide_pairs_d2q9(fin, rho1, rho2, j, u, F, g, m, p, PlaneWriter{fout.f, fout.N}, (unsigned)(x + nx * y));
+      if constexpr (HALF) {
+        if constexpr (EDM)
+          collide_store<0, float, typename ST::Writer, EDM>(fin, rho1, rho2, j, u, F, g, m, p, fout, x + nx * y);
+        else
+          collide_pairs_d2q9(fin, rho1, rho2, j, u, F, g, m, p, fout, (unsigned)(x + nx * y));
+      } else {
+        if constexpr (EDM)
+          collide_store<0, float, PlaneWriter, EDM>(fin, rho1, rho2, j, u, F, g, m, p, PlaneWriter{fout.f, fout.N},
+                                                     x + nx * y);
+        else
+          collide_pairs_d2q9(fin, rho1, rho2, j, u, F, g, m, p, PlaneWriter{fout.f, fout.N}, (unsigned)(x + nx * y));
+      }
     }
     tile = next;
     cur = nloc;
@@ -604,45 +676,67 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
   return fn;
 }
 
-// Populations of one state as a 3-D tensor (x, y, plane) of floats, box 48 x 28 x 18.
-bool encode_pop(CUtensorMap* m, const void* base, const HostParams& h) {
+// Populations of one state as a 3-D tensor (x, y, plane) of 32-bit words, box 48 x 28 x
+// planes: 18 float planes (FP32) or 9 half2 deviation planes (FP16-dev).
+bool encode_pop(CUtensorMap* m, const void* base, const HostParams& h, unsigned planes = 2 * kQ) {
   auto fn = encode_fn();
   if (!fn) return false;
-  const cuuint64_t dims[3] = {(cuuint64_t)h.nx, (cuuint64_t)h.ny, 2 * kQ};
+  const cuuint64_t dims[3] = {(cuuint64_t)h.nx, (cuuint64_t)h.ny, planes};
   const cuuint64_t strides[2] = {(cuuint64_t)h.nx * 4, (cuuint64_t)h.N * 4};
-  const cuuint32_t box[3] = {kBX, kBY, 2 * kQ};
+  const cuuint32_t box[3] = {kBX, kBY, planes};
   const cuuint32_t es[3] = {1, 1, 1};
   return fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<void*>(base), dims, strides, box, es,
             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-template <int S, bool EDM, bool BATCH>
-cudaError_t launch_v(const CUtensorMap& map, const void* fa, void* fb, const StepT<float>& p, TmaArgs a, int num_sms,
-                     cudaStream_t s) {
+// Reference densities of an FP16-dev state as a 2-D tensor (2 nx floats, ny), box 96 x 28.
+bool encode_rho(CUtensorMap* m, const void* base, const HostParams& h) {
+  auto fn = encode_fn();
+  if (!fn) return false;
+  const cuuint64_t dims[2] = {(cuuint64_t)h.nx * 2, (cuuint64_t)h.ny};
+  const cuuint64_t strides[1] = {(cuuint64_t)h.nx * 8};
+  const cuuint32_t box[2] = {2 * kBX, kBY};
+  const cuuint32_t es[2] = {1, 1};
+  return fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<void*>(base), dims, strides, box, es,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+template <int S, bool EDM, bool BATCH, typename ST>
+cudaError_t launch_v(const CUtensorMap& map, const CUtensorMap& map_rho, const void* fa, void* fb,
+                     const StepT<float>& p, TmaArgs a, int num_sms, cudaStream_t s) {
   static bool configured = false;
   if (!configured) {
-    cudaError_t e = cudaFuncSetAttribute(tma2d_kernel<S, EDM, BATCH>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         kSmemBytes);
+    cudaError_t e = cudaFuncSetAttribute(tma2d_kernel<S, EDM, BATCH, ST>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
     if (e != cudaSuccess) return e;
     configured = true;
   }
   if (a.ntiles <= 0) return cudaSuccess;
   const int slots = 2 * num_sms;  // resident CTAs
   const int grid = a.ntiles < slots ? a.ntiles : slots;
-  tma2d_kernel<S, EDM, BATCH><<<grid, NT, kSmemBytes, s>>>(map, Plain<0, float>::reader(fa, (unsigned)p.N),
-                                                           Plain<0, float>::writer(fb, (unsigned)p.N), p, a);
+  tma2d_kernel<S, EDM, BATCH, ST><<<grid, NT, kSmemBytes, s>>>(map, map_rho, ST::reader(fa, (unsigned)p.N),
+                                                               ST::writer(fb, (unsigned)p.N), p, a);
   return cudaGetLastError();
 }
 
-template <bool BATCH>
-cudaError_t launch_any(const CUtensorMap& map, const void* fa, void* fb, const StepT<float>& p, const TmaArgs& a,
-                       int smax, bool edm, int num_sms, cudaStream_t s) {
+template <bool BATCH, typename ST>
+cudaError_t launch_st(const CUtensorMap& map, const CUtensorMap& map_rho, const void* fa, void* fb,
+                      const StepT<float>& p, const TmaArgs& a, int smax, bool edm, int num_sms, cudaStream_t s) {
   if (smax == 0)
-    return edm ? launch_v<0, true, BATCH>(map, fa, fb, p, a, num_sms, s)
-               : launch_v<0, false, BATCH>(map, fa, fb, p, a, num_sms, s);
-  return edm ? launch_v<kMaxProbe, true, BATCH>(map, fa, fb, p, a, num_sms, s)
-             : launch_v<kMaxProbe, false, BATCH>(map, fa, fb, p, a, num_sms, s);
+    return edm ? launch_v<0, true, BATCH, ST>(map, map_rho, fa, fb, p, a, num_sms, s)
+               : launch_v<0, false, BATCH, ST>(map, map_rho, fa, fb, p, a, num_sms, s);
+  return edm ? launch_v<kMaxProbe, true, BATCH, ST>(map, map_rho, fa, fb, p, a, num_sms, s)
+             : launch_v<kMaxProbe, false, BATCH, ST>(map, map_rho, fa, fb, p, a, num_sms, s);
+}
+
+template <bool BATCH>
+cudaError_t launch_any(const CUtensorMap& map, const CUtensorMap& map_rho, const void* fa, void* fb,
+                       const StepT<float>& p, const TmaArgs& a, int smax, bool edm, bool half, int num_sms,
+                       cudaStream_t s) {
+  return half ? launch_st<BATCH, HalfDev<0>>(map, map_rho, fa, fb, p, a, smax, edm, num_sms, s)
+              : launch_st<BATCH, Plain<0, float>>(map, map_rho, fa, fb, p, a, smax, edm, num_sms, s);
 }
 
 }  // namespace
@@ -652,13 +746,20 @@ bool tma2d_supported(const HostParams& h) { return h.nx % 4 == 0 && h.nz == 1 &&
 cudaError_t tma2d_prepare(TmaMaps* m, const void* fa, const void* fb, const HostParams& h) {
   static_assert(sizeof(CUtensorMap) == 128, "tensor map size");
   CUtensorMap* maps = reinterpret_cast<CUtensorMap*>(m->bytes);
-  return encode_pop(&maps[0], fa, h) && encode_pop(&maps[1], fb, h) ? cudaSuccess : cudaErrorInvalidValue;
+  std::memset(m->bytes, 0, sizeof(m->bytes));
+  if (!h.half) return encode_pop(&maps[0], fa, h) && encode_pop(&maps[1], fb, h) ? cudaSuccess : cudaErrorInvalidValue;
+  const size_t ro = HalfDev<0>::rho_offset((size_t)h.N);
+  const bool ok = encode_pop(&maps[0], fa, h, kQ) && encode_pop(&maps[1], fb, h, kQ) &&
+                  encode_rho(&maps[2], (const char*)fa + ro, h) && encode_rho(&maps[3], (const char*)fb + ro, h);
+  return ok ? cudaSuccess : cudaErrorInvalidValue;
 }
 
 cudaError_t tma2d_step(const TmaMaps& m, int from, const void* fa, void* fb, int* err, int* counter,
                        const HostParams& h, cudaStream_t s) {
   const StepT<float> p = to_step(h);
-  const CUtensorMap& map = reinterpret_cast<const CUtensorMap*>(m.bytes)[from];
+  const CUtensorMap* maps = reinterpret_cast<const CUtensorMap*>(m.bytes);
+  const CUtensorMap& map = maps[from];
+  const CUtensorMap& map_rho = maps[h.half ? 2 + from : from];
   TmaArgs a{};
   a.stall_bytes = h.tma_stall_test ? 16u : 0u;
   a.err = err;
@@ -666,12 +767,13 @@ cudaError_t tma2d_step(const TmaMaps& m, int from, const void* fa, void* fb, int
   a.parity = from & 1;  // the state alternates with every step, and so do the counters
   a.ntx = (p.nx + TX - 1) / TX;
   a.ntiles = a.ntx * ((p.ny + TY - 1) / TY);
-  return launch_any<false>(map, fa, fb, p, a, h.smax, h.forcing == 1, h.num_sms, s);
+  return launch_any<false>(map, map_rho, fa, fb, p, a, h.smax, h.forcing == 1, h.half != 0, h.num_sms, s);
 }
 
 size_t tma2d_member_bytes() { return sizeof(TmaMember); }
 
 int tma2d_member_fill(void* dst, const TmaMaps& m, const HostParams& h, void* buf0, void* buf1, int tile0) {
+  static_assert(sizeof(TmaMember::map) == sizeof(TmaMaps::bytes), "member maps");
   TmaMember mb;
   std::memset(&mb, 0, sizeof(mb));
   std::memcpy(mb.map, m.bytes, sizeof(mb.map));
@@ -686,7 +788,7 @@ int tma2d_member_fill(void* dst, const TmaMaps& m, const HostParams& h, void* bu
 }
 
 cudaError_t tma2d_batch_step(const void* members, int nmem, int total_tiles, int state, int* err, int* counter,
-                             int smax_max, int edm, int num_sms, cudaStream_t s) {
+                             int smax_max, int edm, int half, int num_sms, cudaStream_t s) {
   TmaArgs a{};
   a.err = err;
   a.counter = counter;
@@ -700,7 +802,7 @@ cudaError_t tma2d_batch_step(const void* members, int nmem, int total_tiles, int
   std::memset(&none, 0, sizeof(none));
   CUtensorMap unused;
   std::memset(&unused, 0, sizeof(unused));
-  return launch_any<true>(unused, nullptr, nullptr, none, a, smax_max, edm != 0, num_sms, s);
+  return launch_any<true>(unused, unused, nullptr, nullptr, none, a, smax_max, edm != 0, half != 0, num_sms, s);
 }
 
 }  // namespace lbnci

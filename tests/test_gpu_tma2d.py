@@ -76,6 +76,31 @@ def test_fp32_tma2d_steps(name):
     assert checked == 6 and obs["n_bad"] == 0
 
 
+@pytest.mark.parametrize("name", ["channel192x80_walls", "periodic160x96", "ragged128x50", "edm192x64"])
+def test_fp16dev_tma2d_steps(name):
+    """FP16-deviation storage on the TMA kernel (deviation planes and reference densities
+    copied by TMA, decoded in shared memory): each step within the FP16-dev per-step bound
+    (3e-4 on the population scale) of one oracle step from the GPU's own previous state."""
+    case = CASES[name]
+    p = oracle.make_params(lattice=oracle.D2Q9, **case["p"])
+    fl = case["gen"]()
+    Q, N = 9, p.nx * p.ny
+    with lbnci.Sim(_cfg(p, lbnci.LB_FP16DEV)) as sim:
+        assert sim.step_path() == lbnci.LB_PATH_TMA2D
+        sim.init_fields(fl.rho1, fl.rho2)
+        sim.step(20)
+        for _ in range(4):
+            f0 = sim.get_populations()
+            sim.step(1)
+            got = sim.get_populations()
+            ref = oracle.step(p, f0, 1)
+            near, _ = _near_tie_sites(p, f0)
+            rel = (np.abs(got - ref) / _scale(p, ref)).reshape(2 * Q, N)
+            assert (~near).mean() > 0.97
+            assert rel[:, ~near].max() <= 3e-4, f"{name}: {rel[:, ~near].max():.3e}"
+        assert sim.observables()["n_bad"] == 0
+
+
 def test_fp32_tma2d_after_set_populations():
     """A state set from the host after some steps is what the next step reads (the
     tensor maps follow the buffer swap)."""
@@ -106,7 +131,8 @@ def test_step_path_selection(monkeypatch):
     assert path(**base, precision=lbnci.LB_FP32) == lbnci.LB_PATH_TMA2D
     assert path(**dict(base, nx=37), precision=lbnci.LB_FP32) == lbnci.LB_PATH_FUSED2D
     assert path(**base, precision=lbnci.LB_FP64) == lbnci.LB_PATH_FUSED2D
-    assert path(**base, precision=lbnci.LB_FP16DEV) == lbnci.LB_PATH_FUSED2D
+    assert path(**base, precision=lbnci.LB_FP16DEV) == lbnci.LB_PATH_TMA2D
+    assert path(**dict(base, nx=38), precision=lbnci.LB_FP16DEV) == lbnci.LB_PATH_FUSED2D
     assert path(lattice=1, nx=16, ny=8, nz=8, wall_y=1, wall_z=1, tau=1.0, A_s=0.01, beta=0.7,
                 precision=lbnci.LB_FP32) == lbnci.LB_PATH_D3Q27
     monkeypatch.setenv("LBNCI_FUSED", "classic")
