@@ -292,15 +292,21 @@ __device__ __forceinline__ void collide_store(const T fin[2][Lattice<LAT>::Q], T
     return;
   }
   const T rho = rho1 + rho2;
-  const T uF = u[0] * F[0] + u[1] * F[1] + u[2] * F[2];
-  const T uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+  constexpr bool D3 = Lattice<LAT>::D == 3;  // D2Q9: u and F have no z component
+  const T uF = u[0] * F[0] + u[1] * F[1] + (D3 ? u[2] * F[2] : T(0));
+  const T uu = u[0] * u[0] + u[1] * u[1] + (D3 ? u[2] * u[2] : T(0));
   const T seg = M<T>::div(p.beta * rho1 * rho2, rho);
   const T pamp = p.pamp * g;
   const T c1 = M<T>::div(rho1, rho);
   // FP32: the same operator regrouped per site,
-  //   f*_i = (1 - omega) f_i + w_i [K0 + c.u (omega rho (3 + 4.5 c.u) + 9 guo c.F) + 3 guo c.F + pamp (c.m)^2]
+  //   f*_i = (1 - omega) f_i + w_i B_i,
+  //   B_i = K0 + c.u (omega rho (3 + 4.5 c.u) + 9 guo c.F) + 3 guo c.F + pamp (c.m)^2,
   //   K0 = omega rho (1 - 1.5 u.u) - 3 guo u.F - pamp/3,
-  // so that each direction costs a short chain of multiply-adds. The rest population
+  // evaluated per pair of opposite directions (i, opposite(i)): c.u, c.F and c.m change
+  // sign between the two, so B splits into a part even in c,
+  //   E = K0 + 4.5 omega rho (c.u)^2 + 9 guo (c.u)(c.F) + pamp (c.m)^2,
+  // and an odd part O = 3 omega rho c.u + 3 guo c.F (B = E + O and E - O), and the
+  // recolouring term changes sign; the pair shares those products. The rest population
   // of each component is set to rho_k minus the others (its exact value), so per-site
   // mass is kept to the rounding of one sum instead of drifting with the coherent
   // rounding of K0.
@@ -311,7 +317,8 @@ __device__ __forceinline__ void collide_store(const T fin[2][Lattice<LAT>::Q], T
   T s1 = T(0), s2 = T(0);
   static_for<Q>([&](auto I) {
     constexpr int i = decltype(I)::value;
-    if constexpr (i > 0) {
+    constexpr int o = opposite(i);
+    if constexpr (i > 0 && i < o) {
       constexpr T w = T(Lattice<LAT>::w(i));
       constexpr int ix = cc(i, 0), iy = cc(i, 1), iz = cc(i, 2);
       constexpr T wl = T(Lattice<LAT>::w(i) / (speed2(i) == 1 ? 1.0 : (speed2(i) == 2 ? 1.4142135623730951
@@ -323,15 +330,18 @@ __device__ __forceinline__ void collide_store(const T fin[2][Lattice<LAT>::Q], T
         if constexpr (iz == 1) r += v[2]; else if constexpr (iz == -1) r -= v[2];
         return r;
       };
-      const T fi = fin[0][i] + fin[1][i];
       const T cu = dotc(u), cF = dotc(F), cm = dotc(m);
-      const T B = K0 + cu * (a3 + a45 * cu + g9 * cF) + g3 * cF + pamp * (cm * cm);
-      const T fs = om1 * fi + w * B;
-      const T o1 = c1 * fs + seg * wl * cm;
-      const T o2 = fs - o1;
-      s1 += o1;
-      s2 += o2;
-      fout.template put<i>((unsigned)idx, o1, o2, rho1, rho2);
+      const T E = fmaf(pamp, cm * cm, fmaf(g9, cu * cF, fmaf(a45, cu * cu, K0)));
+      const T O = fmaf(g3, cF, a3 * cu);
+      const T fsp = fmaf(w, E + O, om1 * (fin[0][i] + fin[1][i]));
+      const T fsm = fmaf(w, E - O, om1 * (fin[0][o] + fin[1][o]));
+      const T rc = (seg * wl) * cm;
+      const T o1p = fmaf(c1, fsp, rc), o1m = fmaf(c1, fsm, -rc);
+      const T o2p = fsp - o1p, o2m = fsm - o1m;
+      s1 += o1p + o1m;
+      s2 += o2p + o2m;
+      fout.template put<i>((unsigned)idx, o1p, o2p, rho1, rho2);
+      fout.template put<o>((unsigned)idx, o1m, o2m, rho1, rho2);
     }
   });
   fout.template put<0>((unsigned)idx, rho1 - s1, rho2 - s2, rho1, rho2);

@@ -193,60 +193,6 @@ struct PlaneWriter {
   __device__ __forceinline__ void put_rho(unsigned, float, float) const {}
 };
 
-// The FP32 Guo collision of lb_kernels.cuh (BGK + source + perturbation, then
-// recolouring) for D2Q9, evaluated per pair of opposite directions (i, opposite(i)):
-// with c.u, c.F, c.m changing sign between the two, the bracket
-//   B_i = K0 + c.u (3 omega rho + 4.5 omega rho c.u + 9 guo c.F) + 3 guo c.F + pamp (c.m)^2
-// splits into a part even in c, E = K0 + 4.5 omega rho (c.u)^2 + 9 guo (c.u)(c.F) +
-// pamp (c.m)^2, and an odd part O = 3 omega rho c.u + 3 guo c.F, B = E + O and E - O,
-// and the recolouring term changes sign; each pair shares those products.
-template <typename WR>
-__device__ __forceinline__ void collide_pairs_d2q9(const float fin[2][kQ], float rho1, float rho2, const float j[3],
-                                                   const float u[3], const float F[3], float g, const float m[3],
-                                                   const StepT<float>& p, const WR& fout, unsigned idx) {
-  (void)j;
-  const float rho = rho1 + rho2;
-  const float uF = u[0] * F[0] + u[1] * F[1];
-  const float uu = u[0] * u[0] + u[1] * u[1];
-  const float seg = __fdividef(p.beta * rho1 * rho2, rho);
-  const float pamp = p.pamp * g;
-  const float c1 = __fdividef(rho1, rho);
-  const float orho = p.omega * rho;
-  const float K0 = orho * (1.0f - 1.5f * uu) - 3.0f * p.guo * uF - pamp * (1.0f / 3.0f);
-  const float a3 = 3.0f * orho, a45 = 4.5f * orho, g3 = 3.0f * p.guo, g9 = 9.0f * p.guo;
-  const float om1 = 1.0f - p.omega;
-  float s1 = 0.f, s2 = 0.f;
-  static_for<kQ>([&](auto I) {
-    constexpr int i = decltype(I)::value;
-    constexpr int o = opposite(i);
-    if constexpr (i > 0 && i < o) {
-      constexpr float w = float(Lattice<0>::w(i));
-      constexpr int ix = cc(i, 0), iy = cc(i, 1);
-      constexpr float wl = float(Lattice<0>::w(i) / (speed2(i) == 1 ? 1.0 : 1.4142135623730951));
-      auto dotc = [&](const float v[3]) {
-        float r = 0.f;
-        if constexpr (ix == 1) r += v[0]; else if constexpr (ix == -1) r -= v[0];
-        if constexpr (iy == 1) r += v[1]; else if constexpr (iy == -1) r -= v[1];
-        return r;
-      };
-      const float cu = dotc(u), cF = dotc(F), cm = dotc(m);
-      const float E = fmaf(pamp, cm * cm, fmaf(g9, cu * cF, fmaf(a45, cu * cu, K0)));
-      const float O = fmaf(g3, cF, a3 * cu);
-      const float fsp = fmaf(w, E + O, om1 * (fin[0][i] + fin[1][i]));
-      const float fsm = fmaf(w, E - O, om1 * (fin[0][o] + fin[1][o]));
-      const float rc = (seg * wl) * cm;
-      const float o1p = fmaf(c1, fsp, rc), o1m = fmaf(c1, fsm, -rc);
-      const float o2p = fsp - o1p, o2m = fsm - o1m;
-      s1 += o1p + o1m;
-      s2 += o2p + o2m;
-      fout.template put<i>(idx, o1p, o2p, rho1, rho2);
-      fout.template put<o>(idx, o1m, o2m, rho1, rho2);
-    }
-  });
-  fout.template put<0>(idx, rho1 - s1, rho2 - s2, rho1, rho2);
-  fout.put_rho(idx, rho1, rho2);
-}
-
 // One lattice of a batched step (device memory): its tensor maps, step parameters, the
 // two state buffers and its tiles' place in the batch. (Aligned as CUtensorMap is.)
 struct TmaMember {
@@ -622,18 +568,11 @@ tma2d_kernel(const __grid_constant__ CUtensorMap map_pop, const __grid_constant_
 #pragma unroll
       for (int c = 0; c < 3; ++c) u[c] = __fdividef(j[c] + 0.5f * F[c], rho);
       const float m[3] = {-n0, -n1, 0.f};
-      if constexpr (HALF) {
-        if constexpr (EDM)
-          collide_store<0, float, typename ST::Writer, EDM>(fin, rho1, rho2, j, u, F, g, m, p, fout, x + nx * y);
-        else
-          collide_pairs_d2q9(fin, rho1, rho2, j, u, F, g, m, p, fout, (unsigned)(x + nx * y));
-      } else {
-        if constexpr (EDM)
-          collide_store<0, float, PlaneWriter, EDM>(fin, rho1, rho2, j, u, F, g, m, p, PlaneWriter{fout.f, fout.N},
-                                                     x + nx * y);
-        else
-          collide_pairs_d2q9(fin, rho1, rho2, j, u, F, g, m, p, PlaneWriter{fout.f, fout.N}, (unsigned)(x + nx * y));
-      }
+      if constexpr (HALF)
+        collide_store<0, float, typename ST::Writer, EDM>(fin, rho1, rho2, j, u, F, g, m, p, fout, x + nx * y);
+      else
+        collide_store<0, float, PlaneWriter, EDM>(fin, rho1, rho2, j, u, F, g, m, p, PlaneWriter{fout.f, fout.N},
+                                                   x + nx * y);
     }
     tile = next;
     cur = nloc;
