@@ -121,13 +121,13 @@ cudaError_t launch_march3d_v(const void* fa, void* fb, const void* psi, const Ho
   if (e != cudaSuccess) return e;
   const int bx = (p.nx + kMarchTX - 1) / kMarchTX, by = (p.ny + kMarchTY - 1) / kMarchTY;
   const int per_sm = sizeof(T) == 4 ? 2 : 1;
-  // enough z segments to give every SM its resident blocks, one plane at least each
-  int nseg = (h.num_sms * per_sm + bx * by - 1) / (bx * by);
-  nseg = nseg < 1 ? 1 : (nseg > p.nz ? p.nz : nseg);
-  const int seg_len = (p.nz + nseg - 1) / nseg;
-  nseg = (p.nz + seg_len - 1) / seg_len;
-  march3d_kernel<ST, EDM><<<dim3(bx, by, nseg), dim3(kMarchTX, kMarchTY, 1), sm, s>>>(
-      ST::reader(fa, (unsigned)p.N), ST::writer(fb, (unsigned)p.N), (const T*)psi, p, seg_len);
+  // one CTA per resident slot, each with an equal share of the columns' planes (a grid
+  // of bx by z-segment blocks left a partial second wave)
+  const long long work = (long long)bx * by * p.nz;
+  long long grid = (long long)h.num_sms * per_sm;
+  if (grid > work) grid = work;
+  march3d_kernel<ST, EDM><<<(unsigned)grid, dim3(kMarchTX, kMarchTY, 1), sm, s>>>(
+      ST::reader(fa, (unsigned)p.N), ST::writer(fb, (unsigned)p.N), (const T*)psi, p, bx, work);
   return cudaGetLastError();
 }
 

@@ -1,6 +1,7 @@
 // lb_march3d.cuh -- the collision half of the D3Q27 step, marching along z.
 //
-// A block owns a 32 x 8 column of sites and walks it through a z segment. Shared memory
+// A block walks 32 x 8 columns of sites through z segments: the launch has one CTA per
+// resident slot and splits all columns' planes evenly between them. Shared memory
 // holds two rings of planes:
 //   psi ring     3 planes of psi on the column plus a halo of smax + 1 (from the psi
 //                array written by moments_kernel; the plane beyond a z wall holds the
@@ -57,7 +58,7 @@ __device__ __forceinline__ void grad_ring(const T* __restrict__ pm, const T* __r
 template <typename ST, bool EDM>
 __global__ void __launch_bounds__(kMarchTX * kMarchTY, (sizeof(typename ST::Compute) == 4 ? 2 : 1))
 march3d_kernel(typename ST::Reader f, typename ST::Writer fout, const typename ST::Compute* __restrict__ psi,
-               StepT<typename ST::Compute> p, int seg_len) {
+               StepT<typename ST::Compute> p, int ncol_x, long long work) {
   using T = typename ST::Compute;
   constexpr int Q = 27, TX = kMarchTX, TY = kMarchTY, NT = TX * TY;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -66,14 +67,22 @@ march3d_kernel(typename ST::Reader f, typename ST::Writer fout, const typename S
   const int GX = TX + 2 * S, GY = TY + 2 * S, GXY = GX * GY;
   T* s_psi = reinterpret_cast<T*>(smem_raw);  // [3][RXY]
   T* s_ng = s_psi + 3 * RXY;                   // [W][4][GXY]: n_x, n_y, n_z, |grad psi|
-  const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
-  const int zs = blockIdx.z * seg_len;
-  const int ze = min(zs + seg_len, p.nz);
   const int tx = threadIdx.x, ty = threadIdx.y, tid = tx + TX * ty;
-  const int x = x0 + tx, y = y0 + ty;
-  const bool col_active = x < p.nx && y < p.ny;
   auto ring3 = [](int q) { int r = q % 3; return r < 0 ? r + 3 : r; };
   auto ringW = [W](int q) { int r = q % W; return r < 0 ? r + W : r; };
+
+  // The work is every column's nz planes, numbered column by column; each of the
+  // gridDim.x CTAs (the resident ones) takes an equal share and marches through the
+  // column segments in it, filling its rings afresh at each segment's start.
+  const long long w0 = work * blockIdx.x / gridDim.x, w1 = work * (blockIdx.x + 1) / gridDim.x;
+  for (long long w = w0; w < w1;) {
+  const int col = (int)(w / p.nz);
+  const int zs = (int)(w - (long long)col * p.nz);
+  const int ze = (int)min((long long)p.nz, zs + (w1 - w));
+  w += ze - zs;
+  const int x0 = (col % ncol_x) * TX, y0 = (col / ncol_x) * TY;
+  const int x = x0 + tx, y = y0 + ty;
+  const bool col_active = x < p.nx && y < p.ny;
 
   // psi plane q (beyond a z wall only the first plane is read: the mirror of the wall
   // plane): this thread's cells c = tid + k NT, loaded into registers, then stored.
@@ -147,6 +156,7 @@ march3d_kernel(typename ST::Reader f, typename ST::Writer fout, const typename S
       T frep[3] = {T(0), T(0), T(0)};
       if (S > 0 && g > p.g_th) {
         int hit = 0;
+        T A = T(0);  // A_h(h) of the hit (indexed at compile time: no local copy of p)
         static_for<kMaxProbe>([&](auto I) {
           constexpr int st = decltype(I)::value + 1;
           if (hit != 0 || st > S) return;  // found, stopped at a wall, or past h_max
@@ -163,10 +173,9 @@ march3d_kernel(typename ST::Reader f, typename ST::Writer fout, const typename S
           if (!(pl[3 * GXY + cp] > p.g_th)) return;
           T dot = pl[cp] * n0 + pl[GXY + cp] * n1;
           dot += pl[2 * GXY + cp] * n2;
-          if (dot < T(0)) hit = st;
+          if (dot < T(0)) { hit = st; A = p.Ah[st]; }
         });
         if (hit > 0) {
-          const T A = p.Ah[hit];
           const T deltaI = T(0.5) * g;
           frep[0] = -A * n0 * deltaI;
           frep[1] = -A * n1 * deltaI;
@@ -185,6 +194,7 @@ march3d_kernel(typename ST::Reader f, typename ST::Writer fout, const typename S
     if (more) psi_store(q + 1, vnext);
     __syncthreads();
   }
+  }  // column segments
 }
 
 }  // namespace lbnci
