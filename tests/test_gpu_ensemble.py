@@ -1,7 +1,9 @@
 """Ensembles of uneven D2Q9 channels stepped by one batched launch per step (CUDA graph):
 every member must evolve exactly as the same lattice stepped alone, in every precision,
 whatever the number of steps (graph replays plus a single step) and the tile shape the
-autotuner picks; and, in FP64, as the oracle."""
+autotuner picks; and, in FP64, as the oracle. The member sizes mix lattices that run the
+batched TMA kernel (FP32 and FP16-dev with nx % 4 == 0) with lattices that run the one-pass
+batch kernel (nx % 4 != 0), and NCI on with NCI off."""
 import numpy as np
 import pytest
 
@@ -29,7 +31,7 @@ def _lib():
 
 
 @pytest.mark.parametrize("precision,forcing", [(lbnci.LB_FP64, 0), (lbnci.LB_FP32, 0), (lbnci.LB_FP16DEV, 0),
-                                               (lbnci.LB_FP64, 1), (lbnci.LB_FP32, 1)])
+                                               (lbnci.LB_FP64, 1), (lbnci.LB_FP32, 1), (lbnci.LB_FP16DEV, 1)])
 def test_members_match_standalone(precision, forcing):
     cfgs, fields = _cfgs(precision, forcing)
     with lbnci.Ensemble(cfgs) as ens:
