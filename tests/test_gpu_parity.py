@@ -202,18 +202,37 @@ FP32_TOL = 2e-6  # per-step error bound on the population scale (see the design 
 
 def _near_tie_sites(p, f, margin=1e-5):
     """Sites whose NCI decision is within `margin` of a floating-point tie, judged on the
-    oracle's FP64 fields: |grad psi| near g_th at the site or a probe, a probe offset
-    s*n near a half-integer, or a facing test n(y).n(x) near 0."""
+    oracle's FP64 fields: |grad psi| near g_th at the site, or, at a probe of its ray up
+    to the oracle's hit (every probe when there is none), a probe offset s*n near a
+    half-integer, |grad psi| near g_th at the probe, or a facing test n(y).n(x) near 0."""
     of = oracle.fields(p, f)
     N = oracle.N_of(p)
-    g = np.sqrt((of["grad"] ** 2).sum(axis=0))
+    grad = of["grad"]
+    g = np.sqrt((grad ** 2).sum(axis=0))
     near = np.abs(g - p.g_th) < margin
-    # a site next to a near-threshold cell can see its probe decision flip
-    n = np.where(g > 0, -of["grad"] / np.where(g > 0, g, 1), 0.0)
+    n = np.where(g > 0, -grad / np.where(g > 0, g, 1), 0.0)
     iface = g > p.g_th
+    site = np.arange(N)
+    x, y, z = site % p.nx, (site // p.nx) % p.ny, site // (p.nx * p.ny)
+    hit = of["hit"]
     for s in range(1, int(np.floor(p.h_max)) + 1):
-        v = np.abs(s * n)
-        near |= iface & (np.abs(v - np.floor(v) - 0.5) < margin).any(axis=0)
+        v = s * n
+        near |= iface & (np.abs(np.abs(v) - np.floor(np.abs(v)) - 0.5) < margin).any(axis=0)
+        d = (np.sign(v) * np.floor(np.abs(v) + 0.5)).astype(np.int64)  # half away from zero
+        if p.lattice == oracle.D2Q9:
+            d[2] = 0
+        live = iface & ((hit <= 0) | (s <= hit))
+        px = (x + d[0]) % p.nx
+        py, pz = y + d[1], z + d[2]
+        if p.wall_y:
+            live &= (py >= 0) & (py < p.ny)
+        if p.wall_z:
+            live &= (pz >= 0) & (pz < p.nz)
+        probe = px + p.nx * ((py % p.ny) + p.ny * (pz % p.nz))
+        gp = g[probe]
+        dot = (n[:, probe] * n).sum(axis=0)
+        near |= live & (np.abs(gp - p.g_th) < margin)
+        near |= live & (gp > p.g_th) & (np.abs(dot) < margin)
     return near, of
 
 
