@@ -110,14 +110,15 @@ cudaError_t launch_tiled(const void* f, void* fout, const void* psi, const HostP
   return launch_tiled_v<LAT, ST, FIELDS, false>(f, fout, psi, h, p, fo, s);
 }
 
-// D3Q27 collision marching along z (after moments_kernel has written psi).
-template <typename ST, bool EDM>
+// D3Q27 collision marching along z (after moments_kernel has written psi), built for
+// each number of probe steps S = smax.
+template <typename ST, bool EDM, int S>
 cudaError_t launch_march3d_v(const void* fa, void* fb, const void* psi, const HostParams& h,
                              const StepT<typename ST::Compute>& p, cudaStream_t s) {
   using T = typename ST::Compute;
   static size_t configured = 0;
-  const size_t sm = march3d_smem_bytes<T>(p.smax);
-  cudaError_t e = allow_smem(march3d_kernel<ST, EDM>, sm, &configured);
+  const size_t sm = march3d_smem_bytes<T>(S);
+  cudaError_t e = allow_smem(march3d_kernel<ST, EDM, S>, sm, &configured);
   if (e != cudaSuccess) return e;
   const int bx = (p.nx + kMarchTX - 1) / kMarchTX, by = (p.ny + kMarchTY - 1) / kMarchTY;
   const int per_sm = sizeof(T) == 4 ? 2 : 1;
@@ -126,18 +127,31 @@ cudaError_t launch_march3d_v(const void* fa, void* fb, const void* psi, const Ho
   const long long work = (long long)bx * by * p.nz;
   long long grid = (long long)h.num_sms * per_sm;
   if (grid > work) grid = work;
-  march3d_kernel<ST, EDM><<<(unsigned)grid, dim3(kMarchTX, kMarchTY, 1), sm, s>>>(
+  march3d_kernel<ST, EDM, S><<<(unsigned)grid, dim3(kMarchTX, kMarchTY, 1), sm, s>>>(
       ST::reader(fa, (unsigned)p.N), ST::writer(fb, (unsigned)p.N), (const T*)psi, p, bx, work);
   return cudaGetLastError();
+}
+
+template <typename ST, bool EDM>
+cudaError_t launch_march3d_s(const void* fa, void* fb, const void* psi, const HostParams& h,
+                             const StepT<typename ST::Compute>& p, cudaStream_t s) {
+  static_assert(kMaxProbe == 4, "one build per probe count");
+  switch (p.smax) {
+    case 0: return launch_march3d_v<ST, EDM, 0>(fa, fb, psi, h, p, s);
+    case 1: return launch_march3d_v<ST, EDM, 1>(fa, fb, psi, h, p, s);
+    case 2: return launch_march3d_v<ST, EDM, 2>(fa, fb, psi, h, p, s);
+    case 3: return launch_march3d_v<ST, EDM, 3>(fa, fb, psi, h, p, s);
+    default: return launch_march3d_v<ST, EDM, 4>(fa, fb, psi, h, p, s);
+  }
 }
 
 template <typename ST>
 cudaError_t launch_march3d(const void* fa, void* fb, const void* psi, const HostParams& h,
                            const StepT<typename ST::Compute>& p, cudaStream_t s) {
   if constexpr (edm_build_exists<ST>()) {
-    if (p.edm) return launch_march3d_v<ST, true>(fa, fb, psi, h, p, s);
+    if (p.edm) return launch_march3d_s<ST, true>(fa, fb, psi, h, p, s);
   }
-  return launch_march3d_v<ST, false>(fa, fb, psi, h, p, s);
+  return launch_march3d_s<ST, false>(fa, fb, psi, h, p, s);
 }
 
 template <int LAT, typename ST>

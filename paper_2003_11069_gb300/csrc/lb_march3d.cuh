@@ -55,21 +55,24 @@ __device__ __forceinline__ void grad_ring(const T* __restrict__ pm, const T* __r
   g[2] = T(3) * g[2];
 }
 
-template <typename ST, bool EDM>
+// S = smax (number of NCI probe steps) is a template parameter: every extent of the
+// rings, the plane ring's modulus and the probe loop are compile-time constants.
+template <typename ST, bool EDM, int S>
 __global__ void __launch_bounds__(kMarchTX * kMarchTY, (sizeof(typename ST::Compute) == 4 ? 2 : 1))
 march3d_kernel(typename ST::Reader f, typename ST::Writer fout, const typename ST::Compute* __restrict__ psi,
                StepT<typename ST::Compute> p, int ncol_x, long long work) {
   using T = typename ST::Compute;
   constexpr int Q = 27, TX = kMarchTX, TY = kMarchTY, NT = TX * TY;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int S = p.smax, R = S + 1, W = 2 * S + 1;
-  const int RX = TX + 2 * R, RY = TY + 2 * R, RXY = RX * RY;
-  const int GX = TX + 2 * S, GY = TY + 2 * S, GXY = GX * GY;
+  constexpr int R = S + 1, W = 2 * S + 1;
+  constexpr int RX = TX + 2 * R, RY = TY + 2 * R, RXY = RX * RY;
+  constexpr int GX = TX + 2 * S, GY = TY + 2 * S, GXY = GX * GY;
   T* s_psi = reinterpret_cast<T*>(smem_raw);  // [3][RXY]
   T* s_ng = s_psi + 3 * RXY;                   // [W][4][GXY]: n_x, n_y, n_z, |grad psi|
   const int tx = threadIdx.x, ty = threadIdx.y, tid = tx + TX * ty;
-  auto ring3 = [](int q) { int r = q % 3; return r < 0 ? r + 3 : r; };
-  auto ringW = [W](int q) { int r = q % W; return r < 0 ? r + W : r; };
+  // ring slots of plane q >= -(2 S + 1) (the first psi plane and the lowest probe plane)
+  auto ring3 = [](int q) { return (int)((unsigned)(q + 3 * W) % 3u); };
+  auto ringW = [](int q) { return (int)((unsigned)(q + 2 * W) % (unsigned)W); };
 
   // The work is every column's nz planes, numbered column by column; each of the
   // gridDim.x CTAs (the resident ones) takes an equal share and marches through the
@@ -86,7 +89,7 @@ march3d_kernel(typename ST::Reader f, typename ST::Writer fout, const typename S
 
   // psi plane q (beyond a z wall only the first plane is read: the mirror of the wall
   // plane): this thread's cells c = tid + k NT, loaded into registers, then stored.
-  constexpr int kPsiPer = 4;  // cells of a psi plane per thread: RX RY <= kPsiPer NT for smax <= 4
+  constexpr int kPsiPer = (RXY + NT - 1) / NT;  // cells of a psi plane per thread
   auto psi_load = [&](int q, T v[kPsiPer]) {
     if (p.wall_z && (q < -1 || q > p.nz)) return;
     const int gz = p.wall_z ? clampc(q, p.nz) : wrapn(q, p.nz);
