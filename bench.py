@@ -101,10 +101,28 @@ def measured_hbm_peak():
         return HBM_FALLBACK_GBS, "fallback"
 
 
-def kernel_source_hash() -> str:
+def _unit_closure(unit: str) -> list:
+    """A translation unit of the CUDA library and the local headers it includes,
+    transitively (sorted names)."""
+    import re
+    d = os.path.join(ROOT, "paper_2003_11069_gb300", "csrc")
+    seen, todo = set(), [unit]
+    while todo:
+        name = todo.pop()
+        if name in seen or not os.path.exists(os.path.join(d, name)):
+            continue
+        seen.add(name)
+        with open(os.path.join(d, name)) as fh:
+            todo += re.findall(r'^\s*#include\s+"([^"]+)"', fh.read(), re.M)
+    return sorted(seen)
+
+
+def kernel_source_hash(unit: str = None) -> str:
+    """Hash of the CUDA sources: of one translation unit and its headers (the sources
+    a kernel is built from), or of every file when unit is None."""
     h = hashlib.sha256()
     d = os.path.join(ROOT, "paper_2003_11069_gb300", "csrc")
-    for name in sorted(os.listdir(d)):
+    for name in (_unit_closure(unit) if unit else sorted(os.listdir(d))):
         with open(os.path.join(d, name), "rb") as fh:
             h.update(name.encode())
             h.update(fh.read())
@@ -113,13 +131,13 @@ def kernel_source_hash() -> str:
 
 def recorded_traffic(workload: str, precision: str):
     """DRAM bytes per launch from the committed ncu summary, if it was taken on the
-    current kernel sources (else None)."""
+    current sources of the kernel's translation unit (else None)."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         with open(path) as fh:
             rec = json.load(fh)
         ent = rec.get(f"{workload}/{precision}")
-        if ent and ent.get("kernel_sources") == kernel_source_hash():
+        if ent and ent.get("kernel_sources") == kernel_source_hash(ent.get("kernel_unit")):
             return ent.get("dram_bytes_per_step")
     except Exception:
         pass
