@@ -295,9 +295,11 @@ tma2d_kernel(const __grid_constant__ CUtensorMap map_pop, const __grid_constant_
     if (tid == 0) atomicOr(a.err, 2);
     return;
   }
+  // Programmatic dependent launch: the next step's grid may be scheduled now; its CTAs
+  // take the slots this grid's CTAs leave and run their prologue meanwhile.
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
   if (tid == 0) {
     mbar_init(&bar[0], 1);
-    if (blockIdx.x == 0) a.counter[a.parity ^ 1] = 0;  // the next launch's counter
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     if (!BATCH)
       asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<unsigned long long>(&map_pop)) : "memory");
@@ -366,6 +368,12 @@ tma2d_kernel(const __grid_constant__ CUtensorMap map_pop, const __grid_constant_
   auto lo11 = [](unsigned v) { return (int)(v & 2047u); };
   auto mid11 = [](unsigned v) { return (int)((v >> 11) & 2047u); };
   auto row8 = [](unsigned v) { return (int)(v >> 22) - 8; };
+
+  // Up to here only registers and shared memory were touched, so this may have run
+  // while the previous step's grid was finishing. Wait for that grid to complete (its
+  // writes visible) before reading its state or touching the tile counters.
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  if (tid == 0 && blockIdx.x == 0) a.counter[a.parity ^ 1] = 0;  // the next launch's counter
 
   unsigned phase = 0;    // parity of the next completion of the mbarrier
   bool pending = false;  // a TMA load into the stage is in flight
@@ -655,9 +663,21 @@ cudaError_t launch_v(const CUtensorMap& map, const CUtensorMap& map_rho, const v
   if (a.ntiles <= 0) return cudaSuccess;
   const int slots = 2 * num_sms;  // resident CTAs
   const int grid = a.ntiles < slots ? a.ntiles : slots;
-  tma2d_kernel<S, EDM, BATCH, ST><<<grid, NT, kSmemBytes, s>>>(map, map_rho, ST::reader(fa, (unsigned)p.N),
-                                                               ST::writer(fb, (unsigned)p.N), p, a);
-  return cudaGetLastError();
+  // programmatic stream serialisation: the launch may begin while the previous kernel on
+  // the stream finishes; the kernel waits for it (griddepcontrol.wait) before any
+  // global access
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)grid);
+  cfg.blockDim = dim3(NT);
+  cfg.dynamicSmemBytes = kSmemBytes;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, tma2d_kernel<S, EDM, BATCH, ST>, map, map_rho, ST::reader(fa, (unsigned)p.N),
+                            ST::writer(fb, (unsigned)p.N), p, a);
 }
 
 template <bool BATCH, typename ST>

@@ -191,6 +191,31 @@ def test_fp32_tma2d_tiny_and_ragged(nx, ny, walls):
     assert rel[:, ~near].max() <= FP32_TOL, rel[:, ~near].max()
 
 
+@pytest.mark.parametrize("precision", [lbnci.LB_FP32, lbnci.LB_FP16DEV])
+@pytest.mark.parametrize("nx,ny,walls", [(160, 96, 0), (192, 80, 1), (2048, 256, 1)])
+def test_chained_steps_equal_separate_steps(precision, nx, ny, walls):
+    """lb_step(n) launches n steps back to back, and each launch may begin while the
+    previous one finishes (programmatic dependent launch: a CTA's prologue overlaps the
+    previous grid's tail, and it waits for that grid before touching global memory). The
+    chained steps must give exactly the state of the same steps taken one at a time with
+    the stream drained in between, on a periodic-y lattice (every edge tile reads the
+    periodic images of its box with plain loads), a walled one, and the 2048 x 256
+    channel (1024 tiles, several per CTA)."""
+    fl = inputs.channel_emulsion_2d(nx, ny, seed=nx + ny, r_lo=9, r_hi=12)
+    cfg = lbnci.lb_config_make(nx=nx, ny=ny, wall_y=walls, tau=1.0, A_s=0.01, beta=0.7, A_h=0.05,
+                               force=(1e-5, 0, 0), precision=precision)
+    with lbnci.Sim(cfg) as chained, lbnci.Sim(cfg) as single:
+        assert chained.step_path() == lbnci.LB_PATH_TMA2D
+        chained.init_fields(fl.rho1, fl.rho2)
+        single.init_fields(fl.rho1, fl.rho2)
+        chained.step(30)
+        for _ in range(30):
+            single.step(1)
+            single.observables()  # ends with a stream synchronisation
+        assert np.array_equal(chained.get_populations(), single.get_populations())
+        assert chained.observables()["n_nci"] > 0
+
+
 def test_tma_wait_failure_is_reported_and_context_survives(monkeypatch):
     """Failure path of the TMA kernel's bounded waits, without a GPU fault: with
     LBNCI_TMA_STALL_TEST=1 every CTA expects 16 bytes more than its first copy brings, so
