@@ -341,6 +341,22 @@ tma2d_kernel(const __grid_constant__ CUtensorMap map_pop, const __grid_constant_
     else pull_box(bx, c, bym, byp, out);
   };
 
+  // Up to here only shared memory was touched, so this may have run while the previous
+  // step's grid was finishing. Wait for that grid to complete (its writes visible)
+  // before reading its state or touching the tile counters; then the first copy is
+  // issued and the per-thread offsets below are computed while it is in flight.
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  if (tid == 0 && blockIdx.x == 0) a.counter[a.parity ^ 1] = 0;  // the next launch's counter
+
+  unsigned phase = 0;    // parity of the next completion of the mbarrier
+  bool pending = false;  // a TMA load into the stage is in flight
+  int tile = blockIdx.x;
+  TileLoc cur = locate(tile < a.ntiles ? tile : 0);
+  if (tile < a.ntiles) {
+    if (tid == 0) issue(cur);
+    pending = true;
+  }
+
   // This thread's halo cells (tid, tid + NT) and ring cell (tid) are the same in every
   // tile. Each is packed once into one word: offset in the psi region (or, for the
   // ring cell, in the probe region) | offset in the population box (or psi region) << 11
@@ -368,21 +384,6 @@ tma2d_kernel(const __grid_constant__ CUtensorMap map_pop, const __grid_constant_
   auto lo11 = [](unsigned v) { return (int)(v & 2047u); };
   auto mid11 = [](unsigned v) { return (int)((v >> 11) & 2047u); };
   auto row8 = [](unsigned v) { return (int)(v >> 22) - 8; };
-
-  // Up to here only registers and shared memory were touched, so this may have run
-  // while the previous step's grid was finishing. Wait for that grid to complete (its
-  // writes visible) before reading its state or touching the tile counters.
-  asm volatile("griddepcontrol.wait;" ::: "memory");
-  if (tid == 0 && blockIdx.x == 0) a.counter[a.parity ^ 1] = 0;  // the next launch's counter
-
-  unsigned phase = 0;    // parity of the next completion of the mbarrier
-  bool pending = false;  // a TMA load into the stage is in flight
-  int tile = blockIdx.x;
-  TileLoc cur = locate(tile < a.ntiles ? tile : 0);
-  if (tile < a.ntiles) {
-    if (tid == 0) issue(cur);
-    pending = true;
-  }
 
   // Thread 0 reserves tiles one iteration ahead, so the counter's round trip is never
   // waited for: at each tile it publishes the tile reserved before (read by all after
