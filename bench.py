@@ -59,11 +59,11 @@ WORKLOADS = {
                      desc="96 independent D2Q9 channels, length 512-2048, width 64-256, area fraction "
                           "0.7-0.9, G log-uniform 1e-6..1e-4, A_h uniform 0..0.1, one batched launch per "
                           "step (CUDA graph), autotuned tile shape"),
-    "duct3d_small": dict(lattice=1, nx=256, ny=64, nz=64, wall_y=1, wall_z=1, tau=1.0, A_s=0.01, beta=0.7,
+    "duct3d_small": dict(lattice=1, nx=384, ny=96, nz=96, wall_y=1, wall_z=1, tau=1.0, A_s=0.01, beta=0.7,
                          A_h=0.03, force=(2e-6, 0.0, 0.0),
                          gen=lambda nx, ny, nz, seed: inputs.duct_emulsion_3d(nx, ny, nz, seed=seed),
-                         desc="D3Q27 packed-emulsion square duct 256x64x64 (profiling size), walls y,z, FCC "
-                              "droplets R 10, G=2e-6, A_h=0.03"),
+                         desc="D3Q27 packed-emulsion square duct 384x96x96 (profiling size: 3 GB of FP32 "
+                              "state), walls y,z, FCC droplets R 10, G=2e-6, A_h=0.03"),
     "warmstart": dict(lattice=0, nx=0, ny=0, nz=1, wall_y=1, wall_z=0, tau=1.0, A_s=0.01, beta=0.7,
                       A_h=0.0, force=(0.0, 0.0, 0.0), gen=None,
                       desc="U-Net warm start: D2Q9 packed-emulsion channels, length 512-1024, width 64-96, "
