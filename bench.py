@@ -117,15 +117,25 @@ def _unit_closure(unit: str) -> list:
     return sorted(seen)
 
 
+def _code_only(text: str) -> str:
+    """C/C++/CUDA source without comments and with whitespace collapsed (a change to a
+    comment is not a change to the kernel)."""
+    import re
+    text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
+    text = re.sub(r"//[^\n]*", " ", text)
+    return " ".join(text.split())
+
+
 def kernel_source_hash(unit: str = None) -> str:
-    """Hash of the CUDA sources: of one translation unit and its headers (the sources
-    a kernel is built from), or of every file when unit is None."""
+    """Hash of the CUDA code (comments and whitespace ignored): of one translation unit
+    and its headers (the sources a kernel is built from), or of every file when unit is
+    None."""
     h = hashlib.sha256()
     d = os.path.join(ROOT, "paper_2003_11069_gb300", "csrc")
     for name in (_unit_closure(unit) if unit else sorted(os.listdir(d))):
-        with open(os.path.join(d, name), "rb") as fh:
+        with open(os.path.join(d, name), encoding="utf-8") as fh:
             h.update(name.encode())
-            h.update(fh.read())
+            h.update(_code_only(fh.read()).encode())
     return h.hexdigest()[:16]
 
 

@@ -3,8 +3,9 @@
 // Omega = Omega^(3)[Omega^(1) + Omega^(2)] with the near-contact force of Eq. (near_c);
 // the per-site arithmetic is that of lb_kernels.cuh).
 //
-// Persistent CTAs of 512 threads walk 32 x 16 tiles, tile = blockIdx.x + k gridDim.x,
-// one thread per site. The gradient of psi and the NCI ray search at a site read psi
+// Persistent CTAs of 512 threads (two per SM) walk 32 x 16 tiles, one thread per site:
+// tiles blockIdx.x and blockIdx.x + gridDim.x first, then tiles from an atomic counter.
+// The gradient of psi and the NCI ray search at a site read psi
 // up to R = smax + 1 = 5 sites away, and psi at a site is a sum of the 18 populations
 // streamed into it, so a tile needs the populations of its 48 x 28 neighbourhood
 // (x0-8..x0+39, y0-6..y0+21; the x range is widened to keep TMA coordinates 16-byte
@@ -27,6 +28,11 @@
 //            coalesced stores of the 18 new populations.
 // Ragged tiles use the same path: an own position beyond the lattice holds the psi of
 // its periodic image (or, beyond a wall, of its mirror) and stores nothing.
+//
+// Consecutive steps overlap through programmatic dependent launch: a CTA lets the next
+// step's grid be scheduled as soon as it starts; that grid's CTAs take the slots this
+// grid's CTAs leave, initialise their mbarrier and wait for this grid to complete
+// before they read the state or touch the tile counters.
 //
 // Every wait on an mbarrier is bounded (about one second); on expiry the kernel
 // records a flag (bit 0) that the host reports, waits (bounded again) for its own
