@@ -129,7 +129,13 @@ lb_status lb_init_fields(lb_sim* sim, const double* rho1, const double* rho2,
                          const double* u, int on_device);
 
 /* Advance nsteps >= 0 full steps (stream, moments, gradient, NCI, collide,
- * recolour). Asynchronous on cfg->stream. */
+ * recolour). Asynchronous on cfg->stream. On the persistent TMA path
+ * (lb_step_path() == LB_PATH_TMA2D) a step's launch may begin while the kernel before
+ * it on the stream finishes (programmatic dependent launch); it reads and writes
+ * global memory only after that kernel has completed, so results and stream order are
+ * those of serial launches. Errors: LB_EINVAL (NULL sim, nsteps < 0, an ensemble
+ * member), LB_ECUDA (a launch failed; the step counter stops at the last step
+ * launched). */
 lb_status lb_step(lb_sim* sim, long long nsteps);
 
 /* Reductions of the current state (see lb_obs) and, optionally, psi [N] and
