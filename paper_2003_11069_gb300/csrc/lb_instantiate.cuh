@@ -120,14 +120,14 @@ cudaError_t launch_march3d_v(const void* fa, void* fb, const void* psi, const Ho
   const size_t sm = march3d_smem_bytes<T>(S);
   cudaError_t e = allow_smem(march3d_kernel<ST, EDM, S>, sm, &configured);
   if (e != cudaSuccess) return e;
-  const int bx = (p.nx + kMarchTX - 1) / kMarchTX, by = (p.ny + kMarchTY - 1) / kMarchTY;
-  const int per_sm = sizeof(T) == 4 ? 2 : 1;
-  // one CTA per resident slot, each with an equal share of the columns' planes (a grid
-  // of bx by z-segment blocks left a partial second wave)
+  constexpr int TX = MarchTile<T>::TX, TY = MarchTile<T>::TY;
+  const int bx = (p.nx + TX - 1) / TX, by = (p.ny + TY - 1) / TY;
+  // one CTA per SM (the rings fill its shared memory), each with an equal share of the
+  // columns' planes (a grid of bx by z-segment blocks left a partial second wave)
   const long long work = (long long)bx * by * p.nz;
-  long long grid = (long long)h.num_sms * per_sm;
+  long long grid = (long long)h.num_sms;
   if (grid > work) grid = work;
-  march3d_kernel<ST, EDM, S><<<(unsigned)grid, dim3(kMarchTX, kMarchTY, 1), sm, s>>>(
+  march3d_kernel<ST, EDM, S><<<(unsigned)grid, dim3(TX, TY, 1), sm, s>>>(
       ST::reader(fa, (unsigned)p.N), ST::writer(fb, (unsigned)p.N), (const T*)psi, p, bx, work);
   return cudaGetLastError();
 }

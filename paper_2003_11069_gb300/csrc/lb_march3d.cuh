@@ -1,8 +1,12 @@
 // lb_march3d.cuh -- the collision half of the D3Q27 step, marching along z.
 //
-// A block walks 32 x 8 columns of sites through z segments: the launch has one CTA per
-// resident slot and splits all columns' planes evenly between them. Shared memory
-// holds two rings of planes:
+// A block walks columns of 64 x 8 sites (FP32 arithmetic: 512 threads, one CTA per SM;
+// FP64: 32 x 8, 256 threads) through z segments: the launch has one CTA per resident
+// slot and splits all columns' planes evenly between them. A column twice as wide as a
+// 128-byte line halves the share of a warp's shifted pulls that reach into the
+// neighbouring column's lines, which that column's CTA, at another z, has already let
+// go from L2 (32 x 8 columns read the state 1.75 times from DRAM). Shared memory holds
+// two rings of planes:
 //   psi ring     3 planes of psi on the column plus a halo of smax + 1 (from the psi
 //                array written by moments_kernel; the plane beyond a z wall holds the
 //                mirror of the wall plane);
@@ -21,13 +25,19 @@
 
 namespace lbnci {
 
-constexpr int kMarchTX = 32, kMarchTY = 8;
+// Column of a block: 64 x 8 sites for 4-byte arithmetic (the rings take 182 KB for
+// smax = 4), 32 x 8 for FP64 (202 KB).
+template <typename T>
+struct MarchTile {
+  static constexpr int TX = sizeof(T) == 4 ? 64 : 32, TY = 8, NT = TX * TY;
+};
 
 template <typename T>
 size_t march3d_smem_bytes(int smax) {
+  constexpr int TX = MarchTile<T>::TX, TY = MarchTile<T>::TY;
   const int R = smax + 1;
-  const size_t psi = 3 * (size_t)(kMarchTX + 2 * R) * (kMarchTY + 2 * R);
-  const size_t ng = (size_t)(2 * smax + 1) * 4 * (kMarchTX + 2 * smax) * (kMarchTY + 2 * smax);
+  const size_t psi = 3 * (size_t)(TX + 2 * R) * (TY + 2 * R);
+  const size_t ng = (size_t)(2 * smax + 1) * 4 * (TX + 2 * smax) * (TY + 2 * smax);
   return sizeof(T) * (psi + ng);
 }
 
@@ -58,11 +68,11 @@ __device__ __forceinline__ void grad_ring(const T* __restrict__ pm, const T* __r
 // S = smax (number of NCI probe steps) is a template parameter: every extent of the
 // rings, the plane ring's modulus and the probe loop are compile-time constants.
 template <typename ST, bool EDM, int S>
-__global__ void __launch_bounds__(kMarchTX * kMarchTY, (sizeof(typename ST::Compute) == 4 ? 2 : 1))
+__global__ void __launch_bounds__(MarchTile<typename ST::Compute>::NT, 1)
 march3d_kernel(typename ST::Reader f, typename ST::Writer fout, const typename ST::Compute* __restrict__ psi,
                StepT<typename ST::Compute> p, int ncol_x, long long work) {
   using T = typename ST::Compute;
-  constexpr int Q = 27, TX = kMarchTX, TY = kMarchTY, NT = TX * TY;
+  constexpr int Q = 27, TX = MarchTile<T>::TX, TY = MarchTile<T>::TY, NT = TX * TY;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   constexpr int R = S + 1, W = 2 * S + 1;
   constexpr int RX = TX + 2 * R, RY = TY + 2 * R, RXY = RX * RY;
