@@ -11,7 +11,8 @@ lines go back to memory before, not during, the step) and each step is timed alo
 with CUDA events on the library's stream.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--workload channel2d|duct3d|droplet2d] [--precision fp32|fp64]
+                  [--workload channel2d|duct3d|duct3d_small|droplet2d|ensemble|warmstart]
+                  [--precision fp32|fp64|fp16dev]
 
 --impl reference times the FP64 CPU oracle on the host cores (the deliberately slow
 correctness reference, not a tuned CPU code). Under torchrun every rank runs its own
