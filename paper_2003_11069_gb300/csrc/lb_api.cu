@@ -764,16 +764,15 @@ lb_status lb_ensemble_create(const lb_config* cfgs, int n, lb_ensemble** out) {
     c = cudaMemcpyAsync(e->d_members, e->host_members.data(), rec * (nc > 0 ? nc : 1), cudaMemcpyHostToDevice,
                         e->stream);
   if (c == cudaSuccess && nt > 0) {
-    const size_t trec = tma2d_member_bytes();
-    std::vector<unsigned char> ht(trec * nt);
+    std::vector<unsigned char> ht(tma2d_table_bytes(nt));
     for (int k = 0; k < nt; ++k) {
       lb_sim* s = e->members[e->tma[k]];
-      e->tma_tiles += tma2d_member_fill(ht.data() + trec * k, s->maps, s->p, s->fa, s->fb, e->tma_tiles);
+      e->tma_tiles += tma2d_member_fill(ht.data(), k, nt, s->maps, s->p, s->fa, s->fb, e->tma_tiles);
       e->tma_smax = std::max(e->tma_smax, s->p.smax);
     }
-    c = cudaMalloc(&e->d_tma, trec * nt);
+    c = cudaMalloc(&e->d_tma, ht.size());
     if (c == cudaSuccess) c = cudaMalloc((void**)&e->d_tma_flags, 4 * sizeof(int));
-    if (c == cudaSuccess) c = cudaMemcpyAsync(e->d_tma, ht.data(), trec * nt, cudaMemcpyHostToDevice, e->stream);
+    if (c == cudaSuccess) c = cudaMemcpyAsync(e->d_tma, ht.data(), ht.size(), cudaMemcpyHostToDevice, e->stream);
     if (c == cudaSuccess) c = cudaMemsetAsync(e->d_tma_flags, 0, 4 * sizeof(int), e->stream);
     if (c == cudaSuccess) c = cudaStreamSynchronize(e->stream);
     for (int k = 0; k < nt; ++k) e->members[e->tma[k]]->ens_flag = e->d_tma_flags;

@@ -59,12 +59,15 @@ cudaError_t tma2d_prepare(TmaMaps* m, const void* fa, const void* fb, const Host
 // use alternate counters).
 cudaError_t tma2d_step(const TmaMaps& m, int from, const void* fa, void* fb, int* err, int* counter,
                        const HostParams& h, cudaStream_t s);
-// Batched TMA step over the members of an ensemble: a device table of member records
-// (tma2d_member_bytes each, filled on the host by tma2d_member_fill, which returns the
-// member's tile count; tile0 = tiles of the members before it). Members read their
-// buffer `state` and write the other; counter as for tma2d_step, reserved for the batch.
-size_t tma2d_member_bytes();
-int tma2d_member_fill(void* dst, const TmaMaps& m, const HostParams& h, void* buf0, void* buf1, int tile0);
+// Batched TMA step over the members of an ensemble: a device table of tma2d_table_bytes
+// (nmem) bytes, filled on the host by tma2d_member_fill for k = 0 .. nmem - 1 (member
+// records, then a compact index of the members' first tiles and tile grids that the
+// kernel searches; returns the member's tile count; tile0 = tiles of the members before
+// it). Members read their buffer `state` and write the other; counter as for tma2d_step,
+// reserved for the batch.
+size_t tma2d_table_bytes(int nmem);
+int tma2d_member_fill(void* table, int k, int nmem, const TmaMaps& m, const HostParams& h, void* buf0, void* buf1,
+                      int tile0);
 cudaError_t tma2d_batch_step(const void* members, int nmem, int total_tiles, int state, int* err, int* counter,
                              int smax_max, int edm, int half, int num_sms, cudaStream_t s);
 

@@ -235,6 +235,7 @@ struct TmaArgs {
   int parity;    // this launch uses counter[parity] and zeroes counter[parity ^ 1]
   int ntx, ntiles;
   const TmaMember* members;  // batched step: the member table
+  const int4* index;         // batched step: per member {first tile, tile columns, tiles, 0}
   int nmem;
   int state;     // batched step: members read buf[state] and write buf[state ^ 1]
   unsigned stall_bytes;  // failure-path test only: bytes expected on top of the first copy
@@ -315,14 +316,16 @@ tma2d_kernel(const __grid_constant__ CUtensorMap map_pop, const __grid_constant_
   auto locate = [&](int t) {
     TileLoc l{0, 0, 0};
     if constexpr (BATCH) {
+      // last member whose first tile is <= t, searched in the compact index (16 bytes a
+      // member: its lines stay in L1, where the full records, one line apart, do not)
       int lo = 0, hi = a.nmem - 1;
-      while (lo < hi) {  // last member whose first tile is <= t
+      while (lo < hi) {
         const int mid = (lo + hi + 1) >> 1;
-        if (a.members[mid].tile0 <= t) lo = mid; else hi = mid - 1;
+        if (a.index[mid].x <= t) lo = mid; else hi = mid - 1;
       }
       l.m = lo;
-      const TmaMember& mb = a.members[lo];
-      tile_origin(t - mb.tile0, mb.ntx, mb.ntiles, l.x0, l.y0);
+      const int4 e = a.index[lo];
+      tile_origin(t - e.x, e.y, e.z, l.x0, l.y0);
     } else {
       tile_origin(t, a.ntx, a.ntiles, l.x0, l.y0);
     }
@@ -736,9 +739,11 @@ cudaError_t tma2d_step(const TmaMaps& m, int from, const void* fa, void* fb, int
   return launch_any<false>(map, map_rho, fa, fb, p, a, h.smax, h.forcing == 1, h.half != 0, h.num_sms, s);
 }
 
-size_t tma2d_member_bytes() { return sizeof(TmaMember); }
+static_assert(sizeof(TmaMember) % 64 == 0, "member records keep the tensor maps 64-byte aligned and the index 16");
+size_t tma2d_table_bytes(int nmem) { return (size_t)nmem * (sizeof(TmaMember) + sizeof(int4)); }
 
-int tma2d_member_fill(void* dst, const TmaMaps& m, const HostParams& h, void* buf0, void* buf1, int tile0) {
+int tma2d_member_fill(void* table, int k, int nmem, const TmaMaps& m, const HostParams& h, void* buf0, void* buf1,
+                      int tile0) {
   static_assert(sizeof(TmaMember::map) == sizeof(TmaMaps::bytes), "member maps");
   TmaMember mb;
   std::memset(&mb, 0, sizeof(mb));
@@ -749,7 +754,9 @@ int tma2d_member_fill(void* dst, const TmaMaps& m, const HostParams& h, void* bu
   mb.ntx = (h.nx + TX - 1) / TX;
   mb.ntiles = mb.ntx * ((h.ny + TY - 1) / TY);
   mb.tile0 = tile0;
-  std::memcpy(dst, &mb, sizeof(mb));
+  std::memcpy((unsigned char*)table + (size_t)k * sizeof(TmaMember), &mb, sizeof(mb));
+  const int4 e = make_int4(tile0, mb.ntx, mb.ntiles, 0);
+  std::memcpy((unsigned char*)table + (size_t)nmem * sizeof(TmaMember) + (size_t)k * sizeof(int4), &e, sizeof(e));
   return mb.ntiles;
 }
 
@@ -762,6 +769,7 @@ cudaError_t tma2d_batch_step(const void* members, int nmem, int total_tiles, int
   a.ntx = 1;
   a.ntiles = total_tiles;
   a.members = (const TmaMember*)members;
+  a.index = (const int4*)((const unsigned char*)members + (size_t)nmem * sizeof(TmaMember));
   a.nmem = nmem;
   a.state = state & 1;
   StepT<float> none;
