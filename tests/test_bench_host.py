@@ -59,3 +59,33 @@ def test_reference_arm_rank_gating():
     line = json.loads(r.stdout.strip().splitlines()[-1])
     assert line["impl"] == "reference" and line["unit"] == "MLUPS" and line["value"] > 0
     assert line["cpu_baseline"]["kind"] == "oracle" and line["e2e"]["h2d_bytes_per_step"] == 0
+
+
+def test_recorded_traffic_follows_the_kernel_code(tmp_path, monkeypatch):
+    """The DRAM traffic recorded from an ncu capture is reported only while the code of the
+    kernel's translation unit and the headers it includes is unchanged: comments and
+    whitespace do not count, any code change does, and files the unit does not include do
+    not either."""
+    sys.path.insert(0, ROOT)
+    import bench
+    csrc = tmp_path / "paper_2003_11069_gb300" / "csrc"
+    csrc.mkdir(parents=True)
+    (csrc / "k.cu").write_text('#include "h.cuh"\n// a kernel\n__global__ void k(int* a) { a[0] = 1; }\n')
+    (csrc / "h.cuh").write_text("#pragma once\n/* helper */ inline int two() { return 2; }\n")
+    (csrc / "other.cuh").write_text("inline int three() { return 3; }\n")
+    prof = tmp_path / "profiles"
+    prof.mkdir()
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    assert bench._unit_closure("k.cu") == ["h.cuh", "k.cu"]
+    h0 = bench.kernel_source_hash("k.cu")
+    (prof / "traffic.json").write_text(json.dumps({"w/fp32": {"kernel_unit": "k.cu", "kernel_sources": h0,
+                                                                "dram_bytes_per_step": 123}}))
+    assert bench.recorded_traffic("w", "fp32") == 123
+    (csrc / "k.cu").write_text('#include "h.cuh"\n// the kernel, reworded\n__global__ void k(int* a)\n{ a[0] = 1; }\n')
+    (csrc / "other.cuh").write_text("inline int three() { return 4; }\n")
+    assert bench.kernel_source_hash("k.cu") == h0
+    assert bench.recorded_traffic("w", "fp32") == 123
+    (csrc / "h.cuh").write_text("#pragma once\n/* helper */ inline int two() { return 3; }\n")
+    assert bench.kernel_source_hash("k.cu") != h0
+    assert bench.recorded_traffic("w", "fp32") is None
+    assert bench.recorded_traffic("w", "fp64") is None
