@@ -62,6 +62,26 @@ def test_config_validation(bad, status):
     assert lbnci.lb_last_error(None)
 
 
+@pytest.mark.parametrize("lattice,nx,ny,nz,ok", [
+    (0, 16384, 14563, 1, True),    # 18 N = 4,294,803,456 < 2^32
+    (0, 16384, 14564, 1, False),   # 18 N = 4,295,098,368
+    (1, 512, 512, 303, True),      # 54 N = 4,289,200,128
+    (1, 512, 512, 304, False),     # 54 N = 4,303,355,904
+])
+def test_population_index_bound(lattice, nx, ny, nz, ok):
+    """Population indices are 32-bit: a lattice with 2 Q N >= 2^32 is rejected before
+    anything is allocated; the largest one below the bound is accepted."""
+    cfg = lbnci.lb_config_make(lattice=lattice, nx=nx, ny=ny, nz=nz, wall_y=1, wall_z=int(lattice == 1),
+                               precision=lbnci.LB_FP32)
+    if ok:
+        assert lbnci.lb_workspace_size(cfg) > 2 * (18 if lattice == 0 else 54) * nx * ny * nz * 4
+    else:
+        with pytest.raises(lbnci.LBError) as ei:
+            lbnci.lb_workspace_size(cfg)
+        assert ei.value.status == lbnci.LB_EINVAL
+        assert "2^32" in lbnci.lb_last_error(None)
+
+
 def test_workspace_size_formula():
     for lat, nz, prec, state, psi, Q in ((0, 1, lbnci.LB_FP64, 8 * 18, 8, 9), (0, 1, lbnci.LB_FP32, 4 * 18, 4, 9),
                                          (1, 6, lbnci.LB_FP32, 4 * 54, 4, 27),
