@@ -158,6 +158,37 @@ def test_fp64_mass_conservation_long():
     assert o["n_nci"] > 0
 
 
+@pytest.mark.parametrize("A_h", [0.0, 0.05])
+def test_fp64_droplet_2000_steps_laplace_and_mass(A_h):
+    """The plain-method FP64 case: a droplet of radius 30 (tanh profile, width 2) in a
+    periodic 128 x 128 box, tau = 1, A_s = 0.01, beta = 0.7, 2000 steps, with and without
+    NCI. The GPU state equals the oracle's (1e-12 on the population scale; in practice
+    bitwise), each component's mass is kept to rounding, and the pressure jump
+    c_s^2 (rho_in - rho_out) is within 20% of sigma/R with sigma = 4 A_s tau/9 (a single
+    radius carries the intercept of the fit; the slope is pinned on the oracle across
+    radii). With one droplet no interface faces another within h_max: NCI stays off."""
+    n, R, A_s, tau = 128, 30.0, 0.01, 1.0
+    p = oracle.make_params(nx=n, ny=n, tau=tau, A_s=A_s, beta=0.7, A_h=A_h)
+    fl = inputs.droplet(n, n, radius=R)
+    with lbnci.Sim(_cfg(p)) as sim:
+        sim.init_fields(fl.rho1, fl.rho2)
+        f0 = sim.get_populations()
+        m0 = sim.observables()["mass"]
+        sim.step(2000)
+        got = sim.get_populations()
+        obs = sim.observables()
+        fd = sim.fields()
+    ref = oracle.step(p, f0, 2000)
+    assert _max_rel(p, got, ref) <= FP64_RTOL
+    assert np.all(np.abs(obs["mass"] - m0) / m0 < 1e-12)
+    rho = (fd["rho1"] + fd["rho2"]).reshape(n, n)
+    dp = (rho[n // 2, n // 2] - rho[0, 0]) / 3.0
+    sigma = 4 * A_s * tau / 9
+    assert abs(dp / (sigma / R) - 1) < 0.2, dp / (sigma / R)
+    assert np.max(np.abs(fd["u"])) < 5e-4
+    assert obs["n_nci"] == 0
+
+
 def test_zero_steps_and_tiny_lattices():
     """nsteps = 0 leaves the state unchanged; 1-wide periodic axes and a one-row walled
     channel match the oracle."""
