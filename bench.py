@@ -548,7 +548,7 @@ def main_ensemble(args, w, lbnci, torch, ws, rank, local, dist):
                    "l2": "state larger than L2 (not flushed)", **extra,
                    "speedup_vs_one_launch_per_member": round(seq / ms_per_step, 3) if seq else None},
         "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-                     "frac": round(achieved / peak, 4), "traffic": None,
+                     "frac": round(achieved / peak, 4), "traffic": recorded_traffic(args.workload, args.precision),
                      "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)", "kernel": extra["step_kernels"],
                      "alg_bytes_per_site": bpsite},
         "cpu_baseline": None, "e2e": None, "gpu_launches": int(launches), "clocks": clocks,
