@@ -114,22 +114,34 @@ typedef struct {
   long long n_bad;       /* sites with a non-finite or non-positive density */
 } lb_obs;
 
-/* Device bytes lb_create needs when it is given a workspace (cfg->workspace). */
+/* Device bytes lb_create needs when it is given a workspace (cfg->workspace): two
+ * population states of the two sets f^k_i of Eq. (CGLBE) plus scratch. */
 lb_status lb_workspace_size(const lb_config* cfg, size_t* bytes);
 
 /* Validate cfg, take the current CUDA device, allocate (or carve from the
  * workspace) two population buffers and scratch. The populations start at zero:
- * call lb_init_fields or lb_set_populations before lb_step. */
+ * call lb_init_fields or lb_set_populations before lb_step. The model is the
+ * two-component lattice Boltzmann equation, Eq. (CGLBE) of "Materials and Methods",
+ * on the D2Q9 or D3Q27 lattice with the parameters of lb_config (tau of Omega^(1), A_s
+ * of Omega^(2), beta of Omega^(3), A_h, h_min, h_max of Eq. (near_c)). Errors:
+ * LB_EINVAL (bad configuration), LB_ENOMEM, LB_ECUDA (no usable GPU). */
 lb_status lb_create(const lb_config* cfg, lb_sim** out);
 
 /* f^k_i = f_eq_i(rho_k, u) (second-order equilibrium, c_s^2 = 1/3) at every site:
- * the state of a mixture at rest or moving with u, taken as post-collision at t = 0.
- * rho1, rho2: [N]; u: [3][N] or NULL for u = 0. Resets the step counter. */
+ * the state of a mixture at rest or moving with u, taken as post-collision at t = 0
+ * (the densities rho_k of Eq. (CGLBE); psi = (rho1 - rho2)/(rho1 + rho2) follows).
+ * rho1, rho2: [N]; u: [3][N] or NULL for u = 0. Resets the step counter. Walls come
+ * from cfg->wall_y / wall_z (the channels and ducts of the paper's studies); there is
+ * no per-site solid mask. Non-finite or negative values are not rejected here: they are
+ * reported by the next lb_observables / lb_fields as LB_ENUMERIC. Errors: LB_EINVAL
+ * (NULL rho1 or rho2), LB_ECUDA. */
 lb_status lb_init_fields(lb_sim* sim, const double* rho1, const double* rho2,
                          const double* u, int on_device);
 
-/* Advance nsteps >= 0 full steps (stream, moments, gradient, NCI, collide,
- * recolour). Asynchronous on cfg->stream. On the persistent TMA path
+/* Advance nsteps >= 0 full steps of Eq. (CGLBE) ("Materials and Methods"): stream,
+ * moments, gradient of psi, normal n and delta_I, the NCI ray and F_rep of Eq. (near_c),
+ * then the collision Omega^(3)[Omega^(1) + Omega^(2)] (BGK with the force, the
+ * surface-tension perturbation, recolouring). Asynchronous on cfg->stream. On the persistent TMA path
  * (lb_step_path() == LB_PATH_TMA2D) a step's launch may begin while the kernel before
  * it on the stream finishes (programmatic dependent launch); it reads and writes
  * global memory only after that kernel has completed, so results and stream order are
@@ -139,7 +151,9 @@ lb_status lb_init_fields(lb_sim* sim, const double* rho1, const double* rho2,
 lb_status lb_step(lb_sim* sim, long long nsteps);
 
 /* Reductions of the current state (see lb_obs) and, optionally, psi [N] and
- * u [3][N]. The macroscopic fields are those the next collision would see:
+ * u [3][N]. flow_rate_disp, (1/nx) sum rho_1 u_x, is the periodic-channel stand-in for the
+ * dispersed-phase flow rate Q_d = nu V_d of the paper's "Results" (droplets of volume
+ * V_d passing at frequency nu). The macroscopic fields are those the next collision would see:
  * densities of the streamed populations and u = (j + F/2)/rho with F = G + F_rep.
  * Synchronises cfg->stream. Returns LB_ENUMERIC (with out filled) if n_bad > 0. */
 lb_status lb_observables(lb_sim* sim, lb_obs* out, double* psi_out, double* u_out,
@@ -147,12 +161,15 @@ lb_status lb_observables(lb_sim* sim, lb_obs* out, double* psi_out, double* u_ou
 
 /* Per-site fields of the current state, each optional (NULL = skip):
  * rho1, rho2, psi [N]; grad psi, F_rep, u [3][N]; hit [N] = NCI distance h
- * (0 where no facing interface was found). Synchronises cfg->stream. */
+ * (0 where no facing interface was found). psi and its gradient as defined after
+ * Eq. (stjump), h(x) as sketched in Fig. 5, F_rep = -A_h(h) n delta_I by Eq. (near_c).
+ * Synchronises cfg->stream. Returns LB_ENUMERIC (outputs filled) if a density is
+ * non-finite or non-positive. */
 lb_status lb_fields(lb_sim* sim, double* rho1, double* rho2, double* psi, double* grad,
                     double* frep, int* hit, double* u, int on_device);
 
-/* Copy the populations out of / into the sim as FP64 [2][Q][N] (decoded from / encoded
- * to the storage precision; LB_FP16DEV takes each site's reference densities as the
+/* Copy the populations f^k_i of Eq. (CGLBE) out of / into the sim as FP64 [2][Q][N]
+ * (decoded from / encoded to the storage precision; LB_FP16DEV takes each site's reference densities as the
  * sums of the given populations). lb_set_populations resets the step counter. */
 lb_status lb_get_populations(lb_sim* sim, double* f, int on_device);
 lb_status lb_set_populations(lb_sim* sim, const double* f, int on_device);
@@ -213,22 +230,22 @@ const char* lb_ensemble_last_error(const lb_ensemble* ens);
 void lb_ensemble_destroy(lb_ensemble* ens);
 
 /* Observables with no allocation at all. The paper has no counterpart: this is a
- * convenience for callers that cannot let a library allocate device memory (work
- * recorded into a CUDA graph, where cudaMalloc is not allowed during capture; an
- * application whose device memory is fully reserved by its own pool; a loop that
- * must not risk the device synchronisation a cudaMalloc can cause).
+ * convenience for callers that cannot let a library allocate device memory (an
+ * application whose device memory is fully reserved by its own pool allocator; a loop
+ * that must not risk the device synchronisation a cudaMalloc can cause).
  * Computes exactly what lb_observables reports (step is set to 0) for the caller's
  * populations f: a device array [2][Q][N] in the storage type of cfg->precision
  * (double for LB_FP64, float for LB_FP32), laid out as lb_get_populations describes.
- * cfg->workspace is ignored; work runs on cfg->stream and the call synchronises it.
+ * cfg->workspace is ignored; work runs on cfg->stream, and the call copies its result
+ * to the host and synchronises cfg->stream before it returns.
  * Scratch comes from a fixed 8 MiB static device array inside the library (held by
  * every GPU that loads it until the process exits), so lattices are limited to about
  * 2 million sites in FP32 and 1 million in FP64; larger ones return LB_EINVAL with
- * the sizes in lb_last_error(NULL). The first call on a device looks up the array's
- * device address (and may load the library's device code): make that first call
- * before any stream capture. All calls share the array: calls that overlap on the
- * GPU (other streams, other host threads on the same device) race and must not be
- * issued. Returns LB_ENUMERIC (with out filled) if n_bad > 0. */
+ * the sizes in lb_last_error(NULL). Every call looks up the array's device address on
+ * the current device (the first call on a device may load the library's device code).
+ * All calls share the array: calls that overlap on the GPU (other streams, other host
+ * threads on the same device) race and must not be issued. Returns LB_ENUMERIC (with
+ * out filled) if n_bad > 0. */
 lb_status lb_observables_noalloc(const lb_config* cfg, const void* f, lb_obs* out);
 
 #ifdef __cplusplus

@@ -9,7 +9,6 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
-#include <mutex>
 #include <vector>
 #include <new>
 
@@ -516,13 +515,13 @@ int lb_step_path(const lb_sim* s) {
 // ---------------------------------------------------------------------------------
 // Observables without any allocation (lb_observables_noalloc).
 //
-// Some callers cannot let a library allocate device memory: code that records work
-// into a CUDA graph (cudaMalloc is not allowed while a stream is being captured),
-// applications whose device memory is fully reserved by their own pool allocator (a
-// raw cudaMalloc would fail or fragment it), and latency-critical loops in which a
-// cudaMalloc, which may synchronise the device, is not acceptable. For them this
-// entry point computes the same reductions as lb_observables from a population array
-// they already own, using only the fixed scratch array below.
+// Some callers cannot let a library allocate device memory: applications whose device
+// memory is fully reserved by their own pool allocator (a raw cudaMalloc would fail or
+// fragment it), and latency-critical loops in which a cudaMalloc, which may synchronise
+// the device, is not acceptable. For them this entry point computes the same
+// reductions as lb_observables from a population array they already own, using only
+// the fixed scratch array below. Like lb_observables it copies its result to the host
+// and synchronises the caller's stream before it returns.
 //
 // The scratch lives in this translation unit for the whole life of the process: every
 // GPU that loads the library holds kNoAllocScratchBytes of it. All calls share it and
@@ -535,27 +534,22 @@ namespace {
 constexpr size_t kNoAllocScratchBytes = size_t(8) << 20;  // 8 MiB per device
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
 
-constexpr int kMaxDevices = 64;
-std::mutex g_noalloc_mu;
-void* g_noalloc_ptr[kMaxDevices] = {};
-
-// Device address of the scratch array on the current device. In host code the
-// array's name is only a host-side stand-in, so its device address is looked up once
-// per device (with that device current) and cached.
+// Device address of the scratch array on the current device. In host code the array's
+// name is only a host-side stand-in, so its device address is looked up with the
+// device current, on every call: an address kept from an earlier call would be stale
+// after the device's primary context was reset and recreated.
 lb_status noalloc_scratch(void** out) {
   int dev = -1;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return fail(nullptr, LB_ECUDA, "no CUDA device: %s", cudaGetErrorString(e));
-  if (dev < 0 || dev >= kMaxDevices) return fail(nullptr, LB_EUNSUPPORTED, "device ordinal %d out of range", dev);
-  std::lock_guard<std::mutex> lock(g_noalloc_mu);
-  if (!g_noalloc_ptr[dev]) {
-    void* p = nullptr;
-    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-    if (e != cudaSuccess || !p)
-      return fail(nullptr, LB_ECUDA, "cudaGetSymbolAddress of the scratch array failed: %s", cudaGetErrorString(e));
-    g_noalloc_ptr[dev] = p;
+  void* p = nullptr;
+  e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+  if (e != cudaSuccess || !p) {
+    cudaGetLastError();
+    return fail(nullptr, LB_ECUDA, "cudaGetSymbolAddress of the scratch array on device %d failed: %s", dev,
+                cudaGetErrorString(e));
   }
-  *out = g_noalloc_ptr[dev];
+  *out = p;
   return LB_OK;
 }
 

@@ -45,13 +45,6 @@ template <int LAT> dim3 tiled_block() { return dim3(Tile<LAT>::X, Tile<LAT>::Y, 
 
 inline unsigned blocks_for(long long n, int t) { return (unsigned)((n + t - 1) / t); }
 
-template <typename K>
-cudaError_t allow_smem(K kernel, size_t bytes, size_t* configured) {
-  if (bytes <= 48 * 1024 || bytes <= *configured) return cudaSuccess;
-  cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-  if (e == cudaSuccess) *configured = bytes;
-  return e;
-}
 
 // Sites per thread of the fused D2Q9 kernel (2: 32x16 tiles, 4: 32x32 tiles).
 // FP32 kernels come in a Guo and an EDM build; FP64 has one (it checks p.edm itself).
@@ -61,9 +54,9 @@ constexpr bool edm_build_exists() { return !std::is_same<typename ST::Compute, d
 template <typename ST, int SPT, bool EDM>
 cudaError_t launch_fused2d_v(const void* fa, void* fb, const StepT<typename ST::Compute>& p, cudaStream_t s) {
   using T = typename ST::Compute;
-  static size_t configured = 0;
+  static SmemAllowance configured;
   const size_t sm = fused2d_smem_bytes<T>(p.smax, SPT);
-  cudaError_t e = allow_smem(fused2d_kernel<ST, SPT, EDM>, sm, &configured);
+  cudaError_t e = allow_smem(fused2d_kernel<ST, SPT, EDM>, sm, configured);
   if (e != cudaSuccess) return e;
   const dim3 grid((p.nx + kFusedTX - 1) / kFusedTX, (p.ny + kFusedThreadsY * SPT - 1) / (kFusedThreadsY * SPT), 1);
   fused2d_kernel<ST, SPT, EDM><<<grid, dim3(kFusedTX, kFusedThreadsY, 1), sm, s>>>(
@@ -91,9 +84,9 @@ template <int LAT, typename ST, bool FIELDS, bool EDM = false>
 cudaError_t launch_tiled_v(const void* f, void* fout, const void* psi, const HostParams& h,
                            const StepT<typename ST::Compute>& p, const FieldOut& fo, cudaStream_t s) {
   using T = typename ST::Compute;
-  static size_t configured = 0;
+  static SmemAllowance configured;
   const size_t sm = tiled_smem_bytes<LAT, T>(p.smax);
-  cudaError_t e = allow_smem(tiled_kernel<LAT, ST, FIELDS, EDM>, sm, &configured);
+  cudaError_t e = allow_smem(tiled_kernel<LAT, ST, FIELDS, EDM>, sm, configured);
   if (e != cudaSuccess) return e;
   typename ST::Writer w = FIELDS ? typename ST::Writer{} : ST::writer(fout, (unsigned)p.N);
   tiled_kernel<LAT, ST, FIELDS, EDM><<<tiled_grid<LAT>(h), tiled_block<LAT>(), sm, s>>>(
@@ -116,9 +109,9 @@ template <typename ST, bool EDM, int S>
 cudaError_t launch_march3d_v(const void* fa, void* fb, const void* psi, const HostParams& h,
                              const StepT<typename ST::Compute>& p, cudaStream_t s) {
   using T = typename ST::Compute;
-  static size_t configured = 0;
+  static SmemAllowance configured;
   const size_t sm = march3d_smem_bytes<T>(S);
-  cudaError_t e = allow_smem(march3d_kernel<ST, EDM, S>, sm, &configured);
+  cudaError_t e = allow_smem(march3d_kernel<ST, EDM, S>, sm, configured);
   if (e != cudaSuccess) return e;
   constexpr int TX = MarchTile<T>::TX, TY = MarchTile<T>::TY;
   const int bx = (p.nx + TX - 1) / TX, by = (p.ny + TY - 1) / TY;
@@ -214,9 +207,9 @@ int l_batch_tiles(const HostParams& h, int spt) {
 template <typename ST, int SPT, bool EDM>
 cudaError_t launch_batch_v(const void* members, const int* tile0, int n, int total_tiles, int parity,
                            int smax_max, cudaStream_t s) {
-  static size_t configured = 0;
+  static SmemAllowance configured;
   const size_t sm = fused2d_smem_bytes<typename ST::Compute>(smax_max, SPT);
-  cudaError_t e = allow_smem(fused2d_batch_kernel<ST, SPT, EDM>, sm, &configured);
+  cudaError_t e = allow_smem(fused2d_batch_kernel<ST, SPT, EDM>, sm, configured);
   if (e != cudaSuccess) return e;
   fused2d_batch_kernel<ST, SPT, EDM><<<total_tiles, dim3(kFusedTX, kFusedThreadsY, 1), sm, s>>>(
       (const BatchMember<typename ST::Compute>*)members, tile0, n, parity);

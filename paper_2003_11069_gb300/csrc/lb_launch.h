@@ -4,9 +4,37 @@
 
 #include <cuda_runtime.h>
 
+#include <atomic>
+
 #include "lb_lattice.cuh"
 
 namespace lbnci {
+
+// The largest dynamic shared memory each device has been told a kernel may use.
+// cudaFuncSetAttribute applies to the current device only, so a process that launches
+// on several devices needs one record per device; two threads that race here may both
+// set the attribute, which is harmless.
+constexpr int kMaxDevices = 64;
+struct SmemAllowance {
+  std::atomic<size_t> bytes[kMaxDevices];
+};
+
+template <typename K>
+cudaError_t allow_smem(K kernel, size_t bytes, SmemAllowance& a) {
+  if (bytes <= 48 * 1024) return cudaSuccess;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  const bool tracked = dev >= 0 && dev < kMaxDevices;
+  if (tracked && a.bytes[dev].load(std::memory_order_acquire) >= bytes) return cudaSuccess;
+  e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (e == cudaSuccess && tracked) {
+    size_t cur = a.bytes[dev].load(std::memory_order_acquire);
+    while (cur < bytes && !a.bytes[dev].compare_exchange_weak(cur, bytes, std::memory_order_acq_rel)) {
+    }
+  }
+  return e;
+}
 
 // Everything a launcher needs, in FP64; each instantiation converts it to its own
 // arithmetic type once per call.

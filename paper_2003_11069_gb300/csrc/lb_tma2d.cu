@@ -665,13 +665,9 @@ bool encode_rho(CUtensorMap* m, const void* base, const HostParams& h) {
 template <int S, bool EDM, bool BATCH, typename ST>
 cudaError_t launch_v(const CUtensorMap& map, const CUtensorMap& map_rho, const void* fa, void* fb,
                      const StepT<float>& p, TmaArgs a, int num_sms, cudaStream_t s) {
-  static bool configured = false;
-  if (!configured) {
-    cudaError_t e = cudaFuncSetAttribute(tma2d_kernel<S, EDM, BATCH, ST>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
-    if (e != cudaSuccess) return e;
-    configured = true;
-  }
+  static SmemAllowance configured;
+  cudaError_t e = allow_smem(tma2d_kernel<S, EDM, BATCH, ST>, kSmemBytes, configured);
+  if (e != cudaSuccess) return e;
   if (a.ntiles <= 0) return cudaSuccess;
   const int slots = 2 * num_sms;  // resident CTAs
   const int grid = a.ntiles < slots ? a.ntiles : slots;

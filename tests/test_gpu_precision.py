@@ -14,6 +14,8 @@ import pytest
 import oracle
 from paper_2003_11069_gb300 import inputs, lbnci
 
+from test_gpu_parity import _near_tie_sites
+
 pytestmark = pytest.mark.gpu
 
 FP16DEV_STEP_TOL = 3e-4
@@ -79,11 +81,16 @@ def test_fp16dev_one_step_tolerance(lat):
         sim.step(1)
         got = sim.get_populations()
     ref = oracle.step(p, fq, 1)
-    of = oracle.fields(p, fq)
+    # both sides start from the same representable state and decide in FP32 / FP64: NCI
+    # decisions may differ only at FP32 near-ties, and a site's new populations depend on
+    # its own decision only
+    near, of = _near_tie_sites(p, fq)
     Q, N = oracle.Q_of(p), oracle.N_of(p)
-    ok = fields["hit"] == of["hit"]
-    assert ok.mean() > 0.99
+    differ = fields["hit"] != of["hit"]
+    assert not (differ & ~near).any(), f"{int((differ & ~near).sum())} NCI decisions differ away from ties"
     rel = (np.abs(got - ref) / _scale(p, ref)).reshape(2 * Q, N)
+    ok = ~near
+    assert (of["hit"][ok] > 0).sum() > 0
     assert rel[:, ok].max() <= FP16DEV_STEP_TOL, rel[:, ok].max()
 
 

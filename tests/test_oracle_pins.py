@@ -344,6 +344,25 @@ def test_nci_planar_golden():
     assert np.array_equal(hit3.reshape(ny, nx)[:, 0], exp3)
 
 
+def test_nci_probe_threshold_golden():
+    """The probe-side interface test of the ray (golden fixture): a facing probe with
+    0 < |grad psi| <= g_th is passed over, one just above g_th is a hit."""
+    rows = np.loadtxt(os.path.join(GOLDEN, "nci_probe_threshold_y16.txt"), comments="#")
+    nx, ny, A = 4, 16, 0.05
+    psi = np.repeat(rows[:, 1], nx)
+    p = oracle.make_params(nx=nx, ny=ny, A_h=A, h_min=2.0, h_max=4.0, g_th=0.05)
+    g = oracle.gradient(p, psi)
+    gy = rows[:, 2]
+    assert np.allclose(g[1].reshape(ny, nx), gy[:, None], atol=1e-15)
+    assert np.max(np.abs(g[0])) < 1e-16
+    # the fixture's premise: one weak facing row (0 < |g| <= g_th), one just above g_th
+    assert 0 < abs(gy[3]) <= 0.05 and 0.05 < abs(gy[12]) < 0.07
+    fr, hit = oracle.nci(p, psi)
+    assert np.array_equal(hit.reshape(ny, nx), np.repeat(rows[:, 3].astype(int)[:, None], nx, 1))
+    assert np.allclose(fr[1].reshape(ny, nx), A * rows[:, 4][:, None], atol=1e-15, rtol=1e-14)
+    assert np.max(np.abs(fr[0])) < 1e-16
+
+
 def _diag_expected(prof, g_th, smax):
     """Brute force for psi(x, y) = prof[(x + y) mod L] on an L x L periodic D2Q9 lattice.
     For such fields the isotropic gradient has equal x and y components

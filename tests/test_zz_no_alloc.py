@@ -1,7 +1,7 @@
 """lb_observables_noalloc: the same observables as lb_observables, computed with no
-allocation inside the library (for callers that cannot let it allocate: work being
-captured into a CUDA graph, applications whose device memory belongs to their own
-pool, loops that must not risk the synchronisation a cudaMalloc can cause).
+allocation inside the library (for callers that cannot let it allocate: applications
+whose device memory belongs to their own pool, loops that must not risk the
+synchronisation a cudaMalloc can cause).
 
 Called through the C ABI on device populations the test owns, twice in a row (the
 static scratch keeps the previous call's contents, which must not leak into the next
