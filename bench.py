@@ -1,17 +1,18 @@
 """Benchmark of the fused NCI colour-gradient lattice Boltzmann step on GB300.
 
 One "step" is one full lattice Boltzmann time step (stream, moments, gradient, NCI,
-collide, recolour) over the whole lattice. Default workload: the 2D soft-flowing-
-crystal channel, D2Q9, 2048 x 256 sites, walls at top and bottom, periodic in x,
-packed droplets (radius 12-16, hexagonal rows, area fraction 0.8 target), body force
-1e-5, A_h = 0.05, FP32 storage and arithmetic. Metric: MLUPS (million lattice-site
-updates per second), whole job. The 2048 x 256 lattice fits in L2, so L2 is flushed
+collide, recolour) over the whole lattice. Default workload: the 3D packed emulsion in
+a square duct, D3Q27, 512 x 128 x 128 sites, walls in y and z, periodic in x, FCC-packed
+droplets of radius 10, body force 2e-6, A_h = 0.03, FP32 storage and arithmetic
+(--precision fp16dev: FP16 deviation storage, FP32 arithmetic). Metric: MLUPS (million
+lattice-site updates per second), whole job. The duct's state (3.6 GB for the two
+buffers) is far larger than L2, so K steps are timed back to back with CUDA events on
+the library's stream. Lattices that fit in L2 (the 2048 x 256 channel) are flushed
 before every timed step (a 512 MB write, then a 256 MB read so that the write's dirty
-lines go back to memory before, not during, the step) and each step is timed alone
-with CUDA events on the library's stream.
+lines go back to memory before, not during, the step) and each step is timed alone.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--workload channel2d|duct3d|duct3d_small|droplet2d|ensemble|warmstart]
+                  [--workload duct3d|duct3d_small|channel2d|channel2d_large|droplet2d|ensemble|warmstart]
                   [--precision fp32|fp64|fp16dev]
 
 --impl reference times the FP64 CPU oracle on the host cores (the deliberately slow
@@ -48,12 +49,20 @@ WORKLOADS = {
                       A_h=0.05, force=(1e-5, 0.0, 0.0),
                       gen=lambda nx, ny, nz, seed: inputs.channel_emulsion_2d(nx, ny, seed=seed),
                       desc="D2Q9 soft-flowing-crystal channel 2048x256, walls y, packed droplets R 12-16 "
-                           "af 0.8 target, G=1e-5, A_h=0.05"),
+                           "(hexagonal rows, +-1 jitter, film >= 1: area fraction 0.73 of the 0.8 requested), "
+                           "G=1e-5, A_h=0.05"),
+    "channel2d_large": dict(lattice=0, nx=8192, ny=1024, nz=1, wall_y=1, wall_z=0, tau=1.0, A_s=0.01, beta=0.7,
+                            A_h=0.05, force=(1e-5, 0.0, 0.0),
+                            gen=lambda nx, ny, nz, seed: inputs.channel_emulsion_2d(nx, ny, seed=seed),
+                            desc="D2Q9 soft-flowing-crystal channel 8192x1024 (the 2048x256 channel's generator "
+                                 "at 16x the sites, state 2.4 GB in FP32: larger than L2), walls y, packed "
+                                 "droplets R 12-16, G=1e-5, A_h=0.05"),
     "duct3d": dict(lattice=1, nx=512, ny=128, nz=128, wall_y=1, wall_z=1, tau=1.0, A_s=0.01, beta=0.7,
                    A_h=0.03, force=(2e-6, 0.0, 0.0),
                    gen=lambda nx, ny, nz, seed: inputs.duct_emulsion_3d(nx, ny, nz, seed=seed),
                    desc="D3Q27 packed-emulsion square duct 512x128x128, walls y,z, FCC droplets R 10 "
-                        "vf 0.7 target, G=2e-6, A_h=0.03"),
+                        "(film >= 1: volume fraction 0.54, the most R 10 spheres reach in this duct; 0.7 "
+                        "requested), G=2e-6, A_h=0.03"),
     "ensemble": dict(lattice=0, nx=0, ny=0, nz=1, wall_y=1, wall_z=0, tau=1.0, A_s=0.01, beta=0.7,
                      A_h=0.05, force=(1e-5, 0.0, 0.0), members=96,
                      gen=lambda nx, ny, nz, seed: inputs.channel_emulsion_2d(nx, ny, seed=seed),
@@ -90,6 +99,14 @@ def alg_bytes_per_site(lattice: int, precision: str) -> int:
     Q = 9 if lattice == 0 else 27
     per_site = {"fp64": 2 * Q * 8, "fp32": 2 * Q * 4, "fp16dev": Q * 4 + 8}[precision]
     return 2 * per_site
+
+
+L2_BYTES = 129 << 20
+
+
+def state_bytes(lattice: int, precision: str, N: int) -> int:
+    """Bytes of one population state (one of the two buffers)."""
+    return alg_bytes_per_site(lattice, precision) // 2 * N
 
 
 def measured_hbm_peak():
@@ -379,7 +396,7 @@ def main(argv=None):
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="channel2d", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="duct3d", choices=sorted(WORKLOADS))
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64", "fp16dev"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -422,10 +439,14 @@ def main(argv=None):
     fl = w["gen"](nx, ny, nz, 1234 + rank)
     rho1 = torch.from_numpy(fl.rho1).cuda()
     rho2 = torch.from_numpy(fl.rho2).cuda()
-    flush = torch.empty(max(1, args.flush_mb) << 20, dtype=torch.uint8, device="cuda")
+    flush = torch.empty(max(1, args.flush_mb if state_bytes(w["lattice"], args.precision, N) * 2 <= 4 * L2_BYTES
+                            else 1) << 20, dtype=torch.uint8, device="cuda")
     torch.cuda.synchronize()
 
     sim = lbnci.Sim(cfg, workspace="torch")
+    # a state larger than four times L2 (129 MB) is its own flush: steps run back to back
+    big = state_bytes(w["lattice"], args.precision, N) * 2 > 4 * L2_BYTES
+    flush_mb = 0 if big else args.flush_mb
     with torch.cuda.stream(stream):
         sim.init_fields(rho1, rho2)
         sim.step(args.warmup)
@@ -437,19 +458,27 @@ def main(argv=None):
         torch.cuda.synchronize()
         launches0 = sim.launches()
         with ClockSampler(local) as clk:
-            for k in range(args.steps):
-                if args.flush_mb > 0:
-                    flush.fill_(k & 0xFF)  # evict the lattice from L2 before each timed step
-                    # then read half of it back: the write left L2 full of the flush's dirty
-                    # lines, whose write-back would otherwise land in the timed step
-                    flush[: flush.numel() // 2].max()
-                starts[k].record(stream)
-                sim.step(1)
-                ends[k].record(stream)
+            if big:
+                starts[0].record(stream)
+                sim.step(args.steps)
+                ends[0].record(stream)
+            else:
+                for k in range(args.steps):
+                    if flush_mb > 0:
+                        flush.fill_(k & 0xFF)  # evict the lattice from L2 before each timed step
+                        # then read half of it back: the write left L2 full of the flush's dirty
+                        # lines, whose write-back would otherwise land in the timed step
+                        flush[: flush.numel() // 2].max()
+                    starts[k].record(stream)
+                    sim.step(1)
+                    ends[k].record(stream)
             torch.cuda.synchronize()
         launches = sim.launches() - launches0
         path = sim.step_path()
-        step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+        if big:
+            step_ms = [starts[0].elapsed_time(ends[0])]
+        else:
+            step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
         total_ms = max_over_ranks(float(sum(step_ms)), dist, "cuda")
         if dist:
             dist.barrier()
@@ -504,9 +533,11 @@ def main(argv=None):
         "dtype": {"fp32": "f32", "fp64": "f64", "fp16dev": "f16 storage / f32 compute"}[args.precision],
         "data": "synthetic",
         "config": {"workload": w["desc"], "sites": N, "precision": args.precision,
-                   "l2": (f"flushed before every timed step ({args.flush_mb} MB write, then a "
-                          f"{args.flush_mb // 2} MB read so the flush's dirty lines are written back "
-                          f"before the step); each step timed alone" if args.flush_mb > 0 else "not flushed"),
+                   "l2": (f"state {2 * state_bytes(w['lattice'], args.precision, N) / 1e9:.2f} GB (two buffers), "
+                          f"larger than L2 (129 MB): not flushed, {args.steps} steps timed back to back" if big else
+                          f"flushed before every timed step ({flush_mb} MB write, then a "
+                          f"{flush_mb // 2} MB read so the flush's dirty lines are written back "
+                          f"before the step); each step timed alone" if flush_mb > 0 else "not flushed"),
                    "step_kernel": STEP_KERNELS.get(path, "?"),
                    "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU",
                    "droplets": fl.meta.get("droplets"),
