@@ -74,6 +74,12 @@ WORKLOADS = {
                          gen=lambda nx, ny, nz, seed: inputs.duct_emulsion_3d(nx, ny, nz, seed=seed),
                          desc="D3Q27 packed-emulsion square duct 384x96x96 (profiling size: 3 GB of FP32 "
                               "state), walls y,z, FCC droplets R 10, G=2e-6, A_h=0.03"),
+    "duct3d_profile": dict(lattice=1, nx=512, ny=128, nz=48, wall_y=1, wall_z=1, tau=1.0, A_s=0.01, beta=0.7,
+                           A_h=0.03, force=(2e-6, 0.0, 0.0),
+                           gen=lambda nx, ny, nz, seed: inputs.duct_emulsion_3d(nx, ny, nz, seed=seed),
+                           desc="D3Q27 packed-emulsion duct 512x128x48 (profiling size: the bench duct's 256 "
+                                "columns of 32x8 sites, 1.4 GB of FP32 state), walls y,z, FCC droplets R 10, "
+                                "G=2e-6, A_h=0.03"),
     "warmstart": dict(lattice=0, nx=0, ny=0, nz=1, wall_y=1, wall_z=0, tau=1.0, A_s=0.01, beta=0.7,
                       A_h=0.0, force=(0.0, 0.0, 0.0), gen=None,
                       desc="U-Net warm start: D2Q9 packed-emulsion channels, length 512-1024, width 64-96, "
@@ -89,7 +95,9 @@ WORKLOADS = {
 # The kernels lb_step launches, by lb_step_path().
 STEP_KERNELS = {0: "fused2d_kernel (one-pass D2Q9 step)",
                 1: "tma2d_kernel (persistent TMA-fed D2Q9 step, one launch per step)",
-                2: "moments_kernel + march3d_kernel (D3Q27 step, two launches)"}
+                2: "moments_kernel + march3d_kernel (D3Q27 two-pass step, two launches)",
+                3: "interface3d_kernel + carry3d_kernel (D3Q27 single-read step: densities carried by the "
+                   "previous collision, TMA-fed collision; two launches)"}
 
 
 # Bytes of state moved per site update (1 read + 1 write): FP64/FP32 populations are

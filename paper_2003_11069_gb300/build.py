@@ -24,6 +24,7 @@ UNITS = {
     "lb_fp64.cu": ["--fmad=false"],
     "lb_fp32.cu": [],
     "lb_tma2d.cu": [],
+    "lb_carry3d.cu": [],
     "lb_fp16.cu": [],
     "unet_api.cu": [],
 }

@@ -68,6 +68,12 @@ struct lb_sim {
   int* tile_counter;  // two device ints: tile counters of the TMA step kernel
   const int* ens_flag;  // member of an ensemble stepped by the batched TMA kernel: its error word
   void* psi;       // order parameter of the streamed state
+  void* carry;     // single-read D3Q27 path (p.carry3d): carried densities, ring exports,
+  void* ring;      // ghost planes of the z segments, per-site (n, |grad psi|) and NCI distance
+  void* ghost;
+  void* ng;
+  void* hit;
+  bool carry_ok;   // the carried densities belong to the current state
   double* partials;
   double* result;  // kRedSlots doubles
   double* host_result;  // pinned
@@ -106,7 +112,7 @@ size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
 constexpr int kErrSlot = 12;
 
 struct Layout {
-  size_t fa, fb, psi, partials, result, total;
+  size_t fa, fb, psi, partials, result, carry, ring, ghost, ng, hit, total;
 };
 
 const Launchers* launchers_for(const lb_config* c) {
@@ -171,6 +177,20 @@ lb_status validate(const lb_config* c, HostParams* p, Layout* lay, long long* nb
   // LBNCI_TMA_STALL_TEST=1 makes every CTA's first wait run out after about a second.
   p->tma_stall_test = 0;
   if (const char* e = std::getenv("LBNCI_TMA_STALL_TEST")) p->tma_stall_test = std::atoi(e) == 1 ? 1 : 0;
+  // D3Q27 step on lattices of whole 32 x 8 columns: the single-read kernels (density
+  // carry) for FP16-dev storage, where they are the faster step; FP32 runs the two-pass
+  // step unless LBNCI_D3_KERNEL=carry (LBNCI_D3_KERNEL=march or tiled: the two-pass step
+  // for both)
+  const bool carry_ok = c->lattice == LB_D3Q27 && (c->precision == LB_FP32 || c->precision == LB_FP16DEV) &&
+                        c->nx % 32 == 0 && c->ny % 8 == 0 && (c->wall_z || c->nz >= 2);
+  p->carry3d = carry_ok && c->precision == LB_FP16DEV ? 1 : 0;
+  if (const char* e = std::getenv("LBNCI_D3_KERNEL")) {
+    if (std::strcmp(e, "march") == 0 || std::strcmp(e, "tiled") == 0) p->carry3d = 0;
+    if (std::strcmp(e, "carry") == 0 && carry_ok) p->carry3d = 1;
+  }
+  // z segment of the single-read collision kernel (planes; LBNCI_C3_ZSEG, default 16)
+  p->c3_zseg = 16;
+  if (const char* e = std::getenv("LBNCI_C3_ZSEG")) p->c3_zseg = std::atoi(e) > 0 ? std::atoi(e) : 16;
   const int Q = c->lattice == LB_D2Q9 ? 9 : 27;
   (void)Q;
   const Launchers* L = launchers_for(c);
@@ -182,6 +202,14 @@ lb_status validate(const lb_config* c, HostParams* p, Layout* lay, long long* nb
   lay->psi = off; off = align256(off + (size_t)N * L->compute_elem);
   lay->partials = off; off = align256(off + (size_t)(*nblocks) * kRedSlots * sizeof(double));
   lay->result = off; off = align256(off + 16 * sizeof(double));
+  lay->carry = lay->ring = lay->ghost = lay->ng = lay->hit = off;
+  if (p->carry3d) {
+    lay->carry = off; off = align256(off + (size_t)N * 8);
+    lay->ring = off; off = align256(off + carry3d_ring_bytes(*p));
+    lay->ghost = off; off = align256(off + carry3d_ghost_bytes(*p));
+    lay->ng = off; off = align256(off + (size_t)N * 16);
+    lay->hit = off; off = align256(off + (size_t)N);
+  }
   lay->total = off;
   return LB_OK;
 }
@@ -302,6 +330,18 @@ lb_status lb_create(const lb_config* cfg, lb_sim** out) {
     if (!tma2d_supported(s->p) || tma2d_prepare(&s->maps, s->fa, s->fb, s->p) != cudaSuccess) s->p.tma = 0;
     cudaGetLastError();
   }
+  if (s->p.carry3d) {
+    s->carry = base + lay.carry;
+    s->ring = base + lay.ring;
+    s->ghost = base + lay.ghost;
+    s->ng = base + lay.ng;
+    s->hit = base + lay.hit;
+    // without the driver's tensor-map encoder the step falls back to the two-pass kernels
+    if (!carry3d_supported(s->p) || carry3d_prepare(&s->maps, s->fa, s->fb, s->ng, s->hit, s->p) != cudaSuccess)
+      s->p.carry3d = 0;
+    cudaGetLastError();
+  }
+  s->carry_ok = false;
   e = cudaMallocHost((void**)&s->host_result, 16 * sizeof(double));
   if (e != cudaSuccess) {
     if (s->owns) cudaFree(s->base);
@@ -338,6 +378,7 @@ lb_status lb_init_fields(lb_sim* s, const double* rho1, const double* rho2, cons
   }
   e = s->L->init(s->fa, d1, d2, du, s->p, s->stream);
   ++s->launches;
+  s->carry_ok = false;
   if (e != cudaSuccess) return cuda_fail(s, e, "init launch");
   if (!on_device) {
     e = cudaStreamSynchronize(s->stream);
@@ -358,6 +399,15 @@ lb_status lb_step(lb_sim* s, long long nsteps) {
       e = tma2d_step(s->maps, s->fa == s->buf_a ? 0 : 1, s->fa, s->fb, s->errflag, s->tile_counter, s->p,
                      s->stream);
       nk = 1;
+    } else if (s->p.carry3d) {
+      if (!s->carry_ok) {  // a state no step produced: its densities from the populations
+        e = carry3d_init(s->fa, s->carry, s->ring, s->ghost, s->p, s->stream);
+        ++s->launches;
+        if (e != cudaSuccess) return cuda_fail(s, e, "carry initialisation");
+        s->carry_ok = true;
+      }
+      e = carry3d_step(s->maps, s->fa == s->buf_a ? 0 : 1, s->fa, s->fb, s->carry, s->ring, s->ghost, s->ng, s->hit,
+                       s->errflag, s->p, s->stream, &nk);
     } else {
       e = s->L->step(s->fa, s->fb, s->psi, s->p, s->stream, &nk);
     }
@@ -469,6 +519,7 @@ lb_status lb_set_populations(lb_sim* s, const double* f, int on_device) {
   if (on_device) {
     e = s->L->encode(f, s->fa, 0, N, N, N, s->stream);
     ++s->launches;
+    s->carry_ok = false;
     if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
     if (e != cudaSuccess) return cuda_fail(s, e, "population encode");
   } else {
@@ -483,6 +534,7 @@ lb_status lb_set_populations(lb_sim* s, const double* f, int on_device) {
       if (e != cudaSuccess) return cuda_fail(s, e, "population upload (copy)");
       e = s->L->encode((const double*)s->fb, s->fa, (int)s0, cnt, cnt, N, s->stream);
       ++s->launches;
+      s->carry_ok = false;
       if (e != cudaSuccess) return cuda_fail(s, e, "population upload (encode launch)");
       e = cudaStreamSynchronize(s->stream);
       if (e != cudaSuccess) return cuda_fail(s, e, "population upload (synchronize)");
@@ -506,7 +558,7 @@ long long lb_kernel_launches(const lb_sim* s) { return s ? s->launches : 0; }
 
 int lb_step_path(const lb_sim* s) {
   if (!s) return -1;
-  if (s->cfg.lattice == LB_D3Q27) return LB_PATH_D3Q27;
+  if (s->cfg.lattice == LB_D3Q27) return s->p.carry3d ? LB_PATH_D3Q27_CARRY : LB_PATH_D3Q27;
   return s->p.tma ? LB_PATH_TMA2D : LB_PATH_FUSED2D;
 }
 

@@ -48,6 +48,8 @@ struct HostParams {
   int half;       // FP16-deviation storage
   int tma_stall_test;  // 1: its first copy is expected to bring 16 more bytes than it does,
                        // so its bounded wait runs out (test of the failure path only)
+  int carry3d;    // 1: D3Q27 FP32 / FP16-dev steps run the single-read carry kernels
+  int c3_zseg;    // planes per z segment of their collision kernel
   double tau, A_s, beta, A_h, h_min, h_max, g_th, G[3];
 };
 
@@ -77,8 +79,9 @@ struct Launchers {
 constexpr int kTmaTX = 32, kTmaTY = 16;
 struct TmaMaps {
   // tensor maps: FP32: box of state buffer A, B; FP16-dev: deviations of A, B, then the
-  // reference densities of A, B
-  alignas(64) unsigned char bytes[4 * 128];
+  // reference densities of A, B; the single-read D3Q27 step adds its per-site
+  // (n, |grad psi|) and NCI distances (slots 4, 5)
+  alignas(64) unsigned char bytes[6 * 128];
 };
 bool tma2d_supported(const HostParams& h);
 cudaError_t tma2d_prepare(TmaMaps* m, const void* fa, const void* fb, const HostParams& h);
@@ -98,6 +101,24 @@ int tma2d_member_fill(void* table, int k, int nmem, const TmaMaps& m, const Host
                       int tile0);
 cudaError_t tma2d_batch_step(const void* members, int nmem, int total_tiles, int state, int* err, int* counter,
                              int smax_max, int edm, int half, int num_sms, cudaStream_t s);
+
+// Single-read D3Q27 step (lb_carry3d.cu) for FP32 and FP16-dev storage on lattices with
+// nx % 32 == 0 and ny % 8 == 0: an interface pass (psi, gradient, normal from the
+// carried densities) and a TMA-fed collision that also produces the next step's
+// densities. Device buffers: carry (N float2), ring (carry3d_ring_bytes), ghost
+// (carry3d_ghost_bytes), ng (N float4), hit (N bytes).
+bool carry3d_supported(const HostParams& h);
+size_t carry3d_ring_bytes(const HostParams& h);
+size_t carry3d_ghost_bytes(const HostParams& h);
+// tensor maps of both state buffers (FP32: populations of A, B; FP16-dev: deviations of
+// A, B, then reference densities of A, B)
+cudaError_t carry3d_prepare(TmaMaps* m, const void* fa, const void* fb, const void* ng, const void* hit,
+                            const HostParams& h);
+// the carried densities of a state no step produced (pulled from it; rings zeroed)
+cudaError_t carry3d_init(const void* f, void* carry, void* ring, void* ghost, const HostParams& h, cudaStream_t s);
+// one step from state `from` (0: buffer A, 1: buffer B) into the other; *nk = launches
+cudaError_t carry3d_step(const TmaMaps& m, int from, const void* fa, void* fb, void* carry, void* ring, void* ghost,
+                         void* ng, void* hit, int* err, const HostParams& h, cudaStream_t s, int* nk);
 
 const Launchers* launchers_fp64(int lattice);
 const Launchers* launchers_fp32(int lattice);

@@ -46,6 +46,7 @@
 
 #include "lb_kernels.cuh"
 #include "lb_launch.h"
+#include "lb_tma.cuh"
 
 namespace lbnci {
 namespace {
@@ -74,65 +75,6 @@ constexpr int kOffBar = kOffP + kPBytes;
 constexpr int kSmemBytes = kOffBar + 256;  // mbarrier, next tile (4 ints), 2 x StepT<float>
 static_assert(2 * (kSmemBytes + 1024) <= 228 * 1024, "shared memory: two CTAs per SM (1 KB reserved each)");
 
-constexpr unsigned long long kWaitLimitNs = 1000000000ull;
-
-// ------------------------------------------------------------------ PTX helpers
-__device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ unsigned long long globaltimer() {
-  unsigned long long t;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-  return t;
-}
-
-__device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ void mbar_expect_tx(unsigned long long* bar, unsigned bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
-               : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, unsigned parity) {
-  unsigned ok;
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-      "selp.u32 %0, 1, 0, p;\n\t}"
-      : "=r"(ok)
-      : "r"(smem_u32(bar)), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-
-// Wait for phase `parity` of an mbarrier for at most kWaitLimitNs; false on expiry.
-__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned parity) {
-  if (mbar_try_wait(bar, parity)) return true;
-  const unsigned long long t0 = globaltimer();
-  while (!mbar_try_wait(bar, parity))
-    if (globaltimer() - t0 > kWaitLimitNs) return false;
-  return true;
-}
-
-__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, int x, int y, int z,
-                                            unsigned long long* bar) {
-  asm volatile(
-      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
-      "[%5];" ::"r"(smem_u32(dst)),
-      "l"(reinterpret_cast<unsigned long long>(map)), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
-      : "memory");
-}
-
-__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int x, int y,
-                                            unsigned long long* bar) {
-  asm volatile(
-      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], "
-      "[%4];" ::"r"(smem_u32(dst)),
-      "l"(reinterpret_cast<unsigned long long>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
-      : "memory");
-}
-
 // Probe offset of the NCI ray: round(s n_a) to the nearest integer (ties to even),
 // returned as the float's bit pattern b with round(s n_a) = b - kMagicBits; adding
 // 1.5 2^23 leaves the integer in the low mantissa bits (|s n_a| <= 4 here). The FP64
@@ -142,7 +84,6 @@ constexpr float kMagic = 12582912.0f;
 constexpr unsigned kMagicBits = 0x4B400000u;
 __device__ __forceinline__ unsigned probe_bits(float s, float v) { return __float_as_uint(fmaf(s, v, kMagic)); }
 
-__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 
 // Halo cell h of a ring of width W around the 32 x 16 tile, in region coordinates
 // (region = (32 + 2W) x (16 + 2W)): two bands of W full rows, then the W-wide sides.
@@ -619,20 +560,6 @@ StepT<float> to_step(const HostParams& h) {
   return p;
 }
 
-PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
-  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
-  if (!fn) {
-    void* ptr = nullptr;
-    cudaDriverEntryPointQueryResult q;
-    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &ptr, 12000, cudaEnableDefault, &q) ==
-            cudaSuccess &&
-        q == cudaDriverEntryPointSuccess)
-      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(ptr);
-    cudaGetLastError();
-  }
-  return fn;
-}
-
 // Populations of one state as a 3-D tensor (x, y, plane) of 32-bit words, box 48 x 28 x
 // planes: 18 float planes (FP32) or 9 half2 deviation planes (FP16-dev). L2 fetches of the
 // box rows (192 bytes) are promoted to 128-byte lines (256-byte promotion measured 3% slower
@@ -742,7 +669,7 @@ size_t tma2d_table_bytes(int nmem) { return (size_t)nmem * (sizeof(TmaMember) + 
 
 int tma2d_member_fill(void* table, int k, int nmem, const TmaMaps& m, const HostParams& h, void* buf0, void* buf1,
                       int tile0) {
-  static_assert(sizeof(TmaMember::map) == sizeof(TmaMaps::bytes), "member maps");
+  static_assert(sizeof(TmaMember::map) <= sizeof(TmaMaps::bytes), "member maps: the first four of the sim's maps");
   TmaMember mb;
   std::memset(&mb, 0, sizeof(mb));
   std::memcpy(mb.map, m.bytes, sizeof(mb.map));
