@@ -67,8 +67,9 @@ WORKLOADS = {
                      A_h=0.05, force=(1e-5, 0.0, 0.0), members=96,
                      gen=lambda nx, ny, nz, seed: inputs.channel_emulsion_2d(nx, ny, seed=seed),
                      desc="96 independent D2Q9 channels, length 512-2048, width 64-256, area fraction "
-                          "0.7-0.9, G log-uniform 1e-6..1e-4, A_h uniform 0..0.1, one batched launch per "
-                          "step (CUDA graph), autotuned tile shape"),
+                          "0.7-0.9 requested (packings reach about 0.73), G log-uniform 1e-6..1e-4, A_h "
+                          "uniform 0..0.1, one batched launch per step (CUDA graph), autotuned L2 "
+                          "promotion and static tiles of the batched kernel"),
     "duct3d_small": dict(lattice=1, nx=384, ny=96, nz=96, wall_y=1, wall_z=1, tau=1.0, A_s=0.01, beta=0.7,
                          A_h=0.03, force=(2e-6, 0.0, 0.0),
                          gen=lambda nx, ny, nz, seed: inputs.duct_emulsion_3d(nx, ny, nz, seed=seed),
@@ -353,6 +354,11 @@ def run_ensemble(args, w, lbnci, torch, prec, ws, rank, local, dist):
         mv.init_fields(m.fields.rho1, m.fields.rho2)
     spt = ens.tune()
     t32x16, t32x32 = ens.tune_times()
+    tma_tune = None
+    if n_tma:
+        promo, nstatic, table = ens.tma_choice()
+        tma_tune = {"l2_promotion_bytes": promo, "static_tiles_per_cta": nstatic,
+                    "ms_per_step": {f"promo{k[0]}_static{k[1]}": round(v, 4) for k, v in table.items()}}
     ens.step(args.warmup)
     torch.cuda.synchronize()
     if dist:
@@ -367,6 +373,7 @@ def run_ensemble(args, w, lbnci, torch, prec, ws, rank, local, dist):
     launches = ens.launches() - launches0
     total_ms = max_over_ranks(start.elapsed_time(end), dist, "cuda")
     obs = [mv.observables(allow_numeric=True) for mv in ens.members]
+    study = flow_study(ens, members, args.study_steps, obs) if rank == 0 else None
     # the same lattices stepped one launch per member per step, for comparison
     seq_ms = None
     if not args.no_e2e:
@@ -393,9 +400,53 @@ def run_ensemble(args, w, lbnci, torch, prec, ws, rank, local, dist):
         kern.append(f"tma2d_kernel batched over {n_tma} members")
     if n_tma < len(members):
         kern.append(f"fused2d_batch_kernel over {len(members) - n_tma} members (tile 32x{8 * spt})")
-    return N, total_ms, launches, clk.summary(), obs, {"step_kernels": "; ".join(kern), "tune_ms_per_step":
-                                                      {"32x16": round(t32x16, 4), "32x32": round(t32x32, 4)},
-                                                      "one_launch_per_member_ms_per_step": seq_ms}
+    extra = {"step_kernels": "; ".join(kern), "one_launch_per_member_ms_per_step": seq_ms,
+             "autotune": {"tma_kernel": tma_tune,
+                          "one_pass_kernel": {"tile": f"32x{8 * spt}", "ms_per_step":
+                                              {"32x16": round(t32x16, 4), "32x32": round(t32x32, 4)}}
+                          if n_tma < len(members) else None}}
+    return N, total_ms, launches, clk.summary(), obs, extra, study
+
+
+def flow_study(ens, members, study_steps, obs):
+    """The study an ensemble runs for (the flow rate of the dispersed phase against the
+    body force G and the near-contact strength A_h, Results, Fig. 3): per member G, A_h,
+    width, target area fraction and the flow rates, time-averaged over the second half of
+    `study_steps` further steps (sampled every study_steps / 40), or the values after the
+    timed steps when study_steps is 0 (null where a member's state went non-finite: with
+    G up to 1e-4 in channels up to 256 wide the Poiseuille speed G W^2 / (8 nu) passes
+    the lattice's low-Mach range, and with A_h near 0.1 the near-contact kicks grow
+    without bound; "diverged" counts them); and the least-squares fit
+    log Q_d = a + b log G + c A_h + d log ny over the members with finite Q_d > 0."""
+    if study_steps > 0:
+        ens.step(study_steps // 2)
+        every = max(1, study_steps // 40)
+        acc = np.zeros((len(members), 2))
+        ns = 0
+        for _ in range((study_steps - study_steps // 2) // every):
+            ens.step(every)
+            o = [mv.observables(allow_numeric=True) for mv in ens.members]
+            acc += [[x["flow_rate"], x["flow_rate_disp"]] for x in o]
+            ns += 1
+        q = acc / max(ns, 1)
+    else:
+        q = np.array([[x["flow_rate"], x["flow_rate_disp"]] for x in obs])
+    finite = np.isfinite(q).all(axis=1)
+    rows = [[float(f"{m.force:.4g}"), round(m.A_h, 4), m.ny, round(m.fields.meta["target_area_fraction"], 3),
+             float(f"{q[k, 0]:.5g}") if finite[k] else None, float(f"{q[k, 1]:.5g}") if finite[k] else None]
+            for k, m in enumerate(members)]
+    ok = finite & (q[:, 1] > 0)
+    fit = None
+    if ok.sum() >= 5:
+        X = np.column_stack([np.ones(ok.sum()), np.log([m.force for m in members])[ok],
+                             np.array([m.A_h for m in members])[ok], np.log([m.ny for m in members])[ok]])
+        coef, *_ = np.linalg.lstsq(X, np.log(q[ok, 1]), rcond=None)
+        fit = {"dlogQd_dlogG": round(float(coef[1]), 4), "dlogQd_dA_h": round(float(coef[2]), 4),
+               "dlogQd_dlogny": round(float(coef[3]), 4), "members_fitted": int(ok.sum())}
+    return {"steps_after_timing": study_steps,
+            "average": "second half, 40 samples" if study_steps > 0 else "none (state after the timed steps)",
+            "columns": ["G", "A_h", "ny", "area_fraction", "Q", "Q_disp"], "members": rows,
+            "diverged": int((~finite).sum()), "fit": fit}
 
 
 def main(argv=None):
@@ -412,6 +463,8 @@ def main(argv=None):
     ap.add_argument("--ws-train", type=int, default=768, help="warmstart: training channels")
     ap.add_argument("--ws-test", type=int, default=64, help="warmstart: held-out channels")
     ap.add_argument("--ws-horizon", type=int, default=60000, help="warmstart: lattice steps per run")
+    ap.add_argument("--study-steps", type=int, default=0,
+                    help="ensemble: further steps after timing over which the flow rates are averaged")
     ap.add_argument("--flush-mb", type=int, default=L2_FLUSH_BYTES >> 20,
                     help="L2 flush buffer written before every timed step (MB)")
     args = ap.parse_args(argv)
@@ -567,7 +620,8 @@ def main(argv=None):
 
 def main_ensemble(args, w, lbnci, torch, ws, rank, local, dist):
     prec = {"fp32": lbnci.LB_FP32, "fp64": lbnci.LB_FP64, "fp16dev": lbnci.LB_FP16DEV}[args.precision]
-    N, total_ms, launches, clocks, obs, extra = run_ensemble(args, w, lbnci, torch, prec, ws, rank, local, dist)
+    N, total_ms, launches, clocks, obs, extra, study = run_ensemble(args, w, lbnci, torch, prec, ws, rank, local,
+                                                                    dist)
     if dist:
         dist.destroy_process_group()
     if rank != 0:
@@ -591,7 +645,7 @@ def main_ensemble(args, w, lbnci, torch, ws, rank, local, dist):
                      "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)", "kernel": extra["step_kernels"],
                      "alg_bytes_per_site": bpsite},
         "cpu_baseline": None, "e2e": None, "gpu_launches": int(launches), "clocks": clocks,
-        "flow_rate_disp": {"min": min(o["flow_rate_disp"] for o in obs), "max": max(o["flow_rate_disp"] for o in obs)},
+        "flow_study": study,
     }
     print(json.dumps(line), flush=True)
     return 0

@@ -220,12 +220,23 @@ lb_status lb_ensemble_member(lb_ensemble* ens, int m, lb_sim** out);
 /* Advance every member by nsteps. Asynchronous on the ensemble's stream. */
 lb_status lb_ensemble_step(lb_ensemble* ens, long long nsteps);
 
-/* Autotuner: time each supported tile shape (32 x 16 and 32 x 32 sites per block) of
- * the batched step on the current state -- writing only the members' back buffers, so
- * the state is unchanged -- and keep the fastest; *spt_out (optional) = 2 or 4. */
+/* Autotuner: time the candidates of both batched kernels on the current state --
+ * writing only the members' back buffers, so the state is unchanged -- and keep the
+ * fastest of each. The one-pass kernel (FP64 members, nx % 4 != 0): tile shape 32 x 16
+ * or 32 x 32 sites per block, *spt_out (optional) = 2 or 4. The TMA kernel (FP32 and
+ * FP16-dev members with nx % 4 == 0): the L2 promotion of its tensor copies (none, 64,
+ * 128, 256 bytes) x the tiles each CTA takes before it draws from the shared tile
+ * counter (1, 2, 3): twelve candidates, one warm-up and five timed launches each.
+ * Synchronises the ensemble's stream. */
 lb_status lb_ensemble_tune(lb_ensemble* ens, int* spt_out);
 /* Per-step times (ms) the last lb_ensemble_tune measured for the two shapes. */
 lb_status lb_ensemble_tune_times(const lb_ensemble* ens, float* ms_32x16, float* ms_32x32);
+/* The TMA kernel's current choice: *l2_promotion_bytes (0, 64, 128 or 256; 128 before
+ * any tuning), *static_tiles (1, 2 or 3; 2 before any tuning), and, when ms12 is not
+ * NULL, the per-step times (ms) of the last lb_ensemble_tune, ms12[ip * 3 + is] for
+ * promotion index ip over {0, 64, 128, 256} and static tiles 1 + is (zero before any
+ * tuning). Any pointer may be NULL. LB_EUNSUPPORTED when no member runs that kernel. */
+lb_status lb_ensemble_tma_choice(const lb_ensemble* ens, int* l2_promotion_bytes, int* static_tiles, float* ms12);
 
 /* Batched step launches since creation; last failure on this ensemble. */
 long long lb_ensemble_launches(const lb_ensemble* ens);

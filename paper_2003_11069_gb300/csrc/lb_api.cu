@@ -107,8 +107,9 @@ lb_status cuda_fail(lb_sim* s, cudaError_t e, const char* what) {
 size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
 
 // The result area holds 16 doubles: the kRedSlots reductions, then, in slot
-// kErrSlot, the kernels' error word (an int), and in slot kErrSlot + 1 the two tile
-// counters of the TMA step kernel (ints).
+// kErrSlot, the kernels' error word (an int), in slot kErrSlot + 1 the two tile
+// counters of the TMA step kernel (ints), and in slot kErrSlot + 2 the two dither-seed
+// words of the FP16-deviation stores (StepT::seedw).
 constexpr int kErrSlot = 12;
 
 struct Layout {
@@ -324,6 +325,8 @@ lb_status lb_create(const lb_config* cfg, lb_sim** out) {
   s->result = (double*)(base + lay.result);
   s->errflag = (int*)(s->result + kErrSlot);
   s->tile_counter = (int*)(s->result + kErrSlot + 1);
+  s->p.seedw = (unsigned*)(s->result + kErrSlot + 2);
+  s->p.parity = 0;
   if (s->p.tma) {
     // tensor maps of both state buffers; without the driver's tensor-map encoder the
     // step falls back to the one-pass fused kernel
@@ -376,7 +379,8 @@ lb_status lb_init_fields(lb_sim* s, const double* rho1, const double* rho2, cons
     if (e != cudaSuccess) return cuda_fail(s, e, "field upload");
     d1 = st; d2 = st + N; du = u ? st + 2 * N : nullptr;
   }
-  e = s->L->init(s->fa, d1, d2, du, s->p, s->stream);
+  e = cudaMemsetAsync(s->p.seedw, 0, 2 * sizeof(unsigned), s->stream);  // the dither sequence restarts
+  if (e == cudaSuccess) e = s->L->init(s->fa, d1, d2, du, s->p, s->stream);
   ++s->launches;
   s->carry_ok = false;
   if (e != cudaSuccess) return cuda_fail(s, e, "init launch");
@@ -395,6 +399,7 @@ lb_status lb_step(lb_sim* s, long long nsteps) {
   for (long long t = 0; t < nsteps; ++t) {
     int nk = 0;
     cudaError_t e;
+    s->p.parity = s->fa == s->buf_a ? 0 : 1;
     if (s->p.tma) {
       e = tma2d_step(s->maps, s->fa == s->buf_a ? 0 : 1, s->fa, s->fb, s->errflag, s->tile_counter, s->p,
                      s->stream);
@@ -515,7 +520,8 @@ lb_status lb_set_populations(lb_sim* s, const double* f, int on_device) {
   if (!s) return fail(nullptr, LB_EINVAL, "sim is NULL");
   if (!f) return fail(s, LB_EINVAL, "f is NULL");
   const int N = s->p.N, Q2 = 2 * s->Q;
-  cudaError_t e;
+  cudaError_t e = cudaMemsetAsync(s->p.seedw, 0, 2 * sizeof(unsigned), s->stream);  // the dither sequence restarts
+  if (e != cudaSuccess) return cuda_fail(s, e, "seed reset");
   if (on_device) {
     e = s->L->encode(f, s->fa, 0, N, N, N, s->stream);
     ++s->launches;
@@ -663,6 +669,11 @@ extern "C" lb_status lb_observables_noalloc(const lb_config* cfg, const void* f,
 // ---------------------------------------------------------------------------------
 // Ensembles: many independent D2Q9 lattices (different sizes and parameters) stepped
 // together by one batched launch per step, replayed from a CUDA graph.
+// Candidates the autotuner times for the batched TMA kernel.
+constexpr int kTmaPromo[4] = {0, 64, 128, 256};
+constexpr int kTmaStatic[3] = {1, 2, 3};
+constexpr int kTmaCand = 12;
+
 struct lb_ensemble {
   int n;
   const Launchers* L;
@@ -686,6 +697,9 @@ struct lb_ensemble {
   bool graph_ok;
   long long launches;
   float tune_ms[2];        // last autotuner timings per step for spt = 2 and 4
+  int tma_promo;           // batched TMA kernel: L2 promotion of its copies (bytes)
+  int tma_nstatic;         // batched TMA kernel: static tiles per CTA before the counter
+  float tma_ms[kTmaCand];  // last autotuner timings per step, [promotion][static tiles]
   char err[256];
 };
 
@@ -728,16 +742,38 @@ cudaError_t ens_launch_cls(lb_ensemble* e, int parity, int* nk) {
 
 // One step of every member: the batched TMA kernel over the tma members, the one-pass
 // batch kernel over the others.
+cudaError_t ens_launch_tma(lb_ensemble* e, int parity, int* nk) {
+  if (e->tma.empty()) return cudaSuccess;
+  ++*nk;
+  return tma2d_batch_step(e->d_tma, (int)e->tma.size(), e->tma_tiles, parity, e->d_tma_flags, e->d_tma_flags + 1,
+                          e->tma_smax, e->members[0]->p.forcing == LB_FORCE_EDM_DISPERSED, e->members[0]->p.half,
+                          e->members[0]->p.num_sms, e->tma_nstatic, e->stream);
+}
+
 cudaError_t ens_launch(lb_ensemble* e, int parity, int* nk) {
-  if (!e->tma.empty()) {
-    ++*nk;
-    cudaError_t c = tma2d_batch_step(e->d_tma, (int)e->tma.size(), e->tma_tiles, parity, e->d_tma_flags,
-                                     e->d_tma_flags + 1, e->tma_smax,
-                                     e->members[0]->p.forcing == LB_FORCE_EDM_DISPERSED,
-                                     e->members[0]->p.half, e->members[0]->p.num_sms, e->stream);
-    if (c != cudaSuccess) return c;
-  }
+  cudaError_t c = ens_launch_tma(e, parity, nk);
+  if (c != cudaSuccess) return c;
   return ens_launch_cls(e, parity, nk);
+}
+
+// Encode every TMA member's tensor maps with L2 promotion `promo` (bytes) and upload
+// the member table (records and tile index) to the device; waits for the copy.
+cudaError_t ens_fill_tma(lb_ensemble* e, int promo) {
+  const int nt = (int)e->tma.size();
+  std::vector<unsigned char> ht(tma2d_table_bytes(nt));
+  int tiles = 0;
+  for (int k = 0; k < nt; ++k) {
+    lb_sim* s = e->members[e->tma[k]];
+    void* buf1 = s->fa == s->buf_a ? s->fb : s->fa;
+    cudaError_t c = tma2d_prepare(&s->maps, s->buf_a, buf1, s->p, promo);
+    if (c != cudaSuccess) return c;
+    tiles += tma2d_member_fill(ht.data(), k, nt, s->maps, s->p, s->buf_a, buf1, tiles);
+  }
+  e->tma_tiles = tiles;
+  e->tma_promo = promo;
+  cudaError_t c = cudaMemcpyAsync(e->d_tma, ht.data(), ht.size(), cudaMemcpyHostToDevice, e->stream);
+  if (c == cudaSuccess) c = cudaStreamSynchronize(e->stream);
+  return c;
 }
 
 }  // namespace
@@ -769,6 +805,16 @@ lb_status lb_ensemble_create(const lb_config* cfgs, int n, lb_ensemble** out) {
   e->n = n;
   e->L = launchers_for(&cfgs[0]);
   e->spt = 2;
+  e->tma_promo = 128;
+  e->tma_nstatic = 2;
+  if (const char* v = std::getenv("LBNCI_TMA_CHOICE")) {  // "promotion:static", e.g. "64:3"
+    int pr = -1, st = -1;
+    const bool ok = std::sscanf(v, "%d:%d", &pr, &st) == 2 && (pr == 0 || pr == 64 || pr == 128 || pr == 256) &&
+                    st >= 1 && st <= 3;
+    if (!ok) { delete e; return efail(nullptr, LB_EINVAL, "LBNCI_TMA_CHOICE=%s: want <0|64|128|256>:<1|2|3>", v); }
+    e->tma_promo = pr;
+    e->tma_nstatic = st;
+  }
   e->stream = (cudaStream_t)cfgs[0].stream;
   cudaError_t c = cudaSuccess;
   if (!e->stream) {  // graph capture needs a stream other than the legacy default one
@@ -810,17 +856,11 @@ lb_status lb_ensemble_create(const lb_config* cfgs, int n, lb_ensemble** out) {
     c = cudaMemcpyAsync(e->d_members, e->host_members.data(), rec * (nc > 0 ? nc : 1), cudaMemcpyHostToDevice,
                         e->stream);
   if (c == cudaSuccess && nt > 0) {
-    std::vector<unsigned char> ht(tma2d_table_bytes(nt));
-    for (int k = 0; k < nt; ++k) {
-      lb_sim* s = e->members[e->tma[k]];
-      e->tma_tiles += tma2d_member_fill(ht.data(), k, nt, s->maps, s->p, s->fa, s->fb, e->tma_tiles);
-      e->tma_smax = std::max(e->tma_smax, s->p.smax);
-    }
-    c = cudaMalloc(&e->d_tma, ht.size());
+    for (int k = 0; k < nt; ++k) e->tma_smax = std::max(e->tma_smax, e->members[e->tma[k]]->p.smax);
+    c = cudaMalloc(&e->d_tma, tma2d_table_bytes(nt));
     if (c == cudaSuccess) c = cudaMalloc((void**)&e->d_tma_flags, 4 * sizeof(int));
-    if (c == cudaSuccess) c = cudaMemcpyAsync(e->d_tma, ht.data(), ht.size(), cudaMemcpyHostToDevice, e->stream);
     if (c == cudaSuccess) c = cudaMemsetAsync(e->d_tma_flags, 0, 4 * sizeof(int), e->stream);
-    if (c == cudaSuccess) c = cudaStreamSynchronize(e->stream);
+    if (c == cudaSuccess) c = ens_fill_tma(e, e->tma_promo);
     for (int k = 0; k < nt; ++k) e->members[e->tma[k]]->ens_flag = e->d_tma_flags;
   }
   if (c != cudaSuccess) {
@@ -893,9 +933,55 @@ lb_status lb_ensemble_step(lb_ensemble* e, long long nsteps) {
   return LB_OK;
 }
 
+namespace {
+
+// Time the batched TMA kernel for every (L2 promotion, static tiles) candidate on the
+// current state and keep the fastest. Each launch reads the state and writes the back
+// buffers only; its tile counter is zeroed before it, outside the timed interval.
+cudaError_t tune_tma(lb_ensemble* e, cudaEvent_t t0, cudaEvent_t t1) {
+  const int nstatic0 = e->tma_nstatic;
+  int best_p = e->tma_promo, best_s = e->tma_nstatic;
+  float best_ms = 1e30f;
+  cudaError_t c = cudaSuccess;
+  int* ctr = e->d_tma_flags + 1 + e->parity;
+  for (int ip = 0; ip < 4 && c == cudaSuccess; ++ip) {
+    c = ens_fill_tma(e, kTmaPromo[ip]);
+    for (int is = 0; is < 3 && c == cudaSuccess; ++is) {
+      e->tma_nstatic = kTmaStatic[is];
+      float total = 0.f;
+      for (int r = 0; r < 6 && c == cudaSuccess; ++r) {  // one warm-up launch, five timed
+        int nk = 0;
+        c = cudaMemsetAsync(ctr, 0, sizeof(int), e->stream);
+        if (c == cudaSuccess) c = cudaEventRecord(t0, e->stream);
+        if (c == cudaSuccess) c = ens_launch_tma(e, e->parity, &nk);
+        if (c == cudaSuccess) c = cudaEventRecord(t1, e->stream);
+        if (c == cudaSuccess) c = cudaEventSynchronize(t1);
+        float ms = 0.f;
+        if (c == cudaSuccess) c = cudaEventElapsedTime(&ms, t0, t1);
+        if (r > 0) total += ms;
+        e->launches += nk;
+      }
+      e->tma_ms[ip * 3 + is] = total / 5.f;
+      if (c == cudaSuccess && total / 5.f < best_ms) {
+        best_ms = total / 5.f;
+        best_p = kTmaPromo[ip];
+        best_s = kTmaStatic[is];
+      }
+    }
+  }
+  if (c != cudaSuccess) { e->tma_nstatic = nstatic0; return c; }
+  e->tma_nstatic = best_s;
+  c = ens_fill_tma(e, best_p);
+  if (c == cudaSuccess) c = cudaMemsetAsync(e->d_tma_flags + 1, 0, 2 * sizeof(int), e->stream);
+  if (c == cudaSuccess) c = cudaStreamSynchronize(e->stream);
+  return c;
+}
+
+}  // namespace
+
 lb_status lb_ensemble_tune(lb_ensemble* e, int* spt_out) {
   if (!e) return efail(nullptr, LB_EINVAL, "ensemble is NULL");
-  // Time each tile shape on the current state, writing only the back buffers (the
+  // Time each candidate on the current state, writing only the back buffers (the
   // state itself is unchanged), and keep the fastest.
   const int shapes[2] = {2, 4};
   cudaEvent_t t0, t1;
@@ -904,6 +990,15 @@ lb_status lb_ensemble_tune(lb_ensemble* e, int* spt_out) {
   if (c != cudaSuccess) return ecuda(e, c, "event creation");
   int best = e->spt;
   float best_ms = 1e30f;
+  if (e->graph_ok) { cudaGraphExecDestroy(e->graph); e->graph_ok = false; }  // the choices are launch arguments
+  if (!e->tma.empty()) {
+    c = tune_tma(e, t0, t1);
+    if (c != cudaSuccess) {
+      cudaEventDestroy(t0);
+      cudaEventDestroy(t1);
+      return ecuda(e, c, "autotune of the TMA kernel");
+    }
+  }
   if (e->cls.empty()) {  // every member runs the TMA kernel: no tile shape to choose
     cudaEventDestroy(t0);
     cudaEventDestroy(t1);
@@ -941,6 +1036,16 @@ lb_status lb_ensemble_tune_times(const lb_ensemble* e, float* ms2, float* ms4) {
   if (!e) return efail(nullptr, LB_EINVAL, "ensemble is NULL");
   if (ms2) *ms2 = e->tune_ms[0];
   if (ms4) *ms4 = e->tune_ms[1];
+  return LB_OK;
+}
+
+lb_status lb_ensemble_tma_choice(const lb_ensemble* e, int* l2_promotion_bytes, int* static_tiles, float* ms12) {
+  if (!e) return efail(nullptr, LB_EINVAL, "ensemble is NULL");
+  if (e->tma.empty()) return efail(const_cast<lb_ensemble*>(e), LB_EUNSUPPORTED, "no member runs the TMA kernel");
+  if (l2_promotion_bytes) *l2_promotion_bytes = e->tma_promo;
+  if (static_tiles) *static_tiles = e->tma_nstatic;
+  if (ms12)
+    for (int k = 0; k < kTmaCand; ++k) ms12[k] = e->tma_ms[k];
   return LB_OK;
 }
 

@@ -27,6 +27,8 @@ StepT<float> to_step3(const HostParams& h) {
     else if (hd <= hmax) { const float r = hmin / hd; p.Ah[k] = A * (r * r * r); }
     else p.Ah[k] = 0.0f;
   }
+  p.seedw = h.seedw;
+  p.parity = h.parity;
   return p;
 }
 

@@ -291,27 +291,30 @@ template <> struct C3Writer<Plain<1, float>> {
   unsigned N;
   float (*o)[27];
   template <int I>
-  __device__ __forceinline__ void put(unsigned site, float a, float b, float, float) const {
+  __device__ __forceinline__ void put_step(unsigned site, float a, float b, float, float, unsigned) const {
     (f + (size_t)I * N)[site] = a;
     (f + (size_t)(27 + I) * N)[site] = b;
     o[0][I] = a;
     o[1][I] = b;
   }
+  __device__ __forceinline__ unsigned site_bits(unsigned) const { return 0u; }
   __device__ __forceinline__ void put_rho(unsigned, float, float) const {}
 };
 template <> struct C3Writer<HalfDev<1>> {
   __half2* __restrict__ d;
   float2* __restrict__ rho;
   unsigned N;
+  unsigned seed;
   float (*o)[27];
+  __device__ __forceinline__ unsigned site_bits(unsigned site) const { return dither_bits(site, seed); }
   template <int I>
-  __device__ __forceinline__ void put(unsigned site, float a, float b, float r1, float r2) const {
+  __device__ __forceinline__ void put_step(unsigned site, float a, float b, float r1, float r2, unsigned hb) const {
     constexpr float w = float(Lattice<1>::w(I));
-    const __half2 h = __floats2half2_rn(fmaf(-w, r1, a), fmaf(-w, r2, b));
-    d[(size_t)I * N + site] = h;
-    const float2 v = __half22float2(h);
-    o[0][I] = fmaf(w, r1, v.x);
-    o[1][I] = fmaf(w, r2, v.y);
+    const unsigned v = half2_stochastic<I>(fmaf(-w, r1, a), fmaf(-w, r2, b), hb);
+    reinterpret_cast<unsigned*>(d)[(size_t)I * N + site] = v;
+    const float2 fv = __half22float2(*reinterpret_cast<const __half2*>(&v));
+    o[0][I] = fmaf(w, r1, fv.x);
+    o[1][I] = fmaf(w, r2, fv.y);
   }
   __device__ __forceinline__ void put_rho(unsigned site, float r1, float r2) const {
     rho[site] = make_float2(r1, r2);
@@ -416,6 +419,8 @@ carry3d_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_constant_
 
   const int nx = p.nx, ny = p.ny, nz = p.nz;
   const unsigned nxy = (unsigned)nx * (unsigned)ny;
+  unsigned seed = 0u;  // dither seed of the FP16 stores
+  if constexpr (HALF) seed = step_seed(p, p.parity, blockIdx.x == 0 && tid == 0);
   // One warp: the copies of plane z of a column, lane w < 18 the class window w (FP32:
   // class w % 9 of component w / 9; FP16-dev: lanes < 9), lanes 27..29 the density
   // boxes (FP16-dev), lanes 30, 31 the plane's (n, |grad psi|) and NCI distances.
@@ -636,7 +641,7 @@ carry3d_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_constant_
       for (int c = 0; c < 3; ++c) u[c] = __fdividef(j[c] + 0.5f * F[c], rho);
       const float m[3] = {-n0, -n1, -n2};
       C3Writer<ST> wr;
-      if constexpr (HALF) { wr.d = fw.d; wr.rho = fw.rho; }
+      if constexpr (HALF) { wr.d = fw.d; wr.rho = fw.rho; wr.seed = seed; }
       else { wr.f = fw.f; }
       wr.N = fw.N;
       wr.o = o;

@@ -163,7 +163,10 @@ template <typename ST, int SPT, bool EDM>
 __global__ void __launch_bounds__(256, (fused2d_min_blocks<ST, SPT>()))
 fused2d_kernel(typename ST::Reader f, typename ST::Writer fout, StepT<typename ST::Compute> p) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  fused2d_tile<ST, SPT, EDM>(f, fout, p, blockIdx.x * kFusedTX, blockIdx.y * (kFusedThreadsY * SPT), smem_raw);
+  typename ST::Writer w = fout;
+  if constexpr (ST::kHalf)
+    w.seed = step_seed(p, p.parity, blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0 && threadIdx.y == 0);
+  fused2d_tile<ST, SPT, EDM>(f, w, p, blockIdx.x * kFusedTX, blockIdx.y * (kFusedThreadsY * SPT), smem_raw);
 }
 
 // One lattice of an ensemble: its step parameters, its two state buffers and the
@@ -195,8 +198,11 @@ fused2d_batch_kernel(const BatchMember<typename ST::Compute>* __restrict__ membe
   const int t = b - tile0[lo];
   const int by = t / mb.ntx, bx = t - by * mb.ntx;
   const unsigned N = (unsigned)p.N;
-  fused2d_tile<ST, SPT, EDM>(ST::reader(mb.buf[parity], N), ST::writer(const_cast<void*>(mb.buf[1 - parity]), N), p,
-                        bx * kFusedTX, by * (kFusedThreadsY * SPT), smem_raw);
+  typename ST::Writer w = ST::writer(const_cast<void*>(mb.buf[1 - parity]), N);
+  if constexpr (ST::kHalf)  // the member's first tile moves its seed on
+    w.seed = step_seed(p, parity, t == 0 && threadIdx.x == 0 && threadIdx.y == 0);
+  fused2d_tile<ST, SPT, EDM>(ST::reader(mb.buf[parity], N), w, p, bx * kFusedTX, by * (kFusedThreadsY * SPT),
+                             smem_raw);
 }
 
 }  // namespace lbnci

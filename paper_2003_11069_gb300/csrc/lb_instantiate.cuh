@@ -33,6 +33,8 @@ StepT<T> convert(const HostParams& h) {
     else if (hd <= hmax) { const T r = hmin / hd; p.Ah[k] = A * (r * r * r); }
     else p.Ah[k] = T(0);
   }
+  p.seedw = h.seedw;
+  p.parity = h.parity;
   return p;
 }
 

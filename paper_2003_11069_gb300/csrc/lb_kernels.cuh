@@ -243,6 +243,7 @@ __device__ __forceinline__ void collide_exact(const T fin[2][Lattice<LAT>::Q], T
   const T seg = M<T>::div(p.beta * rho1 * rho2, rho);
   const T pamp = p.pamp * g;
   const T c1 = M<T>::div(rho1, rho), c2 = M<T>::div(rho2, rho);
+  const unsigned hb = fout.site_bits((unsigned)idx);
   static_for<Q>([&](auto I) {
     constexpr int i = decltype(I)::value;
     constexpr T w = T(Lattice<LAT>::w(i));
@@ -270,7 +271,7 @@ __device__ __forceinline__ void collide_exact(const T fin[2][Lattice<LAT>::Q], T
       o1 += feq_dir<LAT, i, T>(rho1, u1) - feq_dir<LAT, i, T>(rho1, ueq);
       o2 += feq_dir<LAT, i, T>(rho2, u2) - feq_dir<LAT, i, T>(rho2, ueq);
     }
-    fout.template put<i>((unsigned)idx, o1, o2, rho1, rho2);
+    fout.template put_step<i>((unsigned)idx, o1, o2, rho1, rho2, hb);
   });
   fout.put_rho((unsigned)idx, rho1, rho2);
 }
@@ -314,6 +315,7 @@ __device__ __forceinline__ void collide_store(const T fin[2][Lattice<LAT>::Q], T
   const T K0 = orho * (T(1) - T(1.5) * uu) - T(3) * p.guo * uF - pamp * T(1.0 / 3.0);
   const T a3 = T(3) * orho, a45 = T(4.5) * orho, g3 = T(3) * p.guo, g9 = T(9) * p.guo;
   const T om1 = T(1) - p.omega;
+  const unsigned hb = fout.site_bits((unsigned)idx);
   T s1 = T(0), s2 = T(0);
   static_for<Q>([&](auto I) {
     constexpr int i = decltype(I)::value;
@@ -340,11 +342,11 @@ __device__ __forceinline__ void collide_store(const T fin[2][Lattice<LAT>::Q], T
       const T o2p = fsp - o1p, o2m = fsm - o1m;
       s1 += o1p + o1m;
       s2 += o2p + o2m;
-      fout.template put<i>((unsigned)idx, o1p, o2p, rho1, rho2);
-      fout.template put<o>((unsigned)idx, o1m, o2m, rho1, rho2);
+      fout.template put_step<i>((unsigned)idx, o1p, o2p, rho1, rho2, hb);
+      fout.template put_step<o>((unsigned)idx, o1m, o2m, rho1, rho2, hb);
     }
   });
-  fout.template put<0>((unsigned)idx, rho1 - s1, rho2 - s2, rho1, rho2);
+  fout.template put_step<0>((unsigned)idx, rho1 - s1, rho2 - s2, rho1, rho2, hb);
   fout.put_rho((unsigned)idx, rho1, rho2);
 }
 
@@ -394,6 +396,8 @@ tiled_kernel(typename ST::Reader f, typename ST::Writer fout, const typename ST:
   const int RZoff = D == 3 ? R : 0;
   const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY, z0 = blockIdx.z * TZ;
   const int tid = threadIdx.x + TX * (threadIdx.y + TY * threadIdx.z);
+  if constexpr (ST::kHalf && !FIELDS)
+    fout.seed = step_seed(p, p.parity, blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0 && tid == 0);
 
   for_region(tid, TX * TY * TZ, RX, RY, RZ, [&](int t, int lx, int ly, int lz) {
     const int gx = wrapn(x0 - R + lx, p.nx);

@@ -74,6 +74,8 @@ struct StepT {
   T G[3];       // body force
   T Ah[8];      // A_h(h) for integer probe distance h (0 unused): A for h <= h_min,
                 // A (h_min/h)^3 for h_min < h <= h_max, 0 beyond
+  unsigned* seedw;  // FP16-deviation storage: the sim's two dither-seed words (or null);
+  int parity;       // the launch reads seedw[parity] and sets seedw[parity ^ 1] to it + 1
 };
 
 // Largest number of NCI probe steps the kernels support (h_max < kMaxProbe + 1).

@@ -50,6 +50,8 @@ struct HostParams {
                        // so its bounded wait runs out (test of the failure path only)
   int carry3d;    // 1: D3Q27 FP32 / FP16-dev steps run the single-read carry kernels
   int c3_zseg;    // planes per z segment of their collision kernel
+  unsigned* seedw;  // device: two dither-seed words of the FP16-deviation stores
+  int parity;       // state buffer the next step reads (0: the one the sim was created with)
   double tau, A_s, beta, A_h, h_min, h_max, g_th, G[3];
 };
 
@@ -84,7 +86,8 @@ struct TmaMaps {
   alignas(64) unsigned char bytes[6 * 128];
 };
 bool tma2d_supported(const HostParams& h);
-cudaError_t tma2d_prepare(TmaMaps* m, const void* fa, const void* fb, const HostParams& h);
+// promo: L2 promotion of the copies' fetches in bytes (0, 64, 128 or 256; 128 by default)
+cudaError_t tma2d_prepare(TmaMaps* m, const void* fa, const void* fb, const HostParams& h, int promo = 128);
 // One step from state `from` (0: buffer A, 1: buffer B) into the other buffer. counter:
 // two device ints, zero at first use, reserved for this sim's steps (alternate states
 // use alternate counters).
@@ -99,8 +102,9 @@ cudaError_t tma2d_step(const TmaMaps& m, int from, const void* fa, void* fb, int
 size_t tma2d_table_bytes(int nmem);
 int tma2d_member_fill(void* table, int k, int nmem, const TmaMaps& m, const HostParams& h, void* buf0, void* buf1,
                       int tile0);
+// nstatic: tiles each CTA takes statically before it takes tiles from the counter.
 cudaError_t tma2d_batch_step(const void* members, int nmem, int total_tiles, int state, int* err, int* counter,
-                             int smax_max, int edm, int half, int num_sms, cudaStream_t s);
+                             int smax_max, int edm, int half, int num_sms, int nstatic, cudaStream_t s);
 
 // Single-read D3Q27 step (lb_carry3d.cu) for FP32 and FP16-dev storage on lattices with
 // nx % 32 == 0 and ny % 8 == 0: an interface pass (psi, gradient, normal from the

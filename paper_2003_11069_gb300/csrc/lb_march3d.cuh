@@ -80,6 +80,7 @@ march3d_kernel(typename ST::Reader f, typename ST::Writer fout, const typename S
   T* s_psi = reinterpret_cast<T*>(smem_raw);  // [3][RXY]
   T* s_ng = s_psi + 3 * RXY;                   // [W][4][GXY]: n_x, n_y, n_z, |grad psi|
   const int tx = threadIdx.x, ty = threadIdx.y, tid = tx + TX * ty;
+  if constexpr (ST::kHalf) fout.seed = step_seed(p, p.parity, blockIdx.x == 0 && tid == 0);
   // ring slots of plane q >= -(2 S + 1) (the first psi plane and the lowest probe plane)
   auto ring3 = [](int q) { return (int)((unsigned)(q + 3 * W) % 3u); };
   auto ringW = [](int q) { return (int)((unsigned)(q + 2 * W) % (unsigned)W); };

@@ -74,6 +74,7 @@ constexpr int kOffP = kOffPsi + kPsiBytes;
 constexpr int kOffBar = kOffP + kPBytes;
 constexpr int kSmemBytes = kOffBar + 256;  // mbarrier, next tile (4 ints), 2 x StepT<float>
 static_assert(2 * (kSmemBytes + 1024) <= 228 * 1024, "shared memory: two CTAs per SM (1 KB reserved each)");
+static_assert(32 + 2 * sizeof(StepT<float>) <= 256, "mbarrier, next tile and two parameter slots");
 
 // Probe offset of the NCI ray: round(s n_a) to the nearest integer (ties to even),
 // returned as the float's bit pattern b with round(s n_a) = b - kMagicBits; adding
@@ -133,10 +134,11 @@ struct PlaneWriter {
   float* __restrict__ f;
   unsigned N;
   template <int I>
-  __device__ __forceinline__ void put(unsigned site, float a, float b, float, float) const {
+  __device__ __forceinline__ void put_step(unsigned site, float a, float b, float, float, unsigned) const {
     (f + (size_t)I * N)[site] = a;
     (f + (size_t)(kQ + I) * N)[site] = b;
   }
+  __device__ __forceinline__ unsigned site_bits(unsigned) const { return 0u; }
   __device__ __forceinline__ void put_rho(unsigned, float, float) const {}
 };
 
@@ -180,6 +182,8 @@ struct TmaArgs {
   int nmem;
   int state;     // batched step: members read buf[state] and write buf[state ^ 1]
   unsigned stall_bytes;  // failure-path test only: bytes expected on top of the first copy
+  int nstatic;   // tiles each CTA takes statically (blockIdx.x + k gridDim.x, k < nstatic)
+                 // before it takes tiles from the counter
 };
 
 // Tile t of a lattice with ntx tile columns and ntiles tiles -> its origin. Numbering:
@@ -297,6 +301,8 @@ tma2d_kernel(const __grid_constant__ CUtensorMap map_pop, const __grid_constant_
   // issued and the per-thread offsets below are computed while it is in flight.
   asm volatile("griddepcontrol.wait;" ::: "memory");
   if (tid == 0 && blockIdx.x == 0) a.counter[a.parity ^ 1] = 0;  // the next launch's counter
+  unsigned seed_one = 0u;  // dither seed of a single lattice's stochastic rounding
+  if constexpr (HALF && !BATCH) seed_one = step_seed(p_one, a.parity, tid == 0 && blockIdx.x == 0);
 
   unsigned phase = 0;    // parity of the next completion of the mbarrier
   bool pending = false;  // a TMA load into the stage is in flight
@@ -337,9 +343,15 @@ tma2d_kernel(const __grid_constant__ CUtensorMap map_pop, const __grid_constant_
 
   // Thread 0 reserves tiles one iteration ahead, so the counter's round trip is never
   // waited for: at each tile it publishes the tile reserved before (read by all after
-  // phase 1) and reserves the one after it. The first two tiles of a CTA are blockIdx.x
-  // and blockIdx.x + gridDim.x; the counter hands out tiles from 2 gridDim.x on.
-  int reserved = tile + (int)gridDim.x;
+  // phase 1) and reserves the one after it. The first nstatic tiles of a CTA are
+  // blockIdx.x + k gridDim.x; the counter hands out tiles from nstatic gridDim.x on.
+  const int nstatic = a.nstatic > 0 ? a.nstatic : 1;
+  int nres = 1;  // static tiles reserved so far (the current one included)
+  auto next_tile = [&]() {
+    if (nres < nstatic) return (int)blockIdx.x + (nres++) * (int)gridDim.x;
+    return nstatic * (int)gridDim.x + atomicAdd(&a.counter[a.parity], 1);
+  };
+  int reserved = tid == 0 ? next_tile() : 0;
   int k = 0;
   while (tile < a.ntiles) {
     if (tid == 0) {
@@ -350,7 +362,7 @@ tma2d_kernel(const __grid_constant__ CUtensorMap map_pop, const __grid_constant_
         s_next[2] = l.x0;
         s_next[3] = l.y0;
       }
-      reserved = 2 * (int)gridDim.x + atomicAdd(&a.counter[a.parity], 1);
+      reserved = next_tile();
     }
     const int slot = k & 1;
     if constexpr (BATCH) {  // this tile's member parameters (read after the next barrier)
@@ -377,6 +389,10 @@ tma2d_kernel(const __grid_constant__ CUtensorMap map_pop, const __grid_constant_
     if constexpr (BATCH) {
       f = ST::reader(a.members[cur.m].buf[a.state], (unsigned)p.N);
       fout = ST::writer(a.members[cur.m].buf[a.state ^ 1], (unsigned)p.N);
+    }
+    if constexpr (HALF) {  // a member's seed is moved on by the CTA that takes its tile at (0, 0)
+      if constexpr (BATCH) fout.seed = step_seed(p, a.state, tid == 0 && x0 == 0 && y0 == 0);
+      else fout.seed = seed_one;
     }
     const bool walls = p.wall_y != 0;
     const int nx = p.nx, ny = p.ny;
@@ -557,6 +573,8 @@ StepT<float> to_step(const HostParams& h) {
     else if (hd <= hmax) { const float r = hmin / hd; p.Ah[k] = A * (r * r * r); }
     else p.Ah[k] = 0.0f;
   }
+  p.seedw = h.seedw;
+  p.parity = h.parity;
   return p;
 }
 
@@ -564,7 +582,14 @@ StepT<float> to_step(const HostParams& h) {
 // planes: 18 float planes (FP32) or 9 half2 deviation planes (FP16-dev). L2 fetches of the
 // box rows (192 bytes) are promoted to 128-byte lines (256-byte promotion measured 3% slower
 // on back-to-back 2048 x 256 steps).
-bool encode_pop(CUtensorMap* m, const void* base, const HostParams& h, unsigned planes = 2 * kQ) {
+CUtensorMapL2promotion promotion_of(int bytes) {
+  return bytes <= 0 ? CU_TENSOR_MAP_L2_PROMOTION_NONE
+                    : (bytes <= 64 ? CU_TENSOR_MAP_L2_PROMOTION_L2_64B
+                                   : (bytes <= 128 ? CU_TENSOR_MAP_L2_PROMOTION_L2_128B
+                                                   : CU_TENSOR_MAP_L2_PROMOTION_L2_256B));
+}
+
+bool encode_pop(CUtensorMap* m, const void* base, const HostParams& h, unsigned planes = 2 * kQ, int promo = 128) {
   auto fn = encode_fn();
   if (!fn) return false;
   const cuuint64_t dims[3] = {(cuuint64_t)h.nx, (cuuint64_t)h.ny, planes};
@@ -572,12 +597,12 @@ bool encode_pop(CUtensorMap* m, const void* base, const HostParams& h, unsigned 
   const cuuint32_t box[3] = {kBX, kBY, planes};
   const cuuint32_t es[3] = {1, 1, 1};
   return fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<void*>(base), dims, strides, box, es,
-            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, promotion_of(promo),
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
 // Reference densities of an FP16-dev state as a 2-D tensor (2 nx floats, ny), box 96 x 28.
-bool encode_rho(CUtensorMap* m, const void* base, const HostParams& h) {
+bool encode_rho(CUtensorMap* m, const void* base, const HostParams& h, int promo = 128) {
   auto fn = encode_fn();
   if (!fn) return false;
   const cuuint64_t dims[2] = {(cuuint64_t)h.nx * 2, (cuuint64_t)h.ny};
@@ -585,7 +610,7 @@ bool encode_rho(CUtensorMap* m, const void* base, const HostParams& h) {
   const cuuint32_t box[2] = {2 * kBX, kBY};
   const cuuint32_t es[2] = {1, 1};
   return fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<void*>(base), dims, strides, box, es,
-            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, promotion_of(promo),
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
@@ -637,14 +662,18 @@ cudaError_t launch_any(const CUtensorMap& map, const CUtensorMap& map_rho, const
 
 bool tma2d_supported(const HostParams& h) { return h.nx % 4 == 0 && h.nz == 1 && encode_fn() != nullptr; }
 
-cudaError_t tma2d_prepare(TmaMaps* m, const void* fa, const void* fb, const HostParams& h) {
+cudaError_t tma2d_prepare(TmaMaps* m, const void* fa, const void* fb, const HostParams& h, int promo) {
   static_assert(sizeof(CUtensorMap) == 128, "tensor map size");
   CUtensorMap* maps = reinterpret_cast<CUtensorMap*>(m->bytes);
   std::memset(m->bytes, 0, sizeof(m->bytes));
-  if (!h.half) return encode_pop(&maps[0], fa, h) && encode_pop(&maps[1], fb, h) ? cudaSuccess : cudaErrorInvalidValue;
+  if (!h.half)
+    return encode_pop(&maps[0], fa, h, 2 * kQ, promo) && encode_pop(&maps[1], fb, h, 2 * kQ, promo)
+               ? cudaSuccess
+               : cudaErrorInvalidValue;
   const size_t ro = HalfDev<0>::rho_offset((size_t)h.N);
-  const bool ok = encode_pop(&maps[0], fa, h, kQ) && encode_pop(&maps[1], fb, h, kQ) &&
-                  encode_rho(&maps[2], (const char*)fa + ro, h) && encode_rho(&maps[3], (const char*)fb + ro, h);
+  const bool ok = encode_pop(&maps[0], fa, h, kQ, promo) && encode_pop(&maps[1], fb, h, kQ, promo) &&
+                  encode_rho(&maps[2], (const char*)fa + ro, h, promo) &&
+                  encode_rho(&maps[3], (const char*)fb + ro, h, promo);
   return ok ? cudaSuccess : cudaErrorInvalidValue;
 }
 
@@ -661,6 +690,7 @@ cudaError_t tma2d_step(const TmaMaps& m, int from, const void* fa, void* fb, int
   a.parity = from & 1;  // the state alternates with every step, and so do the counters
   a.ntx = (p.nx + TX - 1) / TX;
   a.ntiles = a.ntx * ((p.ny + TY - 1) / TY);
+  a.nstatic = 2;
   return launch_any<false>(map, map_rho, fa, fb, p, a, h.smax, h.forcing == 1, h.half != 0, h.num_sms, s);
 }
 
@@ -686,8 +716,9 @@ int tma2d_member_fill(void* table, int k, int nmem, const TmaMaps& m, const Host
 }
 
 cudaError_t tma2d_batch_step(const void* members, int nmem, int total_tiles, int state, int* err, int* counter,
-                             int smax_max, int edm, int half, int num_sms, cudaStream_t s) {
+                             int smax_max, int edm, int half, int num_sms, int nstatic, cudaStream_t s) {
   TmaArgs a{};
+  a.nstatic = nstatic;
   a.err = err;
   a.counter = counter;
   a.parity = state & 1;

@@ -26,7 +26,8 @@ EXPORTS = ("lb_workspace_size", "lb_create", "lb_init_fields", "lb_step", "lb_ob
            "lb_fields", "lb_get_populations", "lb_set_populations", "lb_destroy",
            "lb_last_error", "lb_kernel_launches", "lb_step_path", "lb_observables_noalloc",
            "lb_ensemble_create", "lb_ensemble_member", "lb_ensemble_step", "lb_ensemble_tune",
-           "lb_ensemble_tune_times", "lb_ensemble_launches", "lb_ensemble_last_error", "lb_ensemble_destroy")
+           "lb_ensemble_tune_times", "lb_ensemble_tma_choice", "lb_ensemble_launches",
+           "lb_ensemble_last_error", "lb_ensemble_destroy")
 
 
 class lb_config(ctypes.Structure):
@@ -108,6 +109,8 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
     lib.lb_ensemble_step.argtypes = [simp, ctypes.c_longlong]
     lib.lb_ensemble_tune.argtypes = [simp, ctypes.POINTER(ctypes.c_int)]
     lib.lb_ensemble_tune_times.argtypes = [simp, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_float)]
+    lib.lb_ensemble_tma_choice.argtypes = [simp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                                           ctypes.POINTER(ctypes.c_float)]
     lib.lb_ensemble_launches.argtypes = [simp]
     lib.lb_ensemble_launches.restype = ctypes.c_longlong
     lib.lb_ensemble_last_error.argtypes = [simp]
@@ -350,6 +353,7 @@ class Ensemble:
     """Owning wrapper of lb_ensemble_*: members are Sim-like views (no ownership)."""
 
     def __init__(self, cfgs):
+        self.h = None
         arr = (lb_config * len(cfgs))(*cfgs)
         h = ctypes.c_void_p()
         _echeck(load().lb_ensemble_create(arr, len(cfgs), ctypes.byref(h)))
@@ -373,6 +377,17 @@ class Ensemble:
         a, b = ctypes.c_float(0), ctypes.c_float(0)
         _echeck(load().lb_ensemble_tune_times(self.h, ctypes.byref(a), ctypes.byref(b)), self.h)
         return a.value, b.value
+
+    def tma_choice(self):
+        """(L2 promotion bytes, static tiles per CTA, {(promotion, static tiles): ms per step})
+        of the batched TMA kernel; the table is empty before any tune()."""
+        pr, st = ctypes.c_int(0), ctypes.c_int(0)
+        ms = (ctypes.c_float * 12)()
+        _echeck(load().lb_ensemble_tma_choice(self.h, ctypes.byref(pr), ctypes.byref(st), ms), self.h)
+        table = {(pb, 1 + i): float(ms[k * 3 + i]) for k, pb in enumerate((0, 64, 128, 256)) for i in range(3)}
+        if not any(table.values()):
+            table = {}
+        return pr.value, st.value, table
 
     def launches(self) -> int:
         return int(load().lb_ensemble_launches(self.h))

@@ -75,10 +75,15 @@ def test_autotune_keeps_state_and_results():
             m.init_fields(fl.rho1, fl.rho2)
         ens.step(3)
         before = [m.get_populations() for m in ens.members]
+        assert ens.tma_choice()[:2] == (128, 2) and ens.tma_choice()[2] == {}
         spt = ens.tune()
         assert spt in (2, 4)
         t2, t4 = ens.tune_times()
         assert t2 > 0 and t4 > 0
+        promo, nstatic, table = ens.tma_choice()
+        assert promo in (0, 64, 128, 256) and nstatic in (1, 2, 3)
+        assert len(table) == 12 and all(v > 0 for v in table.values())
+        assert table[(promo, nstatic)] == min(table.values())
         after = [m.get_populations() for m in ens.members]
         for a, b in zip(before, after):
             assert np.array_equal(a, b)  # tuning wrote only the back buffers
@@ -89,6 +94,42 @@ def test_autotune_keeps_state_and_results():
             sim.init_fields(fl.rho1, fl.rho2)
             sim.step(8)
             assert np.array_equal(got[k], sim.get_populations()), f"member {k}"
+
+
+@pytest.mark.parametrize("choice", ["0:1", "64:3", "256:2"])
+def test_tma_candidates_give_identical_results(monkeypatch, choice):
+    """Every (L2 promotion, static tiles) candidate the autotuner may pick steps the
+    members exactly as the lattices stepped alone: the choice moves tiles between CTAs
+    and changes cache hints, never the arithmetic of a site."""
+    monkeypatch.setenv("LBNCI_TMA_CHOICE", choice)
+    cfgs, fields = _cfgs(lbnci.LB_FP16DEV)
+    with lbnci.Ensemble(cfgs) as ens:
+        pr, st, _ = ens.tma_choice()
+        assert f"{pr}:{st}" == choice
+        for m, fl in zip(ens.members, fields):
+            m.init_fields(fl.rho1, fl.rho2)
+        ens.step(6)
+        got = [m.get_populations() for m in ens.members]
+    monkeypatch.delenv("LBNCI_TMA_CHOICE")
+    for k, (c, fl) in enumerate(zip(cfgs, fields)):
+        with lbnci.Sim(c) as sim:
+            sim.init_fields(fl.rho1, fl.rho2)
+            sim.step(6)
+            assert np.array_equal(got[k], sim.get_populations()), f"member {k}"
+
+
+def test_tma_choice_env_is_validated(monkeypatch):
+    monkeypatch.setenv("LBNCI_TMA_CHOICE", "96:2")
+    cfgs, _ = _cfgs(lbnci.LB_FP32)
+    with pytest.raises(lbnci.LBError):
+        lbnci.Ensemble(cfgs)
+
+
+def test_tma_choice_needs_a_tma_member():
+    cfgs, _ = _cfgs(lbnci.LB_FP64)
+    with lbnci.Ensemble(cfgs) as ens:
+        with pytest.raises(lbnci.LBError):
+            ens.tma_choice()
 
 
 def test_flow_rate_grows_with_forcing():

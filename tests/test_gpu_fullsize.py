@@ -26,8 +26,8 @@ import bench
 import oracle
 from paper_2003_11069_gb300 import inputs, lbnci
 
-from test_gpu_parity import FP32_TOL, _cfg, _near_tie_sites
-from test_gpu_precision import FP16DEV_STEP_TOL
+from test_gpu_parity import _cfg, _near_tie_sites
+from test_gpu_precision import step_error
 
 pytestmark = pytest.mark.gpu
 
@@ -59,10 +59,11 @@ def _mem_available_gb():
     return 0.0
 
 
-def _compare(p, f0, got, gpu_hit, tol, sites=None):
+def _compare(p, f0, got, gpu_hit, precision, sites=None):
     """One oracle step from f0 against the GPU's step `got` ([2][Q][N] arrays of the
     lattice p); `gpu_hit` = the GPU's NCI hit map of f0; `sites` = the compared site
-    indices (all when None). Returns (max relative error, number of compared sites)."""
+    indices (all when None). Returns (max error in units of the precision's per-step
+    bound, number of compared sites)."""
     ref = oracle.step(p, f0, 1, nthreads=0)
     near, of = _near_tie_sites(p, f0)
     Q, N = oracle.Q_of(p), oracle.N_of(p)
@@ -73,15 +74,13 @@ def _compare(p, f0, got, gpu_hit, tol, sites=None):
     assert ok.sum() > 0.95 * sel.sum()
     if p.A_h > 0:
         assert (of["hit"][ok] > 0).sum() > 0, "NCI must be active among the compared sites"
-    g2, r2 = got.reshape(2 * Q, N)[:, ok], ref.reshape(2 * Q, N)[:, ok]
-    w = np.tile(oracle.lattice(p.lattice)[1], 2)[:, None]  # w_i of row k = (component, i)
-    err = float((np.abs(g2 - r2) / np.maximum(np.abs(r2), w)).max())
-    assert err <= tol, err
+    err = float(step_error(p, got, ref, precision)[:, ok].max())
+    assert err <= 1.0, err
     return err, int(ok.sum())
 
 
-@pytest.mark.parametrize("precision,tol", [(lbnci.LB_FP32, FP32_TOL), (lbnci.LB_FP16DEV, FP16DEV_STEP_TOL)])
-def test_channel2048x256_full_size(precision, tol):
+@pytest.mark.parametrize("precision", [lbnci.LB_FP32, lbnci.LB_FP16DEV])
+def test_channel2048x256_full_size(precision):
     p, w = _params("channel2d")
     fl = w["gen"](p.nx, p.ny, p.nz, SEED)
     with lbnci.Sim(_cfg(p, precision)) as sim:
@@ -92,8 +91,8 @@ def test_channel2048x256_full_size(precision, tol):
         hit = sim.fields()["hit"]
         sim.step(1)
         got = sim.get_populations()
-    err, n = _compare(p, f0, got, hit, tol)
-    print(f"channel 2048x256 precision {precision}: max rel err {err:.2e} over {n} sites")
+    err, n = _compare(p, f0, got, hit, precision)
+    print(f"channel 2048x256 precision {precision}: max error {err:.3f} of the per-step bound over {n} sites")
 
 
 def _slab(f, p, xs):
@@ -104,8 +103,8 @@ def _slab(f, p, xs):
     return np.ascontiguousarray(v).reshape(-1)
 
 
-@pytest.mark.parametrize("precision,tol", [(lbnci.LB_FP32, FP32_TOL), (lbnci.LB_FP16DEV, FP16DEV_STEP_TOL)])
-def test_duct512x128x128_full_size_slabs(precision, tol):
+@pytest.mark.parametrize("precision", [lbnci.LB_FP32, lbnci.LB_FP16DEV])
+def test_duct512x128x128_full_size_slabs(precision):
     if _mem_available_gb() < 16:
         pytest.skip("needs several GB of host memory (the 3.6 GB FP64 state, fields, slabs)")
     p, w = _params("duct3d")
@@ -134,12 +133,12 @@ def test_duct512x128x128_full_size_slabs(precision, tol):
     keep = (lx >= SLAB_EDGE) & (lx < SLAB - SLAB_EDGE)
     sites = np.flatnonzero(np.broadcast_to(keep, (p.nz, p.ny, SLAB)).reshape(-1))
     for k, (a, b, h) in enumerate(zip(f0s, gots, hits)):
-        err, n = _compare(ps, a, b, h, tol, sites)
-        print(f"duct 512x128x128 precision {precision} slab {k}: max rel err {err:.2e} over {n} sites")
+        err, n = _compare(ps, a, b, h, precision, sites)
+        print(f"duct 512x128x128 precision {precision} slab {k}: max error {err:.3f} of the per-step bound over {n} sites")
 
 
-@pytest.mark.parametrize("precision,tol", [(lbnci.LB_FP32, FP32_TOL), (lbnci.LB_FP16DEV, FP16DEV_STEP_TOL)])
-def test_ensemble96_full_size_sampled_members(precision, tol):
+@pytest.mark.parametrize("precision", [lbnci.LB_FP32, lbnci.LB_FP16DEV])
+def test_ensemble96_full_size_sampled_members(precision):
     w = bench.WORKLOADS["ensemble"]
     members = inputs.ensemble_channels(w["members"], seed=SEED)
     cfgs = [lbnci.lb_config_make(nx=m.nx, ny=m.ny, wall_y=1, tau=w["tau"], A_s=w["A_s"], beta=w["beta"],
@@ -162,5 +161,5 @@ def test_ensemble96_full_size_sampled_members(precision, tol):
         m = members[k]
         p = oracle.make_params(lattice=oracle.D2Q9, nx=m.nx, ny=m.ny, wall_y=1, tau=w["tau"], A_s=w["A_s"],
                                beta=w["beta"], A_h=m.A_h, force=(m.force, 0.0, 0.0))
-        err, n = _compare(p, f0[k], got[k], hits[k], tol)
-        print(f"ensemble member {k} ({m.nx}x{m.ny}, A_h {m.A_h:.3f}): max rel err {err:.2e} over {n} sites")
+        err, n = _compare(p, f0[k], got[k], hits[k], precision)
+        print(f"ensemble member {k} ({m.nx}x{m.ny}, A_h {m.A_h:.3f}): max error {err:.3f} of the per-step bound over {n} sites")

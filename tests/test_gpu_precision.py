@@ -2,11 +2,13 @@
 
 LB_FP16DEV stores populations as FP16 deviations delta = f - w_i rho_ref from the
 lattice-weight equilibrium at rest (FP32 reference densities per site) and computes in
-FP32. Tolerances follow from FP16's 11-bit significand: a stored deviation is rounded
-by at most 2^-11 |delta| (plus 2^-25 near zero), and |delta| <= 0.3 w_i on these
-states, so one step is within 3e-4 of the oracle on the population scale max(|f|, w_i).
-The long-run test states each observable's error (psi and u in L2, the dispersed
-flow rate, the droplet count, mass drift) for FP32 and FP16-dev storage.
+FP32. Tolerances follow from FP16's 11-bit significand: a state set from the host is
+rounded to nearest (within 2^-11 |delta|, plus 2^-25 near zero); a step's output is
+rounded stochastically (within one FP16 unit, 2^-10 |delta|, or 2^-24 below FP16's
+normal range), on top of the FP32 arithmetic (step_error). The long-run tests state
+each observable's error (psi and u in L2, the dispersed flow rate, the droplet count,
+mass drift) for FP32 and FP16-dev storage, and compare flow rates averaged over long
+horizons.
 """
 import numpy as np
 import pytest
@@ -14,11 +16,26 @@ import pytest
 import oracle
 from paper_2003_11069_gb300 import inputs, lbnci
 
-from test_gpu_parity import _near_tie_sites
+from test_gpu_parity import FP32_TOL, _near_tie_sites
 
 pytestmark = pytest.mark.gpu
 
-FP16DEV_STEP_TOL = 3e-4
+
+def step_error(p, got, ref, precision):
+    """Per element ([2 Q, N]) |got - ref| in units of what one step may differ by in
+    `precision`: FP32, FP32_TOL on the population scale max(|f|, w_i); FP16-deviation
+    storage, in addition one stochastically rounded FP16 store of the deviation
+    delta = f - w_i rho_k (less than one FP16 unit: 2^-10 |delta|, or 2^-24 below FP16's
+    normal range). rho_k, the site's density of component k, is the same before and
+    after the step (the collision keeps each component's mass). At most 1 passes."""
+    Q, N = oracle.Q_of(p), oracle.N_of(p)
+    _, w, _ = oracle.lattice(p.lattice)
+    r3, g3 = ref.reshape(2, Q, N), got.reshape(2, Q, N)
+    bound = FP32_TOL * np.maximum(np.abs(r3), w[None, :, None])
+    if precision == lbnci.LB_FP16DEV:
+        dev = r3 - w[None, :, None] * r3.sum(axis=1)[:, None, :]
+        bound = bound + 2.0 ** -10 * np.abs(dev) + 2.0 ** -24
+    return (np.abs(g3 - r3) / bound).reshape(2 * Q, N)
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -88,10 +105,10 @@ def test_fp16dev_one_step_tolerance(lat):
     Q, N = oracle.Q_of(p), oracle.N_of(p)
     differ = fields["hit"] != of["hit"]
     assert not (differ & ~near).any(), f"{int((differ & ~near).sum())} NCI decisions differ away from ties"
-    rel = (np.abs(got - ref) / _scale(p, ref)).reshape(2 * Q, N)
+    err = step_error(p, got, ref, lbnci.LB_FP16DEV)
     ok = ~near
     assert (of["hit"][ok] > 0).sum() > 0
-    assert rel[:, ok].max() <= FP16DEV_STEP_TOL, rel[:, ok].max()
+    assert err[:, ok].max() <= 1.0, err[:, ok].max()
 
 
 def _droplets(psi2d):
@@ -151,3 +168,41 @@ def test_observable_errors_fp32_and_fp16dev(A_h, steps, bounds):
         b = bounds[name]
         assert rep["L2_psi"] <= b[0] and rep["L2_u"] <= b[1] and rep["Q_d"] <= b[2] and rep["mass"] <= b[3], rep
         assert rep["droplets"] == n_ref
+
+
+def test_time_averaged_dispersed_flow_rate_over_20k_steps():
+    """Equal flow-rate accuracy over a long horizon with the near-contact force on: the
+    512 x 64 crop of the channel workload (walls in y, packed droplets, G = 1e-5) with
+    A_h = 0.005 runs 20,000 steps in the FP64 oracle, in FP32 and with FP16-deviation
+    storage; the dispersed flow rate Q_d averaged over the second half of the run (41
+    samples, every 250 steps) must agree with the oracle's within 0.2%, a fifth of the
+    1% asked of the storage formats (measured on GB300: FP32 1.4e-4, FP16-dev 2.6e-4;
+    FP16-dev stores rounded to nearest instead of stochastically were 6.3e-3 low). At
+    this A_h the flow is not chaotic: an FP64 run whose initial densities are perturbed
+    by 1e-7 ends within 1e-9 of the unperturbed one, so a difference is an error of the
+    arithmetic. (At A_h = 0.05 the same perturbation moves the average by 8% after
+    40,000 steps: no precision can be held to 1% there.)"""
+    nx, ny, steps, every = 512, 64, 20000, 250
+    p = oracle.make_params(lattice=oracle.D2Q9, nx=nx, ny=ny, wall_y=1, tau=1.0, A_s=0.01, beta=0.7, A_h=0.005,
+                           force=(1e-5, 0, 0))
+    fl = inputs.channel_emulsion_2d(nx, ny, seed=1234)
+    f = oracle.init(p, fl.rho1, fl.rho2)
+    q_ref = []
+    for k in range(steps // every):
+        oracle.step_inplace(p, f, every, 0)
+        if (k + 1) * every >= steps // 2:
+            q_ref.append(oracle.observables(p, f)["flow_rate_disp"])
+    ref = float(np.mean(q_ref))
+    assert (oracle.fields(p, f)["hit"] > 0).sum() > 0  # the near-contact force acts
+    for name, prec in (("fp32", lbnci.LB_FP32), ("fp16dev", lbnci.LB_FP16DEV)):
+        q = []
+        with lbnci.Sim(_cfg(p, prec)) as sim:
+            sim.init_fields(fl.rho1, fl.rho2)
+            for k in range(steps // every):
+                sim.step(every)
+                if (k + 1) * every >= steps // 2:
+                    q.append(sim.observables()["flow_rate_disp"])
+        rel = abs(float(np.mean(q)) - ref) / abs(ref)
+        print(f"{name}: time-averaged Q_d {np.mean(q):.6e} vs oracle {ref:.6e}: rel. difference {rel:.2e}")
+        assert len(q) == len(q_ref) == 41
+        assert rel <= 0.002, (name, rel)

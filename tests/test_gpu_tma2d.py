@@ -15,6 +15,7 @@ import oracle
 from paper_2003_11069_gb300 import inputs, lbnci
 
 from test_gpu_parity import FP32_TOL, _cfg, _near_tie_sites, _scale
+from test_gpu_precision import step_error
 
 pytestmark = pytest.mark.gpu
 
@@ -80,7 +81,7 @@ def test_fp32_tma2d_steps(name):
 def test_fp16dev_tma2d_steps(name):
     """FP16-deviation storage on the TMA kernel (deviation planes and reference densities
     copied by TMA, decoded in shared memory): each step within the FP16-dev per-step bound
-    (3e-4 on the population scale) of one oracle step from the GPU's own previous state."""
+    (step_error) of one oracle step from the GPU's own previous state."""
     case = CASES[name]
     p = oracle.make_params(lattice=oracle.D2Q9, **case["p"])
     fl = case["gen"]()
@@ -95,9 +96,9 @@ def test_fp16dev_tma2d_steps(name):
             got = sim.get_populations()
             ref = oracle.step(p, f0, 1)
             near, _ = _near_tie_sites(p, f0)
-            rel = (np.abs(got - ref) / _scale(p, ref)).reshape(2 * Q, N)
+            err = step_error(p, got, ref, lbnci.LB_FP16DEV)
             assert (~near).mean() > 0.97
-            assert rel[:, ~near].max() <= 3e-4, f"{name}: {rel[:, ~near].max():.3e}"
+            assert err[:, ~near].max() <= 1.0, f"{name}: {err[:, ~near].max():.3f}"
         assert sim.observables()["n_bad"] == 0
 
 
