@@ -97,8 +97,9 @@ WORKLOADS = {
 STEP_KERNELS = {0: "fused2d_kernel (one-pass D2Q9 step)",
                 1: "tma2d_kernel (persistent TMA-fed D2Q9 step, one launch per step)",
                 2: "moments_kernel + march3d_kernel (D3Q27 two-pass step, two launches)",
-                3: "interface3d_kernel + carry3d_kernel (D3Q27 single-read step: densities carried by the "
-                   "previous collision, TMA-fed collision; two launches)"}
+                3: "interface3d_kernel + nci3d_kernel + carry3d_kernel (D3Q27 single-read step: densities "
+                   "carried by the previous collision, interface pass, NCI ray pass, TMA-fed collision; three "
+                   "launches)"}
 
 
 # Bytes of state moved per site update (1 read + 1 write): FP64/FP32 populations are
