@@ -100,7 +100,13 @@ lb_status lbu_train_step(lbu_net* net, const float* X, const float* T, const int
  * y[p][o] (BF16 bits, pixel stride y_stride elements) = act(b[o] + sum w[o][t][c] x[...])
  * with x BF16 [batch][h][w][c] (pixel stride x_stride, image h x w, or h/2 x w/2 when
  * upsample = 1: nearest 2x upsampling on the fly), w BF16 [C_out][9][C_in], b FP32 or
- * NULL, act = ReLU when relu = 1. C_in and C_out multiples of 32; strides multiples of 8. */
+ * NULL, act = ReLU when relu = 1. C_in and C_out multiples of 32; strides multiples of 8.
+ * The convolutions run on mma.sync tensor-core instructions; with the environment
+ * variable LBNCI_UNET_MMA=tcgen05 (read at every launch) they run on tcgen05.mma with the
+ * accumulator in tensor memory instead. That kernel's waits are bounded: an expired wait
+ * leaves its output unwritten and sets a device error word, which the next lbu_forward
+ * (host output), lbu_loss_grad or lbu_train_step (with a loss pointer) reports as
+ * LB_ECUDA after it synchronises. */
 lb_status lbu_conv3x3(const unsigned short* x, int x_stride, int batch, int h, int w, int c_in,
                       int upsample, const unsigned short* wgt, const float* bias, int relu,
                       unsigned short* y, int y_stride, int c_out, void* stream);

@@ -5,6 +5,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 #include <string>
@@ -12,6 +13,12 @@
 
 #include "lbnci_unet.h"
 #include "unet_kernels.cuh"
+#include "unet_tc.cuh"
+
+// Error word of the tensor-core convolutions: bit 0 set when a bounded mbarrier wait
+// expired (the launch then wrote no output). Read and cleared by the calls that
+// synchronise their stream.
+__device__ int g_tc_err;
 
 using lbu::bf16;
 
@@ -171,6 +178,47 @@ int grid_for(long long work, int threads) {
   return (int)std::max<long long>(1, std::min<long long>(b, 152LL * 16));
 }
 
+template <int BN, int BK>
+cudaError_t launch_conv_tc_k(const lbu::ConvFwd& a, dim3 grid, cudaStream_t s) {
+  int* err = nullptr;
+  cudaError_t e = cudaGetSymbolAddress((void**)&err, g_tc_err);
+  if (e != cudaSuccess) return e;
+  constexpr int smem = lbu::tc::Smem<BN, BK>::kBytes;
+  e = cudaFuncSetAttribute(lbu::conv3x3_tc_kernel<BN, BK>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e != cudaSuccess) return e;
+  grid.y = a.Cout / BN;
+  lbu::conv3x3_tc_kernel<BN, BK><<<grid, lbu::kTcThreads, smem, s>>>(a, err);
+  return cudaGetLastError();
+}
+// chunks of 32 input channels (stages of 10-16 KB: three to five CTAs of 8 warps per SM)
+template <int BN>
+cudaError_t launch_conv_tc(const lbu::ConvFwd& a, dim3 grid, cudaStream_t s) {
+  return launch_conv_tc_k<BN, 32>(a, grid, s);
+}
+
+// LBNCI_UNET_MMA=tcgen05 selects the tensor-memory convolution (unet_tc.cuh). It computes
+// the same sums (equal to the mma.sync kernel's bit for bit on the measured layers) but is
+// slower here: 7.1 ms against 5.5 ms per training step of batch 32 at 64 x 256; the
+// mma.sync kernel stays the default.
+bool conv_on_tcgen05() {
+  const char* e = std::getenv("LBNCI_UNET_MMA");
+  return e && std::strcmp(e, "tcgen05") == 0;
+}
+
+// Reports (and clears) an expired wait of a tensor-core convolution; call after a
+// synchronisation of the stream.
+lb_status check_tc(lbu_net* n) {
+  int v = 0;
+  cudaError_t e = cudaMemcpyFromSymbol(&v, g_tc_err, sizeof(int));
+  if (e != cudaSuccess) return cuda_fail(n, e, "error word read");
+  if (v) {
+    const int zero = 0;
+    cudaMemcpyToSymbol(g_tc_err, &zero, sizeof(int));
+    return fail(n, LB_ECUDA, "a tensor-core convolution's mbarrier wait expired (no output written)");
+  }
+  return LB_OK;
+}
+
 // one 3x3 convolution launch (forward or data gradient)
 lb_status conv(lbu_net* n, const bf16* x, int xs, int B, int H, int W, int cin, int up, const bf16* w,
                const float* bias, int relu, bf16* y, int ys, int cout, const bf16* mask, int ms,
@@ -178,6 +226,12 @@ lb_status conv(lbu_net* n, const bf16* x, int xs, int B, int H, int W, int cin, 
   lbu::ConvFwd a{x, xs, B, H, W, cin, up, w, bias, relu, y, ys, cout, mask, ms};
   const int M = B * H * W;
   dim3 grid((M + lbu::kConvBM - 1) / lbu::kConvBM, 1);
+  if (conv_on_tcgen05()) {
+    cudaError_t e = cout % 128 == 0 ? launch_conv_tc<128>(a, grid, s)
+                                    : (cout % 64 == 0 ? launch_conv_tc<64>(a, grid, s) : launch_conv_tc<32>(a, grid, s));
+    if (n) ++n->launches;
+    return e == cudaSuccess ? LB_OK : cuda_fail(n, e, "conv3x3 (tcgen05) launch");
+  }
   if (cout % 64 == 0) {
     grid.y = cout / 64;
     lbu::conv3x3_kernel<64><<<grid, 128, 0, s>>>(a);
@@ -567,7 +621,10 @@ lb_status lbu_forward(lbu_net* n, const float* x, int batch, float* y, int on_de
   LBU_TRY(forward_impl(n, batch));
   LBU_CUDA(n, cudaMemcpyAsync(y, n->y, batch * HW * n->cfg.out_ch * sizeof(float),
                               on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, n->stream));
-  if (!on_device) LBU_CUDA(n, cudaStreamSynchronize(n->stream));
+  if (!on_device) {
+    LBU_CUDA(n, cudaStreamSynchronize(n->stream));
+    LBU_TRY(check_tc(n));
+  }
   return LB_OK;
 }
 
@@ -585,6 +642,7 @@ lb_status lbu_loss_grad(lbu_net* n, const float* X, const float* T, const int* i
     double h = 0.0;
     LBU_CUDA(n, cudaMemcpyAsync(&h, n->loss, sizeof(double), cudaMemcpyDeviceToHost, n->stream));
     LBU_CUDA(n, cudaStreamSynchronize(n->stream));
+    LBU_TRY(check_tc(n));
     *loss = (float)h;
   }
   return LB_OK;
@@ -607,6 +665,7 @@ lb_status lbu_train_step(lbu_net* n, const float* X, const float* T, const int* 
     double h = 0.0;
     LBU_CUDA(n, cudaMemcpyAsync(&h, n->loss, sizeof(double), cudaMemcpyDeviceToHost, n->stream));
     LBU_CUDA(n, cudaStreamSynchronize(n->stream));
+    LBU_TRY(check_tc(n));
     *loss = (float)h;
   }
   return LB_OK;

@@ -41,13 +41,19 @@ def _op_check(got, exact, scale, K):
     assert np.mean(got == U.bf16(exact)) >= 0.99, np.mean(got == U.bf16(exact))
 
 
+@pytest.mark.parametrize("mma", ["tcgen05", "sync"])
 @pytest.mark.parametrize("B,H,W,Ci,Co,up,relu,xs_pad,ys_pad", [
     (2, 16, 32, 32, 64, 0, 1, 0, 0),
     (1, 8, 24, 64, 32, 0, 0, 32, 32),   # strided views (channel slices), 192 pixels: ragged tile
     (3, 8, 16, 64, 64, 1, 1, 0, 64),    # nearest-upsampled input
     (1, 2, 4, 256, 128, 0, 1, 0, 0),    # coarsest-level shape
+    (2, 8, 32, 128, 256, 0, 1, 0, 0),   # two output-channel tiles of 128
+    (1, 8, 40, 32, 96, 0, 0, 0, 32),    # three output-channel tiles of 32, 320 pixels
 ])
-def test_conv3x3_forward(B, H, W, Ci, Co, up, relu, xs_pad, ys_pad):
+def test_conv3x3_forward(B, H, W, Ci, Co, up, relu, xs_pad, ys_pad, mma, monkeypatch):
+    """mma: the convolution on the fifth-generation tensor cores (tcgen05.mma, accumulator
+    in tensor memory; LBNCI_UNET_MMA=tcgen05) or on the mma.sync path (the default)."""
+    monkeypatch.setenv("LBNCI_UNET_MMA", mma)
     rng = np.random.default_rng(B * 100 + Ci + Co)
     hi, wi = (H // 2, W // 2) if up else (H, W)
     xs, ys = Ci + xs_pad, Co + ys_pad
@@ -108,8 +114,11 @@ def _rel(a, b):
     return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-30)
 
 
-@pytest.mark.parametrize("levels", [2, 3, 4])
-def test_network_forward_loss_and_gradients(levels):
+@pytest.mark.parametrize("levels,mma", [(2, "sync"), (3, "sync"), (4, "sync"), (3, "tcgen05")])
+def test_network_forward_loss_and_gradients(levels, mma, monkeypatch):
+    """mma: which kernel runs the 3x3 convolutions and their data gradients (the mma.sync
+    default, or tcgen05.mma with the accumulator in tensor memory)."""
+    monkeypatch.setenv("LBNCI_UNET_MMA", mma)
     cfg, params, x, t = _small(levels=levels, H=16, W=32, B=2, seed=levels)
     lam = [1.0, 0.5, 2.0]
     L_e, g_e, y_e = U.loss_and_grads(params, x, t, levels=levels, lam=lam, emulate_bf16=True)
