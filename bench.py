@@ -99,7 +99,9 @@ STEP_KERNELS = {0: "fused2d_kernel (one-pass D2Q9 step)",
                 2: "moments_kernel + march3d_kernel (D3Q27 two-pass step, two launches)",
                 3: "interface3d_kernel + nci3d_kernel + carry3d_kernel (D3Q27 single-read step: densities "
                    "carried by the previous collision, interface pass, NCI ray pass, TMA-fed collision; three "
-                   "launches)"}
+                   "launches)",
+                4: "moments_kernel + normals3d_kernel + collide3d_kernel (D3Q27 streaming step: psi, per-site "
+                   "normals, then the NCI ray, pull, collision and store without shared memory; three launches)"}
 
 
 # Bytes of state moved per site update (1 read + 1 write): FP64/FP32 populations are

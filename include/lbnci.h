@@ -188,14 +188,17 @@ long long lb_kernel_launches(const lb_sim* sim);
  *   LB_PATH_FUSED2D  one-pass fused D2Q9 kernel (FP64; FP32 and FP16-dev when nx % 4 != 0
  *                    or LBNCI_FUSED=classic is set in the environment),
  *   LB_PATH_TMA2D    persistent TMA-fed D2Q9 kernel (FP32 and FP16-dev storage),
- *   LB_PATH_D3Q27    D3Q27 two-pass step: moments, then the collision kernel (FP64; FP32 and
- *                    FP16-dev when nx % 32 != 0 or ny % 8 != 0, or when LBNCI_D3_KERNEL=march
- *                    or tiled is set in the environment),
- *   LB_PATH_D3Q27_CARRY  D3Q27 single-read step (FP32 and FP16-dev): an interface pass over
- *                    densities the previous collision carried forward, then a TMA-fed
- *                    collision that reads each population once.
+ *   LB_PATH_D3Q27    D3Q27 two-pass step: moments, then the collision kernel marching along
+ *                    z (FP64; FP32 and FP16-dev when nx % 32 != 0 or ny % 8 != 0, or when
+ *                    LBNCI_D3_KERNEL=march or tiled is set in the environment),
+ *   LB_PATH_D3Q27_CARRY  D3Q27 single-read step (FP32 and FP16-dev, LBNCI_D3_KERNEL=carry): an
+ *                    interface pass over densities the previous collision carried forward,
+ *                    a ray pass, then a TMA-fed collision that reads each population once,
+ *   LB_PATH_D3Q27_STREAM  D3Q27 streaming step (FP32 and FP16-dev on lattices of whole
+ *                    32 x 8 columns: the default there): moments, per-site normals, then a
+ *                    collision kernel that runs the NCI ray and needs no shared memory.
  * Returns -1 for a NULL sim. */
-enum { LB_PATH_FUSED2D = 0, LB_PATH_TMA2D = 1, LB_PATH_D3Q27 = 2, LB_PATH_D3Q27_CARRY = 3 };
+enum { LB_PATH_FUSED2D = 0, LB_PATH_TMA2D = 1, LB_PATH_D3Q27 = 2, LB_PATH_D3Q27_CARRY = 3, LB_PATH_D3Q27_STREAM = 4 };
 int lb_step_path(const lb_sim* sim);
 
 /* ------------------------------------------------------------------------------

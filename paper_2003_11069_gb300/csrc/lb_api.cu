@@ -178,16 +178,17 @@ lb_status validate(const lb_config* c, HostParams* p, Layout* lay, long long* nb
   // LBNCI_TMA_STALL_TEST=1 makes every CTA's first wait run out after about a second.
   p->tma_stall_test = 0;
   if (const char* e = std::getenv("LBNCI_TMA_STALL_TEST")) p->tma_stall_test = std::atoi(e) == 1 ? 1 : 0;
-  // D3Q27 step on lattices of whole 32 x 8 columns: the single-read kernels (density
-  // carry) for FP16-dev storage, where they are the faster step; FP32 runs the two-pass
-  // step unless LBNCI_D3_KERNEL=carry (LBNCI_D3_KERNEL=march or tiled: the two-pass step
-  // for both)
-  const bool carry_ok = c->lattice == LB_D3Q27 && (c->precision == LB_FP32 || c->precision == LB_FP16DEV) &&
-                        c->nx % 32 == 0 && c->ny % 8 == 0 && (c->wall_z || c->nz >= 2);
-  p->carry3d = carry_ok && c->precision == LB_FP16DEV ? 1 : 0;
+  // D3Q27 FP32 / FP16-dev step on lattices of whole 32 x 8 columns: the streaming step
+  // (moments, normals, collision with the ray), the fastest measured; LBNCI_D3_KERNEL=carry
+  // selects the single-read step (density carry), march or tiled the two-pass step, which
+  // the other lattices and FP64 run
+  const bool col_ok = c->lattice == LB_D3Q27 && (c->precision == LB_FP32 || c->precision == LB_FP16DEV) &&
+                      c->nx % 32 == 0 && c->ny % 8 == 0 && (c->wall_z || c->nz >= 2);
+  p->carry3d = 0;
+  p->stream3d = col_ok ? 1 : 0;
   if (const char* e = std::getenv("LBNCI_D3_KERNEL")) {
-    if (std::strcmp(e, "march") == 0 || std::strcmp(e, "tiled") == 0) p->carry3d = 0;
-    if (std::strcmp(e, "carry") == 0 && carry_ok) p->carry3d = 1;
+    if (std::strcmp(e, "march") == 0 || std::strcmp(e, "tiled") == 0) p->stream3d = 0;
+    if (std::strcmp(e, "carry") == 0 && col_ok) { p->carry3d = 1; p->stream3d = 0; }
   }
   // z segment of the single-read collision kernel (planes; LBNCI_C3_ZSEG, default 16)
   p->c3_zseg = 16;
@@ -210,6 +211,9 @@ lb_status validate(const lb_config* c, HostParams* p, Layout* lay, long long* nb
     lay->ghost = off; off = align256(off + carry3d_ghost_bytes(*p));
     lay->ng = off; off = align256(off + (size_t)N * 16);
     lay->hit = off; off = align256(off + (size_t)N);
+  }
+  if (p->stream3d) {
+    lay->ng = off; off = align256(off + (size_t)N * 16);
   }
   lay->total = off;
   return LB_OK;
@@ -344,6 +348,10 @@ lb_status lb_create(const lb_config* cfg, lb_sim** out) {
       s->p.carry3d = 0;
     cudaGetLastError();
   }
+  if (s->p.stream3d) {
+    s->ng = base + lay.ng;
+    if (!stream3d_supported(s->p)) s->p.stream3d = 0;
+  }
   s->carry_ok = false;
   e = cudaMallocHost((void**)&s->host_result, 16 * sizeof(double));
   if (e != cudaSuccess) {
@@ -404,6 +412,8 @@ lb_status lb_step(lb_sim* s, long long nsteps) {
       e = tma2d_step(s->maps, s->fa == s->buf_a ? 0 : 1, s->fa, s->fb, s->errflag, s->tile_counter, s->p,
                      s->stream);
       nk = 1;
+    } else if (s->p.stream3d) {
+      e = stream3d_step(s->fa, s->fb, s->psi, s->ng, s->p, s->stream, &nk);
     } else if (s->p.carry3d) {
       if (!s->carry_ok) {  // a state no step produced: its densities from the populations
         e = carry3d_init(s->fa, s->carry, s->ring, s->ghost, s->p, s->stream);
@@ -564,7 +574,8 @@ long long lb_kernel_launches(const lb_sim* s) { return s ? s->launches : 0; }
 
 int lb_step_path(const lb_sim* s) {
   if (!s) return -1;
-  if (s->cfg.lattice == LB_D3Q27) return s->p.carry3d ? LB_PATH_D3Q27_CARRY : LB_PATH_D3Q27;
+  if (s->cfg.lattice == LB_D3Q27)
+    return s->p.carry3d ? LB_PATH_D3Q27_CARRY : (s->p.stream3d ? LB_PATH_D3Q27_STREAM : LB_PATH_D3Q27);
   return s->p.tma ? LB_PATH_TMA2D : LB_PATH_FUSED2D;
 }
 

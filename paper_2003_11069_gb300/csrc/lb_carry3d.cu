@@ -1,5 +1,6 @@
 // lb_carry3d.cu -- launchers and tensor maps of the single-read D3Q27 step
 // (lb_carry3d.cuh) for FP32 and FP16-deviation storage.
+#include <cstdlib>
 #include <cstring>
 
 #include "lb_carry3d.cuh"
@@ -212,6 +213,47 @@ cudaError_t carry3d_step(const TmaMaps& m, int from, const void* fa, void* fb, v
   const CUtensorMap& mb = maps[h.half ? 2 + from : from];
   e = h.half ? launch_c3_any<HalfDev<1>>(ma, mb, maps[4], maps[5], fa, fb, p, a, h.num_sms, s)
              : launch_c3_any<Plain<1, float>>(ma, mb, maps[4], maps[5], fa, fb, p, a, h.num_sms, s);
+  if (e == cudaSuccess) ++*nk;
+  return e;
+}
+
+namespace {
+template <typename ST>
+cudaError_t launch_collide3d(const void* fa, void* fb, const float4* ng, const StepT<float>& p, dim3 grid,
+                             cudaStream_t s) {
+  if (p.edm)
+    collide3d_kernel<ST, true><<<grid, dim3(32, 8), 0, s>>>(ST::reader(fa, (unsigned)p.N),
+                                                            ST::writer(fb, (unsigned)p.N), ng, p);
+  else
+    collide3d_kernel<ST, false><<<grid, dim3(32, 8), 0, s>>>(ST::reader(fa, (unsigned)p.N),
+                                                             ST::writer(fb, (unsigned)p.N), ng, p);
+  return cudaGetLastError();
+}
+}  // namespace
+
+bool stream3d_supported(const HostParams& h) { return h.nx % 32 == 0 && h.ny % 8 == 0; }
+
+cudaError_t stream3d_step(const void* fa, void* fb, void* psi, void* ng, const HostParams& h, cudaStream_t s,
+                          int* nk) {
+  const StepT<float> p = to_step3(h);
+  *nk = 0;
+  const unsigned nb = (unsigned)((p.N + 255) / 256);
+  if (h.half)
+    moments_kernel<1, HalfDev<1>><<<nb, 256, 0, s>>>(HalfDev<1>::reader(fa, (unsigned)p.N), (float*)psi, p);
+  else
+    moments_kernel<1, Plain<1, float>><<<nb, 256, 0, s>>>(Plain<1, float>::reader(fa, (unsigned)p.N), (float*)psi,
+                                                         p);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  ++*nk;
+  const dim3 grid((unsigned)(h.nx / 32), (unsigned)(h.ny / 8), (unsigned)h.nz);
+  const dim3 gridn((unsigned)(h.nx / 32), (unsigned)(h.ny / 8), (unsigned)((h.nz + kN3Z - 1) / kN3Z));
+  normals3d_kernel<<<gridn, dim3(32, 8), 0, s>>>((const float*)psi, (float4*)ng, p);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  ++*nk;
+  e = h.half ? launch_collide3d<HalfDev<1>>(fa, fb, (const float4*)ng, p, grid, s)
+             : launch_collide3d<Plain<1, float>>(fa, fb, (const float4*)ng, p, grid, s);
   if (e == cudaSuccess) ++*nk;
   return e;
 }

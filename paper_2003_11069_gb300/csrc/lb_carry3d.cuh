@@ -175,12 +175,9 @@ __global__ void __launch_bounds__(kC3T) interface3d_kernel(const float2* __restr
 // when |grad psi| > g_th; probes y_s = x + round(s n), s = 1..smax (half away from zero
 // per component); a probe beyond a wall ends the search; the first probe that is an
 // interface site facing x (n(y).n(x) < 0) gives h = s. Blocks of 32 x 8 sites, one plane.
-__global__ void __launch_bounds__(256) nci3d_kernel(const float4* __restrict__ ng, unsigned char* __restrict__ hit,
-                                                    StepT<float> p) {
-  const int x = blockIdx.x * 32 + threadIdx.x, y = blockIdx.y * 8 + threadIdx.y, z = blockIdx.z;
+__device__ __forceinline__ int nci_ray(const float4* __restrict__ ng, const float4 v, int x, int y, int z,
+                                       const StepT<float>& p) {
   const int nx = p.nx, ny = p.ny, nz = p.nz;
-  const unsigned site = (unsigned)x + (unsigned)nx * ((unsigned)y + (unsigned)ny * (unsigned)z);
-  const float4 v = ng[site];
   int h = 0;
   if (v.w > p.g_th) {
     const float n0 = v.x, n1 = v.y, n2 = v.z;
@@ -226,7 +223,14 @@ __global__ void __launch_bounds__(256) nci3d_kernel(const float4* __restrict__ n
       decide(std::integral_constant<int, 3>{});
     }
   }
-  hit[site] = (unsigned char)h;
+  return h;
+}
+
+__global__ void __launch_bounds__(256) nci3d_kernel(const float4* __restrict__ ng, unsigned char* __restrict__ hit,
+                                                    StepT<float> p) {
+  const int x = blockIdx.x * 32 + threadIdx.x, y = blockIdx.y * 8 + threadIdx.y, z = blockIdx.z;
+  const unsigned site = (unsigned)x + (unsigned)p.nx * ((unsigned)y + (unsigned)p.ny * (unsigned)z);
+  hit[site] = (unsigned char)nci_ray(ng, ng[site], x, y, z, p);
 }
 
 // ------------------------------------------------------------------ collision + carry
@@ -737,6 +741,87 @@ carry3d_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_constant_
     }
     item += gridDim.x;
   }
+}
+
+// ---------------------------------------------------------------------------------
+// The streaming D3Q27 step (FP32 and FP16-dev storage; lattices of whole 32 x 8 columns):
+// moments_kernel writes psi; normals3d_kernel the per-site (n, |grad psi|);
+// collide3d_kernel then runs the near-contact ray of its site over those normals (probes
+// through L2), pulls, collides and stores, with no shared memory and no barrier, its
+// block's neighbours reading the same planes at the same time from L2.
+
+// (n, |grad psi|) of a 32 x 8 column's sites on kN3Z consecutive planes from the psi
+// array: the block keeps psi of its 34 x 10 cells (beyond a wall the mirror cell, along
+// periodic axes the image) on three planes in a shared-memory ring, loading one new plane
+// per plane it computes; every site sums its 26 neighbours in direction order.
+constexpr int kN3Z = 16;
+__global__ void __launch_bounds__(256) normals3d_kernel(const float* __restrict__ psi, float4* __restrict__ ng,
+                                                        StepT<float> p) {
+  constexpr int RX = 34, RXY = RX * 10;
+  __shared__ float s_psi[3 * RXY];
+  const int x0 = blockIdx.x * 32, y0 = blockIdx.y * 8, z0 = blockIdx.z * kN3Z;
+  const int nx = p.nx, ny = p.ny, nz = p.nz;
+  const int tid = threadIdx.x + 32 * threadIdx.y;
+  const int z1 = min(nz, z0 + kN3Z);
+  auto load_plane = [&](int q) {  // plane q (wrapped or mirrored) into ring slot q mod 3
+    const int gz = p.wall_z ? clampc(q, nz) : wrapn(q, nz);
+    float* dst = s_psi + ((q + 3) % 3) * RXY;
+    for (int c = tid; c < RXY; c += 256) {
+      const int ly = c / RX, lx = c - ly * RX;
+      const int gx = wrapn(x0 - 1 + lx, nx);
+      const int gy = p.wall_y ? clampc(y0 - 1 + ly, ny) : wrapn(y0 - 1 + ly, ny);
+      dst[c] = psi[(unsigned)gx + (unsigned)nx * ((unsigned)gy + (unsigned)ny * (unsigned)gz)];
+    }
+  };
+  load_plane(z0 - 1);
+  load_plane(z0);
+  const int x = x0 + threadIdx.x, y = y0 + threadIdx.y;
+  const int cxy = (threadIdx.x + 1) + RX * (threadIdx.y + 1);
+  for (int z = z0; z < z1; ++z) {
+    load_plane(z + 1);
+    __syncthreads();
+    // the three planes z - 1, z, z + 1 in their ring slots
+    const float* pm = s_psi + ((z + 2) % 3) * RXY;
+    const float* p0 = s_psi + (z % 3) * RXY;
+    const float* pp = s_psi + ((z + 1) % 3) * RXY;
+    float g[3];
+    grad_ring<float>(pm, p0, pp, RX, cxy, g);
+    float n[3];
+    const float gn = M<float>::unit(g, n);
+    ng[(unsigned)x + (unsigned)nx * ((unsigned)y + (unsigned)ny * (unsigned)z)] = make_float4(n[0], n[1], n[2], gn);
+    __syncthreads();  // plane z - 1's slot is reloaded next
+  }
+}
+
+template <typename ST, bool EDM>
+__global__ void __launch_bounds__(256) collide3d_kernel(typename ST::Reader f, typename ST::Writer fout,
+                                                        const float4* __restrict__ ng, StepT<float> p) {
+  const int x = blockIdx.x * 32 + threadIdx.x, y = blockIdx.y * 8 + threadIdx.y, z = blockIdx.z;
+  if constexpr (ST::kHalf)
+    fout.seed = step_seed(p, p.parity, blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0 && threadIdx.x == 0 &&
+                                           threadIdx.y == 0);
+  const int site = x + p.nx * (y + p.ny * z);
+  const float4 v = ng[site];
+  const int h = p.smax > 0 ? nci_ray(ng, v, x, y, z, p) : 0;
+  float fin[2][27];
+  pull_any<1, float>(f, x, y, z, p, fin);
+  float rho1, rho2;
+  psi_of<27, float>(fin, &rho1, &rho2);
+  const float rho = rho1 + rho2;
+  float j[3];
+  momentum<1, float>(fin, j);
+  float A = 0.f;  // A_h(h), indexed at compile time
+  static_for<kMaxProbe>([&](auto I) {
+    constexpr int s = decltype(I)::value + 1;
+    if (h == s) A = p.Ah[s];
+  });
+  const float deltaI = 0.5f * v.w;
+  const float F[3] = {p.G[0] - A * v.x * deltaI, p.G[1] - A * v.y * deltaI, p.G[2] - A * v.z * deltaI};
+  float u[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) u[a] = M<float>::div(j[a] + 0.5f * F[a], rho);
+  const float m[3] = {-v.x, -v.y, -v.z};
+  collide_store<1, float, typename ST::Writer, EDM>(fin, rho1, rho2, j, u, F, v.w, m, p, fout, site);
 }
 
 }  // namespace lbnci

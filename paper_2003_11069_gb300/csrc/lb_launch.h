@@ -50,6 +50,7 @@ struct HostParams {
                        // so its bounded wait runs out (test of the failure path only)
   int carry3d;    // 1: D3Q27 FP32 / FP16-dev steps run the single-read carry kernels
   int c3_zseg;    // planes per z segment of their collision kernel
+  int stream3d;   // 1: D3Q27 steps run moments, normals and a streaming collision
   unsigned* seedw;  // device: two dither-seed words of the FP16-deviation stores
   int parity;       // state buffer the next step reads (0: the one the sim was created with)
   double tau, A_s, beta, A_h, h_min, h_max, g_th, G[3];
@@ -121,6 +122,12 @@ cudaError_t carry3d_prepare(TmaMaps* m, const void* fa, const void* fb, const vo
 // the carried densities of a state no step produced (pulled from it; rings zeroed)
 cudaError_t carry3d_init(const void* f, void* carry, void* ring, void* ghost, const HostParams& h, cudaStream_t s);
 // one step from state `from` (0: buffer A, 1: buffer B) into the other; *nk = launches
+// Streaming D3Q27 step (lb_carry3d.cu) for FP32 and FP16-dev storage on lattices of whole
+// 32 x 8 columns: moments (psi), normals3d ((n, |grad psi|) into ng, N float4), collide3d
+// (near-contact ray, pull, collision: fa -> fb). Kernels launched -> *nk.
+bool stream3d_supported(const HostParams& h);
+cudaError_t stream3d_step(const void* fa, void* fb, void* psi, void* ng, const HostParams& h, cudaStream_t s,
+                          int* nk);
 cudaError_t carry3d_step(const TmaMaps& m, int from, const void* fa, void* fb, void* carry, void* ring, void* ghost,
                          void* ng, void* hit, int* err, const HostParams& h, cudaStream_t s, int* nk);
 

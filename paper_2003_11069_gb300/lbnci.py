@@ -251,7 +251,7 @@ def lb_kernel_launches(sim) -> int:
     return int(load().lb_kernel_launches(sim))
 
 
-LB_PATH_FUSED2D, LB_PATH_TMA2D, LB_PATH_D3Q27, LB_PATH_D3Q27_CARRY = 0, 1, 2, 3
+LB_PATH_FUSED2D, LB_PATH_TMA2D, LB_PATH_D3Q27, LB_PATH_D3Q27_CARRY, LB_PATH_D3Q27_STREAM = 0, 1, 2, 3, 4
 
 
 def lb_step_path(sim) -> int:

@@ -1,5 +1,5 @@
-"""The single-read D3Q27 step (LB_PATH_D3Q27_CARRY: the default for FP16-dev storage, selected
-for FP32 with LBNCI_D3_KERNEL=carry) against the FP64 oracle.
+"""The single-read D3Q27 step (LB_PATH_D3Q27_CARRY, selected with LBNCI_D3_KERNEL=carry) against
+the FP64 oracle.
 
 The step's colour gradient uses densities that the previous step's collision carried
 forward (each new population summed into the density of the site it streams to, across
@@ -61,7 +61,7 @@ def test_carry3d_steps_match_oracle(name, precision, zseg, monkeypatch):
     lattices; 5: two or three, the last one shorter, so the densities also cross segment
     boundaries through the ghost planes, periodic ones included)."""
     monkeypatch.setenv("LBNCI_C3_ZSEG", zseg)
-    monkeypatch.setenv("LBNCI_D3_KERNEL", "carry")  # FP32 runs the two-pass step by default
+    monkeypatch.setenv("LBNCI_D3_KERNEL", "carry")  # the streaming step is the default
     geo = CASES[name]
     p = oracle.make_params(lattice=oracle.D3Q27, tau=0.9, A_s=0.01, beta=0.7, A_h=0.03, force=(2e-6, 1e-6, 0),
                            **geo)

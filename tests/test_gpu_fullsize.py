@@ -111,8 +111,7 @@ def test_duct512x128x128_full_size_slabs(precision):
     fl = w["gen"](p.nx, p.ny, p.nz, SEED)
     slabs = [np.arange(-SLAB // 2, SLAB // 2) % p.nx, np.arange(200, 200 + SLAB)]  # the seam, the middle
     with lbnci.Sim(_cfg(p, precision)) as sim:
-        assert sim.step_path() == (lbnci.LB_PATH_D3Q27_CARRY if precision == lbnci.LB_FP16DEV
-                                   else lbnci.LB_PATH_D3Q27)
+        assert sim.step_path() == lbnci.LB_PATH_D3Q27_STREAM
         sim.init_fields(fl.rho1, fl.rho2)
         sim.step(WARM_STEPS)
         f0 = sim.get_populations()

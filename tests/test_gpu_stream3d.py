@@ -1,0 +1,64 @@
+"""The streaming D3Q27 step (LB_PATH_D3Q27_STREAM, the default for FP32 and FP16-dev storage on
+lattices of whole 32 x 8 columns): moments_kernel (psi), normals3d_kernel (per-site n and
+|grad psi|) and collide3d_kernel (the near-contact ray over those normals, pull, collision
+and store without shared memory). Each of four
+consecutive steps must lie within the storage's per-step bound of one oracle step from the
+GPU's own previous state (walls in y and z, periodic axes, a lattice of one column), in
+FP32 and FP16-deviation storage, with Guo and EDM forcing; chained steps equal separate
+ones bitwise."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2003_11069_gb300 import lbnci
+
+from test_gpu_carry3d import CASES, _check_step, _duct
+from test_gpu_parity import _cfg
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    lbnci.load()
+
+
+@pytest.mark.parametrize("forcing", [0, 1])
+@pytest.mark.parametrize("precision", [lbnci.LB_FP32, lbnci.LB_FP16DEV])
+@pytest.mark.parametrize("name", list(CASES))
+def test_stream3d_steps_match_oracle(name, precision, forcing, monkeypatch):
+    monkeypatch.delenv("LBNCI_D3_KERNEL", raising=False)
+    geo = CASES[name]
+    p = oracle.make_params(lattice=oracle.D3Q27, tau=0.9, A_s=0.01, beta=0.7, A_h=0.03, force=(2e-6, 1e-6, 0),
+                           forcing=forcing, **geo)
+    fl = _duct(geo["nx"], geo["ny"], geo["nz"], seed=13)
+    f0 = oracle.step(p, oracle.init(p, fl.rho1, fl.rho2), 20)
+    with lbnci.Sim(_cfg(p, precision)) as sim:
+        assert sim.step_path() == lbnci.LB_PATH_D3Q27_STREAM
+        sim.set_populations(f0)
+        start = sim.get_populations()  # the representable state
+        for k in range(4):
+            sim.step(1)
+            got = sim.get_populations()
+            err = _check_step(p, start, got, precision, f"{name} step {k}")
+            print(f"{name} precision {precision} forcing {forcing} step {k}: max error {err:.3f} of the bound")
+            start = got
+        assert sim.observables()["n_bad"] == 0
+
+
+@pytest.mark.parametrize("precision", [lbnci.LB_FP32, lbnci.LB_FP16DEV])
+def test_stream3d_chained_equals_separate(precision, monkeypatch):
+    monkeypatch.delenv("LBNCI_D3_KERNEL", raising=False)
+    p = oracle.make_params(lattice=oracle.D3Q27, nx=64, ny=24, nz=12, wall_y=1, wall_z=1, tau=1.0, A_s=0.01,
+                           beta=0.7, A_h=0.03, force=(2e-6, 0, 0))
+    fl = _duct(64, 24, 12, seed=21)
+    cfg = _cfg(p, precision)
+    with lbnci.Sim(cfg) as a, lbnci.Sim(cfg) as b:
+        assert a.step_path() == lbnci.LB_PATH_D3Q27_STREAM
+        a.init_fields(fl.rho1, fl.rho2)
+        b.init_fields(fl.rho1, fl.rho2)
+        a.step(5)
+        for _ in range(5):
+            b.step(1)
+        assert np.array_equal(a.get_populations(), b.get_populations())
+        assert a.observables()["n_nci"] > 0

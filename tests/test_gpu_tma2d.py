@@ -137,8 +137,8 @@ def test_step_path_selection(monkeypatch):
     assert path(lattice=1, nx=16, ny=8, nz=8, wall_y=1, wall_z=1, tau=1.0, A_s=0.01, beta=0.7,
                 precision=lbnci.LB_FP32) == lbnci.LB_PATH_D3Q27
     d3 = dict(lattice=1, nx=32, ny=8, nz=8, wall_y=1, wall_z=1, tau=1.0, A_s=0.01, beta=0.7)
-    assert path(**d3, precision=lbnci.LB_FP32) == lbnci.LB_PATH_D3Q27
-    assert path(**d3, precision=lbnci.LB_FP16DEV) == lbnci.LB_PATH_D3Q27_CARRY
+    assert path(**d3, precision=lbnci.LB_FP32) == lbnci.LB_PATH_D3Q27_STREAM
+    assert path(**d3, precision=lbnci.LB_FP16DEV) == lbnci.LB_PATH_D3Q27_STREAM
     assert path(**d3, precision=lbnci.LB_FP64) == lbnci.LB_PATH_D3Q27
     assert path(**dict(d3, ny=12), precision=lbnci.LB_FP32) == lbnci.LB_PATH_D3Q27
     monkeypatch.setenv("LBNCI_FUSED", "classic")
@@ -147,6 +147,7 @@ def test_step_path_selection(monkeypatch):
     assert path(**d3, precision=lbnci.LB_FP16DEV) == lbnci.LB_PATH_D3Q27
     monkeypatch.setenv("LBNCI_D3_KERNEL", "carry")
     assert path(**d3, precision=lbnci.LB_FP32) == lbnci.LB_PATH_D3Q27_CARRY
+    assert path(**d3, precision=lbnci.LB_FP16DEV) == lbnci.LB_PATH_D3Q27_CARRY
 
 
 def test_fp32_tma2d_and_classic_agree():
