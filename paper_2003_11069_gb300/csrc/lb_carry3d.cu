@@ -1,6 +1,6 @@
-// lb_carry3d.cu -- launchers and tensor maps of the single-read D3Q27 step
-// (lb_carry3d.cuh) for FP32 and FP16-deviation storage.
-#include <cstdlib>
+// lb_carry3d.cu -- launchers of the D3Q27 steps of lb_carry3d.cuh for FP32 and
+// FP16-deviation storage: the single-read step (with its tensor maps) and the streaming
+// step.
 #include <cstring>
 
 #include "lb_carry3d.cuh"

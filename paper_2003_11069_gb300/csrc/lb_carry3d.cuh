@@ -1,6 +1,10 @@
-// lb_carry3d.cuh -- the D3Q27 step that reads every population once (FP32 and FP16-dev
-// storage; arXiv:2003.11069, "Materials and Methods": Eq. (CGLBE), the colour gradient,
-// the near-contact force of Eq. (near_c) and Omega = Omega^(3)[Omega^(1) + Omega^(2)]).
+// lb_carry3d.cuh -- D3Q27 steps on lattices of whole 32 x 8 columns for FP32 and FP16-dev
+// storage (arXiv:2003.11069, "Materials and Methods": Eq. (CGLBE), the colour gradient,
+// the near-contact force of Eq. (near_c) and Omega = Omega^(3)[Omega^(1) + Omega^(2)]):
+// the single-read step described first, and, at the end of the file, the streaming step
+// (normals3d_kernel, collide3d_kernel after moments_kernel), the default.
+//
+// Single-read step: every population is read once.
 //
 // The colour gradient at a site needs psi, hence the densities rho_k, of its 26
 // neighbours, and rho_k(y) at the start of a step sums the populations streamed into y:
