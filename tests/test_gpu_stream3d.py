@@ -46,6 +46,24 @@ def test_stream3d_steps_match_oracle(name, precision, forcing, monkeypatch):
         assert sim.observables()["n_bad"] == 0
 
 
+@pytest.mark.parametrize("wall_z", [0, 1])
+def test_stream3d_normals_segments(wall_z, monkeypatch):
+    """nz = 37: the normals kernel marches three z segments of 16 planes, the last one of 5,
+    so its psi rings start and end inside the lattice (periodic z: across the seam)."""
+    monkeypatch.delenv("LBNCI_D3_KERNEL", raising=False)
+    p = oracle.make_params(lattice=oracle.D3Q27, nx=32, ny=16, nz=37, wall_y=1, wall_z=wall_z, tau=0.9, A_s=0.01,
+                           beta=0.7, A_h=0.03, force=(2e-6, 0, 1e-6))
+    fl = _duct(32, 16, 37, seed=29)
+    f0 = oracle.step(p, oracle.init(p, fl.rho1, fl.rho2), 15)
+    with lbnci.Sim(_cfg(p, lbnci.LB_FP32)) as sim:
+        assert sim.step_path() == lbnci.LB_PATH_D3Q27_STREAM
+        sim.set_populations(f0)
+        start = sim.get_populations()
+        sim.step(1)
+        err = _check_step(p, start, sim.get_populations(), lbnci.LB_FP32, f"nz 37 wall_z {wall_z}")
+        print(f"nz 37 wall_z {wall_z}: max error {err:.3f} of the bound")
+
+
 @pytest.mark.parametrize("precision", [lbnci.LB_FP32, lbnci.LB_FP16DEV])
 def test_stream3d_chained_equals_separate(precision, monkeypatch):
     monkeypatch.delenv("LBNCI_D3_KERNEL", raising=False)
