@@ -463,7 +463,8 @@ def main(argv=None):
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=12.0)
-    ap.add_argument("--ws-train", type=int, default=768, help="warmstart: training channels")
+    ap.add_argument("--ws-train", type=int, default=2048,
+                    help="warmstart: training channels (2048: about 20k snapshots, 8 minutes on GB300)")
     ap.add_argument("--ws-test", type=int, default=64, help="warmstart: held-out channels")
     ap.add_argument("--ws-horizon", type=int, default=60000, help="warmstart: lattice steps per run")
     ap.add_argument("--study-steps", type=int, default=0,
