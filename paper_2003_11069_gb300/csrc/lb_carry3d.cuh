@@ -805,10 +805,21 @@ __global__ void __launch_bounds__(256) collide3d_kernel(typename ST::Reader f, t
     fout.seed = step_seed(p, p.parity, blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0 && threadIdx.x == 0 &&
                                            threadIdx.y == 0);
   const int site = x + p.nx * (y + p.ny * z);
-  const float4 v = ng[site];
-  const int h = p.smax > 0 ? nci_ray(ng, v, x, y, z, p) : 0;
+  // FP32: the pulls first, so that their loads are in flight while the ray's dependent
+  // probes resolve (2.5% faster); FP16-dev: the ray first (pulls first raised its
+  // registers from 80 to 103, two blocks per SM instead of three: 11% slower)
   float fin[2][27];
-  pull_any<1, float>(f, x, y, z, p, fin);
+  float4 v;
+  int h;
+  if constexpr (!ST::kHalf) {
+    pull_any<1, float>(f, x, y, z, p, fin);
+    v = ng[site];
+    h = p.smax > 0 ? nci_ray(ng, v, x, y, z, p) : 0;
+  } else {
+    v = ng[site];
+    h = p.smax > 0 ? nci_ray(ng, v, x, y, z, p) : 0;
+    pull_any<1, float>(f, x, y, z, p, fin);
+  }
   float rho1, rho2;
   psi_of<27, float>(fin, &rho1, &rho2);
   const float rho = rho1 + rho2;
