@@ -756,35 +756,55 @@ carry3d_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_constant_
 
 // (n, |grad psi|) of a 32 x 8 column's sites on kN3Z consecutive planes from the psi
 // array: the block keeps psi of its 34 x 10 cells (beyond a wall the mirror cell, along
-// periodic axes the image) on three planes in a shared-memory ring, loading one new plane
-// per plane it computes; every site sums its 26 neighbours in direction order.
+// periodic axes the image) on three planes in a shared-memory ring; the loads of plane
+// z + 2 are issued before plane z is computed and stored after it, so their latency
+// overlaps the arithmetic. Every site sums its 26 neighbours in direction order.
 constexpr int kN3Z = 16;
 __global__ void __launch_bounds__(256) normals3d_kernel(const float* __restrict__ psi, float4* __restrict__ ng,
                                                         StepT<float> p) {
-  constexpr int RX = 34, RXY = RX * 10;
+  constexpr int RX = 34, RXY = RX * 10, PER = (RXY + 255) / 256;
   __shared__ float s_psi[3 * RXY];
   const int x0 = blockIdx.x * 32, y0 = blockIdx.y * 8, z0 = blockIdx.z * kN3Z;
   const int nx = p.nx, ny = p.ny, nz = p.nz;
   const int tid = threadIdx.x + 32 * threadIdx.y;
   const int z1 = min(nz, z0 + kN3Z);
-  auto load_plane = [&](int q) {  // plane q (wrapped or mirrored) into ring slot q mod 3
+  auto load = [&](int q, float v[PER]) {  // plane q (wrapped or mirrored) into registers
     const int gz = p.wall_z ? clampc(q, nz) : wrapn(q, nz);
-    float* dst = s_psi + ((q + 3) % 3) * RXY;
-    for (int c = tid; c < RXY; c += 256) {
-      const int ly = c / RX, lx = c - ly * RX;
-      const int gx = wrapn(x0 - 1 + lx, nx);
-      const int gy = p.wall_y ? clampc(y0 - 1 + ly, ny) : wrapn(y0 - 1 + ly, ny);
-      dst[c] = psi[(unsigned)gx + (unsigned)nx * ((unsigned)gy + (unsigned)ny * (unsigned)gz)];
+#pragma unroll
+    for (int k = 0; k < PER; ++k) {
+      const int c = tid + 256 * k;
+      if (c < RXY) {
+        const int ly = c / RX, lx = c - ly * RX;
+        const int gx = wrapn(x0 - 1 + lx, nx);
+        const int gy = p.wall_y ? clampc(y0 - 1 + ly, ny) : wrapn(y0 - 1 + ly, ny);
+        v[k] = psi[(unsigned)gx + (unsigned)nx * ((unsigned)gy + (unsigned)ny * (unsigned)gz)];
+      }
     }
   };
-  load_plane(z0 - 1);
-  load_plane(z0);
+  auto store = [&](int q, const float v[PER]) {  // into ring slot q mod 3
+    float* dst = s_psi + ((q + 3) % 3) * RXY;
+#pragma unroll
+    for (int k = 0; k < PER; ++k) {
+      const int c = tid + 256 * k;
+      if (c < RXY) dst[c] = v[k];
+    }
+  };
+  {
+    float v[PER];
+    load(z0 - 1, v);
+    store(z0 - 1, v);
+    load(z0, v);
+    store(z0, v);
+    load(z0 + 1, v);
+    store(z0 + 1, v);
+  }
+  __syncthreads();
   const int x = x0 + threadIdx.x, y = y0 + threadIdx.y;
   const int cxy = (threadIdx.x + 1) + RX * (threadIdx.y + 1);
   for (int z = z0; z < z1; ++z) {
-    load_plane(z + 1);
-    __syncthreads();
-    // the three planes z - 1, z, z + 1 in their ring slots
+    float vn[PER];
+    const bool more = z + 1 < z1;  // plane z + 2 is needed by the next iteration
+    if (more) load(z + 2, vn);
     const float* pm = s_psi + ((z + 2) % 3) * RXY;
     const float* p0 = s_psi + (z % 3) * RXY;
     const float* pp = s_psi + ((z + 1) % 3) * RXY;
@@ -793,7 +813,9 @@ __global__ void __launch_bounds__(256) normals3d_kernel(const float* __restrict_
     float n[3];
     const float gn = M<float>::unit(g, n);
     ng[(unsigned)x + (unsigned)nx * ((unsigned)y + (unsigned)ny * (unsigned)z)] = make_float4(n[0], n[1], n[2], gn);
-    __syncthreads();  // plane z - 1's slot is reloaded next
+    __syncthreads();  // plane z - 1's slot is free
+    if (more) store(z + 2, vn);
+    __syncthreads();
   }
 }
 
