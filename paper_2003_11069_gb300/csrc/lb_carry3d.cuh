@@ -819,6 +819,19 @@ __global__ void __launch_bounds__(256) normals3d_kernel(const float* __restrict_
   }
 }
 
+// psi of every site, in 32 x 8 blocks of one plane (the streaming step's moments pass for
+// FP16-dev storage): a block's sources lie within 3 planes of 34 x 10 cells, so the
+// reference densities each pulled population is decoded with are reused from L1 by the
+// block's other sites.
+template <typename ST>
+__global__ void __launch_bounds__(256) moments3_kernel(typename ST::Reader f, float* __restrict__ psi,
+                                                       StepT<float> p) {
+  const int x = blockIdx.x * 32 + threadIdx.x, y = blockIdx.y * 8 + threadIdx.y, z = blockIdx.z;
+  float fin[2][27];
+  pull_any<1, float>(f, x, y, z, p, fin);
+  psi[x + p.nx * (y + p.ny * z)] = psi_of<27, float>(fin);
+}
+
 template <typename ST, bool EDM>
 __global__ void __launch_bounds__(256) collide3d_kernel(typename ST::Reader f, typename ST::Writer fout,
                                                         const float4* __restrict__ ng, StepT<float> p) {
