@@ -3,18 +3,17 @@
 //
 // Implicit GEMM as in conv3x3_kernel (unet_kernels.cuh): D[m][n] = sum_k A[m][k] B[n][k]
 // with m a pixel (128 per CTA), n an output channel (BN = 32, 64 or 128 per CTA) and
-// k = (tap, input channel) in chunks of BK = 64 channels of one tap (32 where the layer
-// has fewer). Per chunk, all 128 threads copy the A rows (the tap-shifted pixels' BK
-// channels, zero rows beyond the first and last image row, periodic columns) and the B
-// rows (the weights) with cp.async into a ring of stages (4 of BK = 64, 6 of BK = 32),
-// in the tensor cores' K-major layout without swizzle: 8 x
-// 16-byte core matrices of 128 contiguous bytes, core matrices adjacent along K 128 bytes
-// apart (leading byte offset), 8-row groups BK x 16 bytes apart (stride byte offset).
-// One thread issues BK/16 tcgen05.mma (K = 16 each) per chunk, accumulating in BN columns
-// of tensor memory, and commits them to the stage's mbarrier; chunks are copied two
-// stages short of the ring ahead of the MMAs, so a stage is refilled once the mbarrier
-// says the MMAs of two chunks back, which read it, are done. The epilogue reads the accumulator
-// with tcgen05.ld (warp w: lanes 32 w .. 32 w + 31, i.e. pixels 32 w ..), adds the bias,
+// k = (tap, input channel) in chunks of BK = 32 channels of one tap. Per chunk, all 256
+// threads copy the A rows (the tap-shifted pixels' BK channels, zero rows beyond the first
+// and last image row, periodic columns) and the B rows (the weights) with cp.async into a
+// ring of four stages, in the tensor cores' K-major layout without swizzle: 8 x 16-byte
+// core matrices of 128 contiguous bytes, core matrices adjacent along K 128 bytes apart
+// (leading byte offset), 8-row groups BK x 16 bytes apart (stride byte offset). One thread
+// issues BK/16 tcgen05.mma (K = 16 each) per chunk, accumulating in BN columns of tensor
+// memory, and commits them to the stage's mbarrier; chunks are copied two stages ahead of
+// the MMAs, so a stage is refilled once the mbarrier says the MMAs of two chunks back,
+// which read it, are done. The epilogue reads the accumulator with tcgen05.ld (warp w:
+// lanes 32 (w % 4) .., i.e. pixels 32 (w % 4) .., columns of half w / 4), adds the bias,
 // applies ReLU or the ReLU-derivative mask and stores BF16.
 //
 // Every mbarrier wait is bounded (about a second of %globaltimer); on expiry the kernel
