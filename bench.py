@@ -102,13 +102,21 @@ STEP_KERNELS = {0: "fused2d_kernel (one-pass D2Q9 step)",
                    "launches)",
                 4: "moments_kernel + normals3d_kernel + collide3d_kernel (D3Q27 streaming step: psi, per-site "
                    "normals, then the NCI ray, pull, collision and store without shared memory; three launches)"}
+STATE_FORMS = {0: "pairs: the populations of both components",
+               1: "total + recolouring: the total populations f*_i of the 26 moving directions, the rest "
+                  "population of each component and (rho_1/rho, beta rho_1 rho_2/rho m) per site, 128 B "
+                  "(two-population FP32: 216 B); the moments pass is moments3_kernel<TotalRecol> and the "
+                  "collision collide3t_kernel"}
 
 
 # Bytes of state moved per site update (1 read + 1 write): FP64/FP32 populations are
 # 2 components x Q values; FP16-dev stores Q half2 deviations plus a float2 of
-# reference densities per site.
-def alg_bytes_per_site(lattice: int, precision: str) -> int:
+# reference densities per site; the total + recolouring form (state form 1, FP32 D3Q27)
+# 26 total populations, 2 rest populations and a float4 of coefficients.
+def alg_bytes_per_site(lattice: int, precision: str, form: int = 0) -> int:
     Q = 9 if lattice == 0 else 27
+    if form == 1:
+        return 2 * ((Q + 1) * 4 + 16)
     per_site = {"fp64": 2 * Q * 8, "fp32": 2 * Q * 4, "fp16dev": Q * 4 + 8}[precision]
     return 2 * per_site
 
@@ -540,6 +548,7 @@ def main(argv=None):
             torch.cuda.synchronize()
         launches = sim.launches() - launches0
         path = sim.step_path()
+        form = sim.state_form()
         if big:
             step_ms = [starts[0].elapsed_time(ends[0])]
         else:
@@ -580,7 +589,7 @@ def main(argv=None):
         return 0
 
     peak, peak_kind = measured_hbm_peak()
-    bpsite = alg_bytes_per_site(w["lattice"], args.precision)
+    bpsite = alg_bytes_per_site(w["lattice"], args.precision, form)
     achieved = bpsite * N / (ms_per_step * 1e-3) / 1e9
     traffic = recorded_traffic(args.workload, args.precision)
     cpu = None
@@ -604,6 +613,7 @@ def main(argv=None):
                           f"{flush_mb // 2} MB read so the flush's dirty lines are written back "
                           f"before the step); each step timed alone" if flush_mb > 0 else "not flushed"),
                    "step_kernel": STEP_KERNELS.get(path, "?"),
+                   "state_form": STATE_FORMS.get(form, "?"),
                    "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU",
                    "droplets": fl.meta.get("droplets"),
                    "fraction": fl.meta.get("area_fraction", fl.meta.get("volume_fraction"))},

@@ -201,6 +201,25 @@ long long lb_kernel_launches(const lb_sim* sim);
 enum { LB_PATH_FUSED2D = 0, LB_PATH_TMA2D = 1, LB_PATH_D3Q27 = 2, LB_PATH_D3Q27_CARRY = 3, LB_PATH_D3Q27_STREAM = 4 };
 int lb_step_path(const lb_sim* sim);
 
+/* The form in which lb_step stores the state between steps (reporting only; every other
+ * call sees the populations of both components whatever the form):
+ *   LB_STATE_PAIRS          the populations f_i^1, f_i^2 of both components, in the
+ *                           storage the precision names,
+ *   LB_STATE_TOTAL_RECOLOUR FP32 streaming D3Q27 steps with Guo forcing (unless
+ *                           LBNCI_D3_STATE=pairs is set in the environment): the total
+ *                           post-collision populations f*_i = f_i^1 + f_i^2 of the 26
+ *                           moving directions, the rest population of each component and,
+ *                           per site, phi_1 = rho_1/rho and s = beta (rho_1 rho_2/rho) m,
+ *                           from which the recolouring ("Materials and Methods",
+ *                           Omega^(3)) gives f_i^1 = phi_1 f*_i + (w_i/|c_i|) c_i.s and
+ *                           f_i^2 = f*_i - f_i^1: 128 instead of 216 bytes per site. A call
+ *                           that reads the state (lb_fields, lb_observables,
+ *                           lb_get_populations) first rewrites it as pairs, one extra
+ *                           kernel launch.
+ * Returns -1 for a NULL sim. */
+enum { LB_STATE_PAIRS = 0, LB_STATE_TOTAL_RECOLOUR = 1 };
+int lb_state_form(const lb_sim* sim);
+
 /* ------------------------------------------------------------------------------
  * Ensembles: n independent D2Q9 lattices of different sizes and parameters (each a
  * full lb_config: size, walls, tau, A_s, beta, A_h, h_min, h_max, g_th, force) stepped

@@ -74,6 +74,8 @@ struct lb_sim {
   void* ng;
   void* hit;
   bool carry_ok;   // the carried densities belong to the current state
+  void* rho1;      // streaming D3Q27 path: rho_1 of each site from the moments pass
+  bool totals_state;  // fa holds the total + recolouring form (p.totals)
   double* partials;
   double* result;  // kRedSlots doubles
   double* host_result;  // pinned
@@ -113,7 +115,7 @@ size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
 constexpr int kErrSlot = 12;
 
 struct Layout {
-  size_t fa, fb, psi, partials, result, carry, ring, ghost, ng, hit, total;
+  size_t fa, fb, psi, partials, result, carry, ring, ghost, ng, hit, rho1, total;
 };
 
 const Launchers* launchers_for(const lb_config* c) {
@@ -190,6 +192,11 @@ lb_status validate(const lb_config* c, HostParams* p, Layout* lay, long long* nb
     if (std::strcmp(e, "march") == 0 || std::strcmp(e, "tiled") == 0) p->stream3d = 0;
     if (std::strcmp(e, "carry") == 0 && col_ok) { p->carry3d = 1; p->stream3d = 0; }
   }
+  // FP32 streaming steps with Guo forcing store the total + recolouring form (128 instead
+  // of 216 bytes per site), unless LBNCI_D3_STATE=pairs keeps the two-population layout
+  p->totals = p->stream3d && c->precision == LB_FP32 && c->forcing == 0 ? 1 : 0;
+  if (const char* e = std::getenv("LBNCI_D3_STATE"))
+    if (std::strcmp(e, "pairs") == 0) p->totals = 0;
   // z segment of the single-read collision kernel (planes; LBNCI_C3_ZSEG, default 16)
   p->c3_zseg = 16;
   if (const char* e = std::getenv("LBNCI_C3_ZSEG")) p->c3_zseg = std::atoi(e) > 0 ? std::atoi(e) : 16;
@@ -197,6 +204,7 @@ lb_status validate(const lb_config* c, HostParams* p, Layout* lay, long long* nb
   (void)Q;
   const Launchers* L = launchers_for(c);
   const size_t state = L->state_bytes((size_t)N);
+  if (p->totals && stream3d_totals_bytes((size_t)N) > state) p->totals = 0;  // the form lives in a state buffer
   *nblocks = tiled_blocks(c->lattice, *p);
   size_t off = 0;
   lay->fa = off; off = align256(off + state);
@@ -204,7 +212,7 @@ lb_status validate(const lb_config* c, HostParams* p, Layout* lay, long long* nb
   lay->psi = off; off = align256(off + (size_t)N * L->compute_elem);
   lay->partials = off; off = align256(off + (size_t)(*nblocks) * kRedSlots * sizeof(double));
   lay->result = off; off = align256(off + 16 * sizeof(double));
-  lay->carry = lay->ring = lay->ghost = lay->ng = lay->hit = off;
+  lay->carry = lay->ring = lay->ghost = lay->ng = lay->hit = lay->rho1 = off;
   if (p->carry3d) {
     lay->carry = off; off = align256(off + (size_t)N * 8);
     lay->ring = off; off = align256(off + carry3d_ring_bytes(*p));
@@ -214,6 +222,7 @@ lb_status validate(const lb_config* c, HostParams* p, Layout* lay, long long* nb
   }
   if (p->stream3d) {
     lay->ng = off; off = align256(off + (size_t)N * 16);
+    lay->rho1 = off; off = align256(off + (size_t)N * sizeof(float));
   }
   lay->total = off;
   return LB_OK;
@@ -229,9 +238,24 @@ long long staging_chunk(const lb_sim* s) {
   return fit >= s->p.N ? s->p.N : fit;
 }
 
+// A state in the total + recolouring form rewritten in the two-population layout that
+// the fields kernel and the population copies read: into the back buffer, which then
+// becomes the state (the same populations; the next step reads this layout).
+lb_status ensure_pairs(lb_sim* s) {
+  if (!s->totals_state) return LB_OK;
+  cudaError_t e = stream3d_totals_to_pairs(s->fa, s->fb, s->p, s->stream);
+  ++s->launches;
+  if (e != cudaSuccess) return cuda_fail(s, e, "state conversion");
+  std::swap(s->fa, s->fb);
+  s->totals_state = false;
+  return LB_OK;
+}
+
 // Run the fields kernel on the current state with the given device outputs and
 // fill s->host_result with the reduced observables (synchronises the stream).
 lb_status run_fields(lb_sim* s, const FieldOut& outs) {
+  lb_status ps = ensure_pairs(s);
+  if (ps != LB_OK) return ps;
   FieldOut fo = outs;
   fo.partials = s->partials;
   int nk = 0;
@@ -350,8 +374,11 @@ lb_status lb_create(const lb_config* cfg, lb_sim** out) {
   }
   if (s->p.stream3d) {
     s->ng = base + lay.ng;
+    s->rho1 = base + lay.rho1;
     if (!stream3d_supported(s->p)) s->p.stream3d = 0;
   }
+  if (!s->p.stream3d) s->p.totals = 0;
+  s->totals_state = false;
   s->carry_ok = false;
   e = cudaMallocHost((void**)&s->host_result, 16 * sizeof(double));
   if (e != cudaSuccess) {
@@ -391,6 +418,7 @@ lb_status lb_init_fields(lb_sim* s, const double* rho1, const double* rho2, cons
   if (e == cudaSuccess) e = s->L->init(s->fa, d1, d2, du, s->p, s->stream);
   ++s->launches;
   s->carry_ok = false;
+  s->totals_state = false;
   if (e != cudaSuccess) return cuda_fail(s, e, "init launch");
   if (!on_device) {
     e = cudaStreamSynchronize(s->stream);
@@ -413,7 +441,8 @@ lb_status lb_step(lb_sim* s, long long nsteps) {
                      s->stream);
       nk = 1;
     } else if (s->p.stream3d) {
-      e = stream3d_step(s->fa, s->fb, s->psi, s->ng, s->p, s->stream, &nk);
+      e = stream3d_step(s->fa, s->fb, s->psi, s->ng, s->rho1, s->totals_state ? 1 : 0, s->p, s->stream, &nk);
+      if (e == cudaSuccess) s->totals_state = stream3d_stores_totals(s->p);
     } else if (s->p.carry3d) {
       if (!s->carry_ok) {  // a state no step produced: its densities from the populations
         e = carry3d_init(s->fa, s->carry, s->ring, s->ghost, s->p, s->stream);
@@ -501,6 +530,8 @@ lb_status lb_get_populations(lb_sim* s, double* f, int on_device) {
   if (!s) return fail(nullptr, LB_EINVAL, "sim is NULL");
   if (!f) return fail(s, LB_EINVAL, "f is NULL");
   const int N = s->p.N, Q2 = 2 * s->Q;
+  lb_status ps = ensure_pairs(s);
+  if (ps != LB_OK) return ps;
   cudaError_t e;
   if (on_device) {
     e = s->L->decode(s->fa, f, 0, N, N, N, s->stream);
@@ -532,6 +563,7 @@ lb_status lb_set_populations(lb_sim* s, const double* f, int on_device) {
   const int N = s->p.N, Q2 = 2 * s->Q;
   cudaError_t e = cudaMemsetAsync(s->p.seedw, 0, 2 * sizeof(unsigned), s->stream);  // the dither sequence restarts
   if (e != cudaSuccess) return cuda_fail(s, e, "seed reset");
+  s->totals_state = false;
   if (on_device) {
     e = s->L->encode(f, s->fa, 0, N, N, N, s->stream);
     ++s->launches;
@@ -577,6 +609,11 @@ int lb_step_path(const lb_sim* s) {
   if (s->cfg.lattice == LB_D3Q27)
     return s->p.carry3d ? LB_PATH_D3Q27_CARRY : (s->p.stream3d ? LB_PATH_D3Q27_STREAM : LB_PATH_D3Q27);
   return s->p.tma ? LB_PATH_TMA2D : LB_PATH_FUSED2D;
+}
+
+int lb_state_form(const lb_sim* s) {
+  if (!s) return -1;
+  return s->p.stream3d && stream3d_stores_totals(s->p) ? LB_STATE_TOTAL_RECOLOUR : LB_STATE_PAIRS;
 }
 
 }  // extern "C"

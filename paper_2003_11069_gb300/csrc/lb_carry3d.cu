@@ -233,20 +233,31 @@ cudaError_t launch_collide3d(const void* fa, void* fb, const float4* ng, const S
 
 bool stream3d_supported(const HostParams& h) { return h.nx % 32 == 0 && h.ny % 8 == 0; }
 
-cudaError_t stream3d_step(const void* fa, void* fb, void* psi, void* ng, const HostParams& h, cudaStream_t s,
-                          int* nk) {
+bool stream3d_stores_totals(const HostParams& h) { return h.totals && !h.half && h.forcing != 1; }
+
+cudaError_t stream3d_step(const void* fa, void* fb, void* psi, void* ng, void* rho1, int totals_in,
+                          const HostParams& h, cudaStream_t s, int* nk) {
   const StepT<float> p = to_step3(h);
   *nk = 0;
+  const bool totals_out = stream3d_stores_totals(h);
+  if (totals_in && !totals_out) return cudaErrorInvalidValue;  // no step reads that form into pairs
   const dim3 grid((unsigned)(h.nx / 32), (unsigned)(h.ny / 8), (unsigned)h.nz);
-  // FP16-dev: 32 x 8 blocks, whose sources' reference densities repeat within the block
-  // (0.85 ms per duct step against 0.95 ms with blocks of 256 consecutive sites); FP32 has
-  // no per-source data to share and keeps the flat kernel (the same time)
+  const unsigned N = (unsigned)p.N;
+  // 32 x 8 blocks where the sources carry per-site data that repeats within the block
+  // (FP16-dev: the reference densities, 0.85 ms per duct step against 0.95 ms with blocks
+  // of 256 consecutive sites; the total form: the recolouring coefficients, about two
+  // thirds of whose sectors hit L1); the two-population FP32 state has none and keeps the
+  // flat kernel (the same time)
   if (h.half) {
-    moments3_kernel<HalfDev<1>><<<grid, dim3(32, 8), 0, s>>>(HalfDev<1>::reader(fa, (unsigned)p.N), (float*)psi, p);
+    moments3_kernel<HalfDev<1>><<<grid, dim3(32, 8), 0, s>>>(HalfDev<1>::reader(fa, N), (float*)psi, nullptr, p);
+  } else if (totals_in) {
+    moments3_kernel<TotalRecol><<<grid, dim3(32, 8), 0, s>>>(TotalRecol::reader(fa, N), (float*)psi, (float*)rho1, p);
+  } else if (totals_out) {
+    moments3_kernel<Plain<1, float>><<<grid, dim3(32, 8), 0, s>>>(Plain<1, float>::reader(fa, N), (float*)psi,
+                                                                  (float*)rho1, p);
   } else {
     const unsigned nb = (unsigned)((p.N + 255) / 256);
-    moments_kernel<1, Plain<1, float>><<<nb, 256, 0, s>>>(Plain<1, float>::reader(fa, (unsigned)p.N), (float*)psi,
-                                                         p);
+    moments_kernel<1, Plain<1, float>><<<nb, 256, 0, s>>>(Plain<1, float>::reader(fa, N), (float*)psi, p);
   }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
@@ -256,10 +267,29 @@ cudaError_t stream3d_step(const void* fa, void* fb, void* psi, void* ng, const H
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   ++*nk;
-  e = h.half ? launch_collide3d<HalfDev<1>>(fa, fb, (const float4*)ng, p, grid, s)
-             : launch_collide3d<Plain<1, float>>(fa, fb, (const float4*)ng, p, grid, s);
+  if (totals_out) {
+    if (totals_in)
+      collide3t_kernel<TotalRecol::Totals, true><<<grid, dim3(32, 8), 0, s>>>(
+          TotalRecol::totals(fa, N), TotalRecol::writer(fb, N), (const float*)rho1, (const float4*)ng, p);
+    else
+      collide3t_kernel<Plain<1, float>::Reader, false><<<grid, dim3(32, 8), 0, s>>>(
+          Plain<1, float>::reader(fa, N), TotalRecol::writer(fb, N), (const float*)rho1, (const float4*)ng, p);
+    e = cudaGetLastError();
+  } else {
+    e = h.half ? launch_collide3d<HalfDev<1>>(fa, fb, (const float4*)ng, p, grid, s)
+               : launch_collide3d<Plain<1, float>>(fa, fb, (const float4*)ng, p, grid, s);
+  }
   if (e == cudaSuccess) ++*nk;
   return e;
 }
+
+cudaError_t stream3d_totals_to_pairs(const void* f, void* out, const HostParams& h, cudaStream_t s) {
+  if (h.N == 0) return cudaSuccess;
+  totals_to_pairs_kernel<<<(unsigned)((h.N + 255) / 256), 256, 0, s>>>(TotalRecol::reader(f, (unsigned)h.N),
+                                                                      (float*)out, h.N);
+  return cudaGetLastError();
+}
+
+size_t stream3d_totals_bytes(size_t N) { return TotalRecol::bytes(N); }
 
 }  // namespace lbnci

@@ -2,7 +2,9 @@
 // storage (arXiv:2003.11069, "Materials and Methods": Eq. (CGLBE), the colour gradient,
 // the near-contact force of Eq. (near_c) and Omega = Omega^(3)[Omega^(1) + Omega^(2)]):
 // the single-read step described first, and, at the end of the file, the streaming step
-// (normals3d_kernel, collide3d_kernel after moments_kernel), the default.
+// (normals3d_kernel, collide3d_kernel after moments_kernel), the default, with the total +
+// recolouring form of the state (TotalRecol, collide3t_kernel) that its FP32 steps under
+// Guo forcing store.
 //
 // Single-read step: every population is read once.
 //
@@ -825,11 +827,14 @@ __global__ void __launch_bounds__(256) normals3d_kernel(const float* __restrict_
 // block's other sites.
 template <typename ST>
 __global__ void __launch_bounds__(256) moments3_kernel(typename ST::Reader f, float* __restrict__ psi,
-                                                       StepT<float> p) {
+                                                       float* __restrict__ rho1, StepT<float> p) {
   const int x = blockIdx.x * 32 + threadIdx.x, y = blockIdx.y * 8 + threadIdx.y, z = blockIdx.z;
+  const int site = x + p.nx * (y + p.ny * z);
   float fin[2][27];
   pull_any<1, float>(f, x, y, z, p, fin);
-  psi[x + p.nx * (y + p.ny * z)] = psi_of<27, float>(fin);
+  float r1, r2;
+  psi[site] = psi_of<27, float>(fin, &r1, &r2);
+  if (rho1) rho1[site] = r1;  // the collision of a state of totals takes rho_1 from here
 }
 
 template <typename ST, bool EDM>
@@ -872,6 +877,194 @@ __global__ void __launch_bounds__(256) collide3d_kernel(typename ST::Reader f, t
   for (int a = 0; a < 3; ++a) u[a] = M<float>::div(j[a] + 0.5f * F[a], rho);
   const float m[3] = {-v.x, -v.y, -v.z};
   collide_store<1, float, typename ST::Writer, EDM>(fin, rho1, rho2, j, u, F, v.w, m, p, fout, site);
+}
+
+// ------------------------------------------------------------------ total + recolouring form
+// With Guo forcing the collision's output at a site is fixed by the total post-collision
+// populations f*_i = f_i^1 + f_i^2 and the recolouring Omega^(3): for a moving direction
+//   f_i^1 = phi_1 f*_i + (w_i/|c_i|) c_i.s,   f_i^2 = f*_i - f_i^1,
+// phi_1 = rho_1/rho, s = beta (rho_1 rho_2/rho) m (the recolouring term written with the
+// vector s instead of the angle to m). TotalRecol keeps a state in that form: plane 0
+// holds f_0^1, planes 1..26 f*_i, plane 27 f_0^2 (planes 0 and 27 are also where the
+// two-population layout keeps the rest populations), then one float4 (phi_1, s) per
+// site: 128 bytes per site instead of 216. The rest populations stay per component,
+// rho_k minus that component's moving populations as a reader recomputes them, so each
+// site's component masses are kept to the rounding of one difference, as in the
+// two-population collision. The exact-difference forcing adds a term per component
+// after the recolouring; its steps keep the two-population form.
+struct TotalRecol {
+  static constexpr int Q = 27;
+  __host__ __device__ static size_t coef_offset(size_t N) { return (28 * N * sizeof(float) + 255) & ~(size_t)255; }
+  static size_t bytes(size_t N) { return coef_offset(N) + N * sizeof(float4); }
+
+  // (w_i/|c_i|) c_i.s of moving direction I, s = (c.y, c.z, c.w), summed over the nonzero
+  // components of c_i in x, y, z order: the collision and every reader evaluate it with
+  // these same operations, so they agree bit for bit.
+  template <int I>
+  __device__ __forceinline__ static float rc(const float4 c) {
+    constexpr int ix = cc(I, 0), iy = cc(I, 1), iz = cc(I, 2);
+    constexpr float wl = float(Lattice<1>::w(I) / (speed2(I) == 1 ? 1.0
+                                                   : (speed2(I) == 2 ? 1.4142135623730951 : 1.7320508075688772)));
+    float r = 0.f;
+    if constexpr (ix == 1) r += c.y; else if constexpr (ix == -1) r -= c.y;
+    if constexpr (iy == 1) r += c.z; else if constexpr (iy == -1) r -= c.z;
+    if constexpr (iz == 1) r += c.w; else if constexpr (iz == -1) r -= c.w;
+    return wl * r;
+  }
+
+  // Both components of direction I at a site (the two-population reader interface).
+  struct Reader {
+    const float* __restrict__ f;
+    const float4* __restrict__ coef;
+    unsigned N;
+    template <int I>
+    __device__ __forceinline__ void get(unsigned site, float& a, float& b) const {
+      if constexpr (I == 0) {
+        a = f[site];
+        b = f[27u * N + site];
+      } else {
+        const float t = f[(unsigned)I * N + site];
+        const float4 c = coef[site];
+        a = fmaf(c.x, t, rc<I>(c));
+        b = t - a;
+      }
+    }
+  };
+  // The totals alone, as pairs (f*_i, 0): the collision needs no split of the pulled
+  // populations (it takes rho_1 from the moments pass).
+  struct Totals {
+    const float* __restrict__ f;
+    unsigned N;
+    template <int I>
+    __device__ __forceinline__ void get(unsigned site, float& a, float& b) const {
+      if constexpr (I == 0) a = f[site] + f[27u * N + site];
+      else a = f[(unsigned)I * N + site];
+      b = 0.f;
+    }
+  };
+  struct Writer {
+    float* __restrict__ f;
+    float4* __restrict__ coef;
+    unsigned N;
+  };
+  __host__ __device__ static Reader reader(const void* base, unsigned N) {
+    return Reader{(const float*)base, (const float4*)((const char*)base + coef_offset(N)), N};
+  }
+  __host__ __device__ static Totals totals(const void* base, unsigned N) { return Totals{(const float*)base, N}; }
+  __host__ __device__ static Writer writer(void* base, unsigned N) {
+    return Writer{(float*)base, (float4*)((char*)base + coef_offset(N)), N};
+  }
+};
+
+// The FP32 operator of collide_store (BGK with the Guo source and the perturbation per
+// pair of opposite directions) on the totals t, stored in the total + recolouring form.
+__device__ __forceinline__ void collide_totals(const float t[27], float rho1, float rho2, float rho, const float u[3],
+                                               const float F[3], float g, const float m[3], const StepT<float>& p,
+                                               const TotalRecol::Writer& fout, unsigned site) {
+  const float uF = u[0] * F[0] + u[1] * F[1] + u[2] * F[2];
+  const float uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+  const float seg = M<float>::div(p.beta * rho1 * rho2, rho);
+  const float pamp = p.pamp * g;
+  const float c1 = M<float>::div(rho1, rho);
+  const float orho = p.omega * rho;
+  const float K0 = orho * (1.f - 1.5f * uu) - 3.f * p.guo * uF - pamp * (1.0f / 3.0f);
+  const float a3 = 3.f * orho, a45 = 4.5f * orho, g3 = 3.f * p.guo, g9 = 9.f * p.guo;
+  const float om1 = 1.f - p.omega;
+  const float4 cf = make_float4(c1, seg * m[0], seg * m[1], seg * m[2]);
+  const unsigned N = fout.N;
+  float s1 = 0.f, s2 = 0.f;
+  static_for<27>([&](auto I) {
+    constexpr int i = decltype(I)::value;
+    constexpr int o = opposite(i);
+    if constexpr (i > 0 && i < o) {
+      constexpr float w = float(Lattice<1>::w(i));
+      constexpr int ix = cc(i, 0), iy = cc(i, 1), iz = cc(i, 2);
+      auto dotc = [&](const float v[3]) {
+        float r = 0.f;
+        if constexpr (ix == 1) r += v[0]; else if constexpr (ix == -1) r -= v[0];
+        if constexpr (iy == 1) r += v[1]; else if constexpr (iy == -1) r -= v[1];
+        if constexpr (iz == 1) r += v[2]; else if constexpr (iz == -1) r -= v[2];
+        return r;
+      };
+      const float cu = dotc(u), cF = dotc(F), cm = dotc(m);
+      const float E = fmaf(pamp, cm * cm, fmaf(g9, cu * cF, fmaf(a45, cu * cu, K0)));
+      const float O = fmaf(g3, cF, a3 * cu);
+      const float fsp = fmaf(w, E + O, om1 * t[i]);
+      const float fsm = fmaf(w, E - O, om1 * t[o]);
+      fout.f[(unsigned)i * N + site] = fsp;
+      fout.f[(unsigned)o * N + site] = fsm;
+      // component 1 of the pair exactly as a reader will recompute it
+      const float ap = fmaf(c1, fsp, TotalRecol::rc<i>(cf));
+      const float am = fmaf(c1, fsm, TotalRecol::rc<o>(cf));
+      s1 += ap + am;
+      s2 += (fsp - ap) + (fsm - am);
+    }
+  });
+  fout.f[site] = rho1 - s1;
+  fout.f[27u * N + site] = rho2 - s2;
+  fout.coef[site] = cf;
+}
+
+// The streaming collision storing the total + recolouring form, from a state in that form
+// (RD = TotalRecol::Totals, TOTALS) or in the two-population layout (RD = Plain reader:
+// the first step after a state was set). rho_1 of the site comes from the moments pass
+// (rho1m), rho from the pulled totals, rho_2 = rho - rho_1. Capped at 64 registers (four
+// blocks per SM; 24 bytes of spills): 395 us per duct step against 441 us at 80 registers
+// and three blocks, the kernel waiting on its loads.
+template <typename RD, bool TOTALS>
+__global__ void __launch_bounds__(256, 4) collide3t_kernel(RD f, TotalRecol::Writer fout,
+                                                           const float* __restrict__ rho1m,
+                                                           const float4* __restrict__ ng, StepT<float> p) {
+  const int x = blockIdx.x * 32 + threadIdx.x, y = blockIdx.y * 8 + threadIdx.y, z = blockIdx.z;
+  const unsigned site = (unsigned)x + (unsigned)p.nx * ((unsigned)y + (unsigned)p.ny * (unsigned)z);
+  float fin[2][27];
+  pull_any<1, float>(f, x, y, z, p, fin);  // the pulls' loads in flight while the ray resolves
+  const float4 v = ng[site];
+  const int h = p.smax > 0 ? nci_ray(ng, v, x, y, z, p) : 0;
+  if constexpr (!TOTALS) {
+#pragma unroll
+    for (int i = 0; i < 27; ++i) fin[0][i] += fin[1][i];
+  }
+  const float* t = fin[0];
+  float rho = 0.f;
+#pragma unroll
+  for (int i = 0; i < 27; ++i) rho += t[i];
+  float j[3] = {0.f, 0.f, 0.f};
+  static_for<27>([&](auto I) {
+    constexpr int i = decltype(I)::value;
+    if constexpr (cc(i, 0) != 0) j[0] += cc(i, 0) > 0 ? t[i] : -t[i];
+    if constexpr (cc(i, 1) != 0) j[1] += cc(i, 1) > 0 ? t[i] : -t[i];
+    if constexpr (cc(i, 2) != 0) j[2] += cc(i, 2) > 0 ? t[i] : -t[i];
+  });
+  const float rho1 = rho1m[site];
+  const float rho2 = rho - rho1;
+  float A = 0.f;  // A_h(h), indexed at compile time
+  static_for<kMaxProbe>([&](auto I) {
+    constexpr int s = decltype(I)::value + 1;
+    if (h == s) A = p.Ah[s];
+  });
+  const float deltaI = 0.5f * v.w;
+  const float F[3] = {p.G[0] - A * v.x * deltaI, p.G[1] - A * v.y * deltaI, p.G[2] - A * v.z * deltaI};
+  float u[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) u[a] = M<float>::div(j[a] + 0.5f * F[a], rho);
+  const float m[3] = {-v.x, -v.y, -v.z};
+  collide_totals(t, rho1, rho2, rho, u, F, v.w, m, p, fout, site);
+}
+
+// A state in the total + recolouring form written out in the two-population layout
+// (into another buffer: the form's coefficient plane overlaps other sites' populations
+// of that layout).
+__global__ void __launch_bounds__(256) totals_to_pairs_kernel(TotalRecol::Reader f, float* __restrict__ out, int N) {
+  const int idx = blockIdx.x * 256 + threadIdx.x;
+  if (idx >= N) return;
+  static_for<27>([&](auto I) {
+    constexpr int i = decltype(I)::value;
+    float a, b;
+    f.template get<i>((unsigned)idx, a, b);
+    out[(size_t)i * N + idx] = a;
+    out[(size_t)(27 + i) * N + idx] = b;
+  });
 }
 
 }  // namespace lbnci

@@ -24,7 +24,7 @@ STATUS = {0: "LB_OK", 1: "LB_EINVAL", 2: "LB_ENOMEM", 3: "LB_ECUDA", 4: "LB_ENUM
 # Every symbol include/lbnci.h declares.
 EXPORTS = ("lb_workspace_size", "lb_create", "lb_init_fields", "lb_step", "lb_observables",
            "lb_fields", "lb_get_populations", "lb_set_populations", "lb_destroy",
-           "lb_last_error", "lb_kernel_launches", "lb_step_path", "lb_observables_noalloc",
+           "lb_last_error", "lb_kernel_launches", "lb_step_path", "lb_state_form", "lb_observables_noalloc",
            "lb_ensemble_create", "lb_ensemble_member", "lb_ensemble_step", "lb_ensemble_tune",
            "lb_ensemble_tune_times", "lb_ensemble_tma_choice", "lb_ensemble_launches",
            "lb_ensemble_last_error", "lb_ensemble_destroy")
@@ -103,6 +103,8 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
     lib.lb_kernel_launches.restype = ctypes.c_longlong
     lib.lb_step_path.argtypes = [simp]
     lib.lb_step_path.restype = ctypes.c_int
+    lib.lb_state_form.argtypes = [simp]
+    lib.lb_state_form.restype = ctypes.c_int
     lib.lb_observables_noalloc.argtypes = [cfgp, vp, ctypes.POINTER(lb_obs)]
     lib.lb_ensemble_create.argtypes = [cfgp, ctypes.c_int, ctypes.POINTER(ctypes.c_void_p)]
     lib.lb_ensemble_member.argtypes = [simp, ctypes.c_int, ctypes.POINTER(ctypes.c_void_p)]
@@ -258,6 +260,13 @@ def lb_step_path(sim) -> int:
     return int(load().lb_step_path(sim))
 
 
+LB_STATE_PAIRS, LB_STATE_TOTAL_RECOLOUR = 0, 1
+
+
+def lb_state_form(sim) -> int:
+    return int(load().lb_state_form(sim))
+
+
 def lb_observables_noalloc(cfg: lb_config, f, allow_numeric=False) -> dict:
     """Observables of device populations f (a CUDA tensor of the storage dtype) with no
     allocation inside the library; see include/lbnci.h for its limits."""
@@ -340,6 +349,9 @@ class Sim:
 
     def step_path(self) -> int:
         return lb_step_path(self.h)
+
+    def state_form(self) -> int:
+        return lb_state_form(self.h)
 
 
 def _echeck(st: int, ens=None) -> int:
