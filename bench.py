@@ -3,11 +3,12 @@
 One "step" is one full lattice Boltzmann time step (stream, moments, gradient, NCI,
 collide, recolour) over the whole lattice. Default workload: the 3D packed emulsion in
 a square duct, D3Q27, 512 x 128 x 128 sites, walls in y and z, periodic in x, FCC-packed
-droplets of radius 10, body force 2e-6, A_h = 0.03, FP32 storage and arithmetic
-(--precision fp16dev: FP16 deviation storage, FP32 arithmetic). Metric: MLUPS (million
-lattice-site updates per second), whole job. The duct's state (3.6 GB for the two
-buffers) is far larger than L2, so K steps are timed back to back with CUDA events on
-the library's stream. Lattices that fit in L2 (the 2048 x 256 channel) are flushed
+droplets of radius 10, body force 2e-6, A_h = 0.03, FP16-deviation storage and FP32
+arithmetic (--precision fp32: FP32 storage), with the same duct in FP32 storage timed
+beside it (fp32_compare: the total + recolouring form and the two-population layout).
+Metric: MLUPS (million lattice-site updates per second), whole job. The duct's state
+(1.9 GB for the two FP16-dev buffers, 3.6 GB in FP32) is far larger than L2, so K steps
+are timed back to back with CUDA events on the library's stream. Lattices that fit in L2 (the 2048 x 256 channel) are flushed
 before every timed step (a 512 MB write, then a 256 MB read so that the write's dirty
 lines go back to memory before, not during, the step) and each step is timed alone.
 
@@ -103,20 +104,21 @@ STEP_KERNELS = {0: "fused2d_kernel (one-pass D2Q9 step)",
                 4: "moments_kernel + normals3d_kernel + collide3d_kernel (D3Q27 streaming step: psi, per-site "
                    "normals, then the NCI ray, pull, collision and store without shared memory; three launches)"}
 STATE_FORMS = {0: "pairs: the populations of both components",
-               1: "total + recolouring: the total populations f*_i of the 26 moving directions, the rest "
-                  "population of each component and (rho_1/rho, beta rho_1 rho_2/rho m) per site, 128 B "
-                  "(two-population FP32: 216 B); the moments pass is moments3_kernel<TotalRecol> and the "
-                  "collision collide3t_kernel"}
+               1: "total + recolouring: the total populations f*_i of the 26 moving directions (FP32, or FP16 "
+                  "deviations from w_i rho_0), the rest population of each component and (rho_1/rho, beta "
+                  "rho_1 rho_2/rho m) per site: FP32 128 B (pairs 216 B), FP16-dev 76 B (pairs 116 B); the "
+                  "moments pass is moments3_kernel<TotalRecol/TotalRecolHalf> and the collision collide3t_kernel"}
 
 
 # Bytes of state moved per site update (1 read + 1 write): FP64/FP32 populations are
 # 2 components x Q values; FP16-dev stores Q half2 deviations plus a float2 of
-# reference densities per site; the total + recolouring form (state form 1, FP32 D3Q27)
-# 26 total populations, 2 rest populations and a float4 of coefficients.
+# reference densities per site; the total + recolouring form (state form 1, D3Q27) Q - 1
+# total populations (FP32, or FP16 deviations), 2 FP32 rest populations and a float4 of
+# coefficients.
 def alg_bytes_per_site(lattice: int, precision: str, form: int = 0) -> int:
     Q = 9 if lattice == 0 else 27
     if form == 1:
-        return 2 * ((Q + 1) * 4 + 16)
+        return 2 * ((Q - 1) * (2 if precision == "fp16dev" else 4) + 8 + 16)
     per_site = {"fp64": 2 * Q * 8, "fp32": 2 * Q * 4, "fp16dev": Q * 4 + 8}[precision]
     return 2 * per_site
 
@@ -460,6 +462,38 @@ def flow_study(ens, members, study_steps, obs):
             "diverged": int((~finite).sum()), "fit": fit}
 
 
+def time_other_storage(lbnci, torch, w, prec, rho1, rho2, steps, warmup, env):
+    """ms per step of `steps` back-to-back steps of workload w in another storage (a fresh
+    sim; `env` is set while it is created, which is when the library reads it)."""
+    old = {k: os.environ.get(k) for k in env}
+    os.environ.update(env)
+    try:
+        stream = torch.cuda.Stream()
+        cfg = lbnci.lb_config_make(lattice=w["lattice"], nx=w["nx"], ny=w["ny"], nz=w["nz"], wall_y=w["wall_y"],
+                                   wall_z=w["wall_z"], tau=w["tau"], A_s=w["A_s"], beta=w["beta"], A_h=w["A_h"],
+                                   force=w["force"], precision=prec, stream=stream.cuda_stream)
+        sim = lbnci.Sim(cfg, workspace="torch")
+    finally:
+        for k, v in old.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
+    form = sim.state_form()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(stream):
+        sim.init_fields(rho1, rho2)
+        sim.step(warmup)
+        stream.synchronize()
+        e0.record(stream)
+        sim.step(steps)
+        e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    sim.close()
+    return ms, form
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -467,7 +501,9 @@ def main(argv=None):
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="duct3d", choices=sorted(WORKLOADS))
-    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64", "fp16dev"])
+    ap.add_argument("--precision", default="fp16dev", choices=["fp32", "fp64", "fp16dev"])
+    ap.add_argument("--no-fp32-compare", action="store_true",
+                    help="duct with FP16-dev storage: skip timing the FP32 storages on the same workload")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=12.0)
@@ -561,6 +597,19 @@ def main(argv=None):
     ms_per_step = total_ms / args.steps
     value = whole_job_mlups(N, args.steps, ws, total_ms * 1e-3)
 
+    # FP16-deviation storage against FP32 storage on the same duct: fresh sims, the same
+    # generated fields, K steps back to back (rank 0's figures; every rank runs its own)
+    fp32_compare = None
+    if big and args.precision == "fp16dev" and w["lattice"] == 1 and not args.no_fp32_compare:
+        fp32_compare = {}
+        for name, env in (("fp32", {}), ("fp32_pairs", {"LBNCI_D3_STATE": "pairs"})):
+            ms, form_v = time_other_storage(lbnci, torch, w, lbnci.LB_FP32, rho1, rho2, args.steps, args.warmup, env)
+            fp32_compare[name] = {"ms_per_step": round(ms, 5), "value": round(N / (ms * 1e-3) / 1e6, 2),
+                                  "state_form": STATE_FORMS.get(form_v, "?").split(":")[0],
+                                  "alg_bytes_per_site": alg_bytes_per_site(1, "fp32", form_v)}
+            fp32_compare[f"speedup_vs_{name}"] = round(ms / ms_per_step, 3)
+        fp32_compare["env"] = "fp32_pairs: LBNCI_D3_STATE=pairs"
+
     # end to end through the public API with host buffers
     e2e = None
     if not args.no_e2e:
@@ -628,6 +677,12 @@ def main(argv=None):
         "clocks": clocks,
         "observables": {"n_nci": obs["n_nci"], "n_interface": obs["n_interface"], "n_bad": obs["n_bad"]},
     }
+    if form == 1:  # the fraction at the two-population storage's bytes, for comparison
+        b2 = alg_bytes_per_site(w["lattice"], args.precision, 0)
+        line["roofline"]["two_population_equivalent"] = {
+            "alg_bytes_per_site": b2, "frac": round(b2 * N / (ms_per_step * 1e-3) / 1e9 / peak, 4)}
+    if fp32_compare is not None:
+        line["fp32_compare"] = fp32_compare
     print(json.dumps(line), flush=True)
     return 0
 

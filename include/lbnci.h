@@ -205,17 +205,20 @@ int lb_step_path(const lb_sim* sim);
  * call sees the populations of both components whatever the form):
  *   LB_STATE_PAIRS          the populations f_i^1, f_i^2 of both components, in the
  *                           storage the precision names,
- *   LB_STATE_TOTAL_RECOLOUR FP32 streaming D3Q27 steps with Guo forcing (unless
- *                           LBNCI_D3_STATE=pairs is set in the environment): the total
- *                           post-collision populations f*_i = f_i^1 + f_i^2 of the 26
- *                           moving directions, the rest population of each component and,
- *                           per site, phi_1 = rho_1/rho and s = beta (rho_1 rho_2/rho) m,
- *                           from which the recolouring ("Materials and Methods",
- *                           Omega^(3)) gives f_i^1 = phi_1 f*_i + (w_i/|c_i|) c_i.s and
- *                           f_i^2 = f*_i - f_i^1: 128 instead of 216 bytes per site. A call
- *                           that reads the state (lb_fields, lb_observables,
- *                           lb_get_populations) first rewrites it as pairs, one extra
- *                           kernel launch.
+ *   LB_STATE_TOTAL_RECOLOUR streaming D3Q27 steps with Guo forcing (FP32 and FP16-dev,
+ *                           unless LBNCI_D3_STATE=pairs is set in the environment when the
+ *                           sim is created): the total post-collision populations
+ *                           f*_i = f_i^1 + f_i^2 of the 26 moving directions, the rest
+ *                           population of each component and, per site, phi_1 = rho_1/rho
+ *                           and s = beta (rho_1 rho_2/rho) m, from which the recolouring
+ *                           ("Materials and Methods", Omega^(3)) gives
+ *                           f_i^1 = phi_1 f*_i + (w_i/|c_i|) c_i.s and f_i^2 = f*_i - f_i^1.
+ *                           FP32 keeps f*_i in FP32 (128 instead of 216 bytes per site);
+ *                           FP16-dev keeps f*_i - w_i rho_0 in FP16, rho_0 the mean total
+ *                           density of the state as lb_init_fields or lb_set_populations set
+ *                           it (76 instead of 116 bytes per site; those two calls then run
+ *                           one fields pass for rho_0 and synchronise the sim's stream).
+ *                           The first step after a state is set reads it as pairs.
  * Returns -1 for a NULL sim. */
 enum { LB_STATE_PAIRS = 0, LB_STATE_TOTAL_RECOLOUR = 1 };
 int lb_state_form(const lb_sim* sim);

@@ -192,11 +192,13 @@ lb_status validate(const lb_config* c, HostParams* p, Layout* lay, long long* nb
     if (std::strcmp(e, "march") == 0 || std::strcmp(e, "tiled") == 0) p->stream3d = 0;
     if (std::strcmp(e, "carry") == 0 && col_ok) { p->carry3d = 1; p->stream3d = 0; }
   }
-  // FP32 streaming steps with Guo forcing store the total + recolouring form (128 instead
-  // of 216 bytes per site), unless LBNCI_D3_STATE=pairs keeps the two-population layout
-  p->totals = p->stream3d && c->precision == LB_FP32 && c->forcing == 0 ? 1 : 0;
+  // streaming steps with Guo forcing store the total + recolouring form (FP32: 128 instead
+  // of 216 bytes per site; FP16-dev: 76 instead of 116), unless LBNCI_D3_STATE=pairs keeps
+  // the two-population layout
+  p->totals = p->stream3d && c->forcing == 0 ? 1 : 0;
   if (const char* e = std::getenv("LBNCI_D3_STATE"))
     if (std::strcmp(e, "pairs") == 0) p->totals = 0;
+  p->rho_ref = 1.0f;
   // z segment of the single-read collision kernel (planes; LBNCI_C3_ZSEG, default 16)
   p->c3_zseg = 16;
   if (const char* e = std::getenv("LBNCI_C3_ZSEG")) p->c3_zseg = std::atoi(e) > 0 ? std::atoi(e) : 16;
@@ -204,7 +206,7 @@ lb_status validate(const lb_config* c, HostParams* p, Layout* lay, long long* nb
   (void)Q;
   const Launchers* L = launchers_for(c);
   const size_t state = L->state_bytes((size_t)N);
-  if (p->totals && stream3d_totals_bytes((size_t)N) > state) p->totals = 0;  // the form lives in a state buffer
+  if (p->totals && stream3d_totals_bytes((size_t)N, p->half) > state) p->totals = 0;  // the form lives in a state buffer
   *nblocks = tiled_blocks(c->lattice, *p);
   size_t off = 0;
   lay->fa = off; off = align256(off + state);
@@ -238,28 +240,14 @@ long long staging_chunk(const lb_sim* s) {
   return fit >= s->p.N ? s->p.N : fit;
 }
 
-// A state in the total + recolouring form rewritten in the two-population layout that
-// the fields kernel and the population copies read: into the back buffer, which then
-// becomes the state (the same populations; the next step reads this layout).
-lb_status ensure_pairs(lb_sim* s) {
-  if (!s->totals_state) return LB_OK;
-  cudaError_t e = stream3d_totals_to_pairs(s->fa, s->fb, s->p, s->stream);
-  ++s->launches;
-  if (e != cudaSuccess) return cuda_fail(s, e, "state conversion");
-  std::swap(s->fa, s->fb);
-  s->totals_state = false;
-  return LB_OK;
-}
-
 // Run the fields kernel on the current state with the given device outputs and
 // fill s->host_result with the reduced observables (synchronises the stream).
 lb_status run_fields(lb_sim* s, const FieldOut& outs) {
-  lb_status ps = ensure_pairs(s);
-  if (ps != LB_OK) return ps;
   FieldOut fo = outs;
   fo.partials = s->partials;
   int nk = 0;
-  cudaError_t e = s->L->fields(s->fa, s->psi, s->p, fo, s->stream, &nk);
+  cudaError_t e = s->totals_state ? stream3d_form_fields(s->fa, s->psi, s->p, fo, s->stream, &nk)
+                                  : s->L->fields(s->fa, s->psi, s->p, fo, s->stream, &nk);
   s->launches += nk + 1;
   if (e != cudaSuccess) return cuda_fail(s, e, "fields launch");
   e = reduce_partials(s->partials, s->nblocks, s->result, s->stream);
@@ -280,6 +268,17 @@ lb_status run_fields(lb_sim* s, const FieldOut& outs) {
     return fail(s, LB_ECUDA, "%s (flag %d); the state is invalid",
                 (flag & 1) ? "a step kernel gave up waiting for its TMA copies"
                            : "a step kernel found its shared memory misaligned for TMA and did nothing", flag);
+  return LB_OK;
+}
+
+// The reference density rho_0 of the FP16 total + recolouring form: the mean total
+// density of a state just set (a fields pass and its reduction; synchronises the stream).
+lb_status refresh_rho_ref(lb_sim* s) {
+  if (!(s->p.stream3d && s->p.totals && s->p.half)) return LB_OK;
+  lb_status st = run_fields(s, FieldOut{});
+  if (st != LB_OK) return st;
+  const double r = (s->host_result[0] + s->host_result[1]) / (double)s->p.N;
+  s->p.rho_ref = std::isfinite(r) && r > 0.0 ? (float)r : 1.0f;
   return LB_OK;
 }
 
@@ -425,7 +424,7 @@ lb_status lb_init_fields(lb_sim* s, const double* rho1, const double* rho2, cons
     if (e != cudaSuccess) return cuda_fail(s, e, "stream synchronize");
   }
   s->step = 0;
-  return LB_OK;
+  return refresh_rho_ref(s);
 }
 
 lb_status lb_step(lb_sim* s, long long nsteps) {
@@ -530,11 +529,14 @@ lb_status lb_get_populations(lb_sim* s, double* f, int on_device) {
   if (!s) return fail(nullptr, LB_EINVAL, "sim is NULL");
   if (!f) return fail(s, LB_EINVAL, "f is NULL");
   const int N = s->p.N, Q2 = 2 * s->Q;
-  lb_status ps = ensure_pairs(s);
-  if (ps != LB_OK) return ps;
+  // a state in the total + recolouring form is read through the form's own reader
+  auto decode = [&](double* out, int s0, int cnt) {
+    return s->totals_state ? stream3d_form_decode(s->fa, out, s0, cnt, cnt, s->p, s->stream)
+                           : s->L->decode(s->fa, out, s0, cnt, cnt, N, s->stream);
+  };
   cudaError_t e;
   if (on_device) {
-    e = s->L->decode(s->fa, f, 0, N, N, N, s->stream);
+    e = decode(f, 0, N);
     ++s->launches;
     if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
     return e == cudaSuccess ? LB_OK : cuda_fail(s, e, "population decode");
@@ -544,7 +546,7 @@ lb_status lb_get_populations(lb_sim* s, double* f, int on_device) {
   if (chunk < 1) return fail(s, LB_EUNSUPPORTED, "staging too small");
   for (long long s0 = 0; s0 < N; s0 += chunk) {
     const int cnt = (int)(N - s0 < chunk ? N - s0 : chunk);
-    e = s->L->decode(s->fa, (double*)s->fb, (int)s0, cnt, cnt, N, s->stream);
+    e = decode((double*)s->fb, (int)s0, cnt);
     ++s->launches;
     if (e != cudaSuccess) return cuda_fail(s, e, "population download (decode launch)");
     for (int q = 0; q < Q2 && e == cudaSuccess; ++q)
@@ -589,7 +591,7 @@ lb_status lb_set_populations(lb_sim* s, const double* f, int on_device) {
     }
   }
   s->step = 0;
-  return LB_OK;
+  return refresh_rho_ref(s);
 }
 
 void lb_destroy(lb_sim* s) {

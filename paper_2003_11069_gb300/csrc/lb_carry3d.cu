@@ -233,7 +233,17 @@ cudaError_t launch_collide3d(const void* fa, void* fb, const float4* ng, const S
 
 bool stream3d_supported(const HostParams& h) { return h.nx % 32 == 0 && h.ny % 8 == 0; }
 
-bool stream3d_stores_totals(const HostParams& h) { return h.totals && !h.half && h.forcing != 1; }
+bool stream3d_stores_totals(const HostParams& h) { return h.totals && h.forcing != 1; }
+
+namespace {
+// the collision storing the total + recolouring form of the precision
+template <typename RD, bool TOTALS, typename WR>
+cudaError_t launch_collide3t(RD rd, WR wr, const void* rho1, const void* ng, const StepT<float>& p, dim3 grid,
+                             cudaStream_t s) {
+  collide3t_kernel<RD, TOTALS, WR><<<grid, dim3(32, 8), 0, s>>>(rd, wr, (const float*)rho1, (const float4*)ng, p);
+  return cudaGetLastError();
+}
+}  // namespace
 
 cudaError_t stream3d_step(const void* fa, void* fb, void* psi, void* ng, void* rho1, int totals_in,
                           const HostParams& h, cudaStream_t s, int* nk) {
@@ -243,18 +253,23 @@ cudaError_t stream3d_step(const void* fa, void* fb, void* psi, void* ng, void* r
   if (totals_in && !totals_out) return cudaErrorInvalidValue;  // no step reads that form into pairs
   const dim3 grid((unsigned)(h.nx / 32), (unsigned)(h.ny / 8), (unsigned)h.nz);
   const unsigned N = (unsigned)p.N;
+  const float rho0 = h.rho_ref;
+  float* r1 = totals_out ? (float*)rho1 : nullptr;
   // 32 x 8 blocks where the sources carry per-site data that repeats within the block
-  // (FP16-dev: the reference densities, 0.85 ms per duct step against 0.95 ms with blocks
-  // of 256 consecutive sites; the total form: the recolouring coefficients, about two
-  // thirds of whose sectors hit L1); the two-population FP32 state has none and keeps the
-  // flat kernel (the same time)
-  if (h.half) {
-    moments3_kernel<HalfDev<1>><<<grid, dim3(32, 8), 0, s>>>(HalfDev<1>::reader(fa, N), (float*)psi, nullptr, p);
+  // (FP16-dev pairs: the reference densities, 0.85 ms per duct step against 0.95 ms with
+  // blocks of 256 consecutive sites; the total forms: the recolouring coefficients, about
+  // two thirds of whose sectors hit L1); the two-population FP32 state has none and keeps
+  // the flat kernel (the same time)
+  if (totals_in && h.half) {
+    moments3_kernel<TotalRecolHalf><<<grid, dim3(32, 8), 0, s>>>(TotalRecolHalf::reader(fa, N, rho0), (float*)psi,
+                                                                 r1, p);
   } else if (totals_in) {
-    moments3_kernel<TotalRecol><<<grid, dim3(32, 8), 0, s>>>(TotalRecol::reader(fa, N), (float*)psi, (float*)rho1, p);
+    moments3_kernel<TotalRecol><<<grid, dim3(32, 8), 0, s>>>(TotalRecol::reader(fa, N), (float*)psi, r1, p);
+  } else if (h.half) {
+    moments3_kernel<HalfDev<1>><<<grid, dim3(32, 8), 0, s>>>(HalfDev<1>::reader(fa, N), (float*)psi, r1, p);
   } else if (totals_out) {
-    moments3_kernel<Plain<1, float>><<<grid, dim3(32, 8), 0, s>>>(Plain<1, float>::reader(fa, N), (float*)psi,
-                                                                  (float*)rho1, p);
+    moments3_kernel<Plain<1, float>><<<grid, dim3(32, 8), 0, s>>>(Plain<1, float>::reader(fa, N), (float*)psi, r1,
+                                                                  p);
   } else {
     const unsigned nb = (unsigned)((p.N + 255) / 256);
     moments_kernel<1, Plain<1, float>><<<nb, 256, 0, s>>>(Plain<1, float>::reader(fa, N), (float*)psi, p);
@@ -267,14 +282,16 @@ cudaError_t stream3d_step(const void* fa, void* fb, void* psi, void* ng, void* r
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   ++*nk;
-  if (totals_out) {
-    if (totals_in)
-      collide3t_kernel<TotalRecol::Totals, true><<<grid, dim3(32, 8), 0, s>>>(
-          TotalRecol::totals(fa, N), TotalRecol::writer(fb, N), (const float*)rho1, (const float4*)ng, p);
-    else
-      collide3t_kernel<Plain<1, float>::Reader, false><<<grid, dim3(32, 8), 0, s>>>(
-          Plain<1, float>::reader(fa, N), TotalRecol::writer(fb, N), (const float*)rho1, (const float4*)ng, p);
-    e = cudaGetLastError();
+  if (totals_out && h.half) {
+    const TotalRecolHalf::Writer wr = TotalRecolHalf::writer(fb, N, rho0);
+    e = totals_in ? launch_collide3t<TotalRecolHalf::Totals, true>(TotalRecolHalf::totals(fa, N, rho0), wr, rho1, ng,
+                                                                   p, grid, s)
+                  : launch_collide3t<HalfDev<1>::Reader, false>(HalfDev<1>::reader(fa, N), wr, rho1, ng, p, grid, s);
+  } else if (totals_out) {
+    const TotalRecol::Writer wr = TotalRecol::writer(fb, N);
+    e = totals_in ? launch_collide3t<TotalRecol::Totals, true>(TotalRecol::totals(fa, N), wr, rho1, ng, p, grid, s)
+                  : launch_collide3t<Plain<1, float>::Reader, false>(Plain<1, float>::reader(fa, N), wr, rho1, ng, p,
+                                                                      grid, s);
   } else {
     e = h.half ? launch_collide3d<HalfDev<1>>(fa, fb, (const float4*)ng, p, grid, s)
                : launch_collide3d<Plain<1, float>>(fa, fb, (const float4*)ng, p, grid, s);
@@ -283,13 +300,48 @@ cudaError_t stream3d_step(const void* fa, void* fb, void* psi, void* ng, void* r
   return e;
 }
 
-cudaError_t stream3d_totals_to_pairs(const void* f, void* out, const HostParams& h, cudaStream_t s) {
-  if (h.N == 0) return cudaSuccess;
-  totals_to_pairs_kernel<<<(unsigned)((h.N + 255) / 256), 256, 0, s>>>(TotalRecol::reader(f, (unsigned)h.N),
-                                                                      (float*)out, h.N);
+namespace {
+// The fields kernel (and its moments pass) on a state in a total + recolouring form, read
+// through the form's two-population reader; the same grid as the other precisions' fields
+// launches (tiled_blocks), so the host reduces the same partials.
+template <typename FORM>
+cudaError_t form_fields(typename FORM::Reader rd, void* psi, const HostParams& h, const FieldOut& fo, cudaStream_t s,
+                        int* nk) {
+  const StepT<float> p = to_step3(h);
+  moments_kernel<1, FORM><<<(unsigned)((p.N + 255) / 256), 256, 0, s>>>(rd, (float*)psi, p);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  static SmemAllowance configured;
+  const size_t sm = tiled_smem_bytes<1, float>(p.smax);
+  e = allow_smem(tiled_kernel<1, FORM, true, false>, sm, configured);
+  if (e != cudaSuccess) return e;
+  const dim3 grid((unsigned)((h.nx + Tile<1>::X - 1) / Tile<1>::X), (unsigned)((h.ny + Tile<1>::Y - 1) / Tile<1>::Y),
+                  (unsigned)((h.nz + Tile<1>::Z - 1) / Tile<1>::Z));
+  tiled_kernel<1, FORM, true, false><<<grid, dim3(Tile<1>::X, Tile<1>::Y, Tile<1>::Z), sm, s>>>(
+      rd, typename FORM::Writer{}, (const float*)psi, p, fo);
+  *nk = 2;
+  return cudaGetLastError();
+}
+}  // namespace
+
+cudaError_t stream3d_form_fields(const void* f, void* psi, const HostParams& h, const FieldOut& fo, cudaStream_t s,
+                                 int* nk) {
+  if (h.half) return form_fields<TotalRecolHalf>(TotalRecolHalf::reader(f, (unsigned)h.N, h.rho_ref), psi, h, fo, s, nk);
+  return form_fields<TotalRecol>(TotalRecol::reader(f, (unsigned)h.N), psi, h, fo, s, nk);
+}
+
+cudaError_t stream3d_form_decode(const void* f, double* out, int s0, int count, long long pitch, const HostParams& h,
+                                 cudaStream_t s) {
+  if (count <= 0) return cudaSuccess;
+  const unsigned nb = (unsigned)((count + 255) / 256);
+  if (h.half)
+    decode_kernel<1, TotalRecolHalf><<<nb, 256, 0, s>>>(TotalRecolHalf::reader(f, (unsigned)h.N, h.rho_ref), out, s0,
+                                                        count, pitch);
+  else
+    decode_kernel<1, TotalRecol><<<nb, 256, 0, s>>>(TotalRecol::reader(f, (unsigned)h.N), out, s0, count, pitch);
   return cudaGetLastError();
 }
 
-size_t stream3d_totals_bytes(size_t N) { return TotalRecol::bytes(N); }
+size_t stream3d_totals_bytes(size_t N, int half) { return half ? TotalRecolHalf::bytes(N) : TotalRecol::bytes(N); }
 
 }  // namespace lbnci

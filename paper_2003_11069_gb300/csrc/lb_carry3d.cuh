@@ -884,35 +884,60 @@ __global__ void __launch_bounds__(256) collide3d_kernel(typename ST::Reader f, t
 // populations f*_i = f_i^1 + f_i^2 and the recolouring Omega^(3): for a moving direction
 //   f_i^1 = phi_1 f*_i + (w_i/|c_i|) c_i.s,   f_i^2 = f*_i - f_i^1,
 // phi_1 = rho_1/rho, s = beta (rho_1 rho_2/rho) m (the recolouring term written with the
-// vector s instead of the angle to m). TotalRecol keeps a state in that form: plane 0
-// holds f_0^1, planes 1..26 f*_i, plane 27 f_0^2 (planes 0 and 27 are also where the
-// two-population layout keeps the rest populations), then one float4 (phi_1, s) per
-// site: 128 bytes per site instead of 216. The rest populations stay per component,
-// rho_k minus that component's moving populations as a reader recomputes them, so each
-// site's component masses are kept to the rounding of one difference, as in the
-// two-population collision. The exact-difference forcing adds a term per component
-// after the recolouring; its steps keep the two-population form.
+// vector s instead of the angle to m). A state in this form holds the 26 moving totals, the
+// rest population of each component and one float4 (phi_1, s) per site. The rest
+// populations stay per component, rho_k minus that component's moving populations as a
+// reader recomputes them from the stored totals, so each site's component masses are kept
+// to the rounding of one difference, as in the two-population collision. The
+// exact-difference forcing adds a term per component after the recolouring; its steps keep
+// the two-population form.
+//
+//   TotalRecol      FP32 totals: plane 0 f_0^1, planes 1..26 f*_i, plane 27 f_0^2 (planes
+//                   0 and 27 are also where the two-population layout keeps the rest
+//                   populations), then the coefficient plane: 128 bytes per site.
+//   TotalRecolHalf  FP16 totals, as deviations from the lattice-weight equilibrium of one
+//                   reference density rho_0 of the sim (f*_i = w_i rho_0 + d_i; the total
+//                   density of the model's two fluids stays close to its mean, so d_i is of
+//                   the order of w_i (|rho - rho_0| + 3 |c_i.u|)): 26 half planes, then the
+//                   two FP32 rest planes and the coefficient plane: 76 bytes per site. A
+//                   step rounds d_i stochastically (half2_stochastic, the site's dither
+//                   bits); the rest populations and the split use the rounded totals.
+//
+// Both offer the two-population reader interface (get<I>: both components of direction I),
+// through which the moments pass, the fields kernel and population copies read them, and
+// Totals (get<I>: the total alone) for the collision, which needs no split.
+
+// (w_i/|c_i|) c_i.s of moving direction I, s = (c.y, c.z, c.w), summed over the nonzero
+// components of c_i in x, y, z order for I < opposite(I), and exactly the negative of its
+// opposite's for the others: the collision and every reader evaluate it with these same
+// operations, so they agree bit for bit, and a pair of opposite directions costs one.
+template <int I>
+__device__ __forceinline__ float recolour_term(const float4 c) {
+  if constexpr (I > opposite(I)) return -recolour_term<opposite(I)>(c);
+  constexpr int ix = cc(I, 0), iy = cc(I, 1), iz = cc(I, 2);
+  constexpr float wl = float(Lattice<1>::w(I) / (speed2(I) == 1 ? 1.0
+                                                 : (speed2(I) == 2 ? 1.4142135623730951 : 1.7320508075688772)));
+  float r = 0.f;
+  if constexpr (ix == 1) r += c.y; else if constexpr (ix == -1) r -= c.y;
+  if constexpr (iy == 1) r += c.z; else if constexpr (iy == -1) r -= c.z;
+  if constexpr (iz == 1) r += c.w; else if constexpr (iz == -1) r -= c.w;
+  return wl * r;
+}
+
+// Component 1 and 2 of a moving direction from its total t and the coefficients c.
+template <int I>
+__device__ __forceinline__ void split_total(float t, const float4 c, float& a, float& b) {
+  a = fmaf(c.x, t, recolour_term<I>(c));
+  b = t - a;
+}
+
 struct TotalRecol {
+  using Compute = float;
   static constexpr int Q = 27;
+  static constexpr bool kHalf = false;
   __host__ __device__ static size_t coef_offset(size_t N) { return (28 * N * sizeof(float) + 255) & ~(size_t)255; }
   static size_t bytes(size_t N) { return coef_offset(N) + N * sizeof(float4); }
 
-  // (w_i/|c_i|) c_i.s of moving direction I, s = (c.y, c.z, c.w), summed over the nonzero
-  // components of c_i in x, y, z order: the collision and every reader evaluate it with
-  // these same operations, so they agree bit for bit.
-  template <int I>
-  __device__ __forceinline__ static float rc(const float4 c) {
-    constexpr int ix = cc(I, 0), iy = cc(I, 1), iz = cc(I, 2);
-    constexpr float wl = float(Lattice<1>::w(I) / (speed2(I) == 1 ? 1.0
-                                                   : (speed2(I) == 2 ? 1.4142135623730951 : 1.7320508075688772)));
-    float r = 0.f;
-    if constexpr (ix == 1) r += c.y; else if constexpr (ix == -1) r -= c.y;
-    if constexpr (iy == 1) r += c.z; else if constexpr (iy == -1) r -= c.z;
-    if constexpr (iz == 1) r += c.w; else if constexpr (iz == -1) r -= c.w;
-    return wl * r;
-  }
-
-  // Both components of direction I at a site (the two-population reader interface).
   struct Reader {
     const float* __restrict__ f;
     const float4* __restrict__ coef;
@@ -923,15 +948,10 @@ struct TotalRecol {
         a = f[site];
         b = f[27u * N + site];
       } else {
-        const float t = f[(unsigned)I * N + site];
-        const float4 c = coef[site];
-        a = fmaf(c.x, t, rc<I>(c));
-        b = t - a;
+        split_total<I>(f[(unsigned)I * N + site], coef[site], a, b);
       }
     }
   };
-  // The totals alone, as pairs (f*_i, 0): the collision needs no split of the pulled
-  // populations (it takes rho_1 from the moments pass).
   struct Totals {
     const float* __restrict__ f;
     unsigned N;
@@ -946,21 +966,125 @@ struct TotalRecol {
     float* __restrict__ f;
     float4* __restrict__ coef;
     unsigned N;
+    unsigned seed;  // unused by this form
+    __device__ __forceinline__ unsigned site_bits(unsigned) const { return 0u; }
+    // the totals of directions I and its opposite O; (tp, tm) = the stored values
+    template <int I, int O>
+    __device__ __forceinline__ void put_pair(unsigned site, float fp, float fm, unsigned, float& tp, float& tm) const {
+      f[(unsigned)I * N + site] = fp;
+      f[(unsigned)O * N + site] = fm;
+      tp = fp;
+      tm = fm;
+    }
+    __device__ __forceinline__ void put_rest(unsigned site, float r1, float r2, float4 c) const {
+      f[site] = r1;
+      f[27u * N + site] = r2;
+      coef[site] = c;
+    }
   };
-  __host__ __device__ static Reader reader(const void* base, unsigned N) {
+  __host__ __device__ static Reader reader(const void* base, unsigned N, float = 0.f) {
     return Reader{(const float*)base, (const float4*)((const char*)base + coef_offset(N)), N};
   }
-  __host__ __device__ static Totals totals(const void* base, unsigned N) { return Totals{(const float*)base, N}; }
-  __host__ __device__ static Writer writer(void* base, unsigned N) {
-    return Writer{(float*)base, (float4*)((char*)base + coef_offset(N)), N};
+  __host__ __device__ static Totals totals(const void* base, unsigned N, float = 0.f) {
+    return Totals{(const float*)base, N};
+  }
+  __host__ __device__ static Writer writer(void* base, unsigned N, float = 0.f) {
+    return Writer{(float*)base, (float4*)((char*)base + coef_offset(N)), N, 0u};
+  }
+};
+
+struct TotalRecolHalf {
+  using Compute = float;
+  static constexpr int Q = 27;
+  static constexpr bool kHalf = true;
+  __host__ __device__ static size_t rest_offset(size_t N) { return (26 * N * sizeof(__half) + 255) & ~(size_t)255; }
+  __host__ __device__ static size_t coef_offset(size_t N) {
+    return (rest_offset(N) + 2 * N * sizeof(float) + 255) & ~(size_t)255;
+  }
+  static size_t bytes(size_t N) { return coef_offset(N) + N * sizeof(float4); }
+
+  // f*_i = w_i rho_0 + d_i, one expression for every reader and the writer
+  template <int I>
+  __device__ __forceinline__ static float total(const __half* d, unsigned N, unsigned site, float rho0) {
+    return fmaf(float(Lattice<1>::w(I)), rho0, __half2float(d[(unsigned)(I - 1) * N + site]));
+  }
+
+  struct Reader {
+    const __half* __restrict__ d;
+    const float* __restrict__ r;
+    const float4* __restrict__ coef;
+    unsigned N;
+    float rho0;
+    template <int I>
+    __device__ __forceinline__ void get(unsigned site, float& a, float& b) const {
+      if constexpr (I == 0) {
+        a = r[site];
+        b = r[N + site];
+      } else {
+        split_total<I>(total<I>(d, N, site, rho0), coef[site], a, b);
+      }
+    }
+  };
+  struct Totals {
+    const __half* __restrict__ d;
+    const float* __restrict__ r;
+    unsigned N;
+    float rho0;
+    template <int I>
+    __device__ __forceinline__ void get(unsigned site, float& a, float& b) const {
+      if constexpr (I == 0) a = r[site] + r[N + site];
+      else a = total<I>(d, N, site, rho0);
+      b = 0.f;
+    }
+  };
+  struct Writer {
+    __half* __restrict__ d;
+    float* __restrict__ r;
+    float4* __restrict__ coef;
+    unsigned N;
+    float rho0;
+    unsigned seed;  // this step's dither seed (step_seed)
+    __device__ __forceinline__ unsigned site_bits(unsigned site) const { return dither_bits(site, seed); }
+    // d_I and d_O rounded stochastically as one half2 (I low, O high) with the site's bits h;
+    // (tp, tm) = the totals a reader will see
+    template <int I, int O>
+    __device__ __forceinline__ void put_pair(unsigned site, float fp, float fm, unsigned h, float& tp,
+                                             float& tm) const {
+      constexpr float w = float(Lattice<1>::w(I));
+      const unsigned v = half2_stochastic<I>(fmaf(-w, rho0, fp), fmaf(-w, rho0, fm), h);
+      const unsigned short lo = (unsigned short)(v & 0xFFFFu), hi = (unsigned short)(v >> 16);
+      unsigned short* du = reinterpret_cast<unsigned short*>(d);
+      du[(unsigned)(I - 1) * N + site] = lo;
+      du[(unsigned)(O - 1) * N + site] = hi;
+      tp = fmaf(w, rho0, __half2float(__ushort_as_half(lo)));
+      tm = fmaf(w, rho0, __half2float(__ushort_as_half(hi)));
+    }
+    __device__ __forceinline__ void put_rest(unsigned site, float r1, float r2, float4 c) const {
+      r[site] = r1;
+      r[N + site] = r2;
+      coef[site] = c;
+    }
+  };
+  __host__ __device__ static Reader reader(const void* base, unsigned N, float rho0) {
+    const char* b = (const char*)base;
+    return Reader{(const __half*)b, (const float*)(b + rest_offset(N)), (const float4*)(b + coef_offset(N)), N, rho0};
+  }
+  __host__ __device__ static Totals totals(const void* base, unsigned N, float rho0) {
+    const char* b = (const char*)base;
+    return Totals{(const __half*)b, (const float*)(b + rest_offset(N)), N, rho0};
+  }
+  __host__ __device__ static Writer writer(void* base, unsigned N, float rho0) {
+    char* b = (char*)base;
+    return Writer{(__half*)b, (float*)(b + rest_offset(N)), (float4*)(b + coef_offset(N)), N, rho0, 0u};
   }
 };
 
 // The FP32 operator of collide_store (BGK with the Guo source and the perturbation per
-// pair of opposite directions) on the totals t, stored in the total + recolouring form.
+// pair of opposite directions) on the totals t, stored in a total + recolouring form.
+template <typename WR>
 __device__ __forceinline__ void collide_totals(const float t[27], float rho1, float rho2, float rho, const float u[3],
                                                const float F[3], float g, const float m[3], const StepT<float>& p,
-                                               const TotalRecol::Writer& fout, unsigned site) {
+                                               const WR& fout, unsigned site) {
   const float uF = u[0] * F[0] + u[1] * F[1] + u[2] * F[2];
   const float uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
   const float seg = M<float>::div(p.beta * rho1 * rho2, rho);
@@ -971,7 +1095,7 @@ __device__ __forceinline__ void collide_totals(const float t[27], float rho1, fl
   const float a3 = 3.f * orho, a45 = 4.5f * orho, g3 = 3.f * p.guo, g9 = 9.f * p.guo;
   const float om1 = 1.f - p.omega;
   const float4 cf = make_float4(c1, seg * m[0], seg * m[1], seg * m[2]);
-  const unsigned N = fout.N;
+  const unsigned hb = fout.site_bits(site);
   float s1 = 0.f, s2 = 0.f;
   static_for<27>([&](auto I) {
     constexpr int i = decltype(I)::value;
@@ -991,32 +1115,33 @@ __device__ __forceinline__ void collide_totals(const float t[27], float rho1, fl
       const float O = fmaf(g3, cF, a3 * cu);
       const float fsp = fmaf(w, E + O, om1 * t[i]);
       const float fsm = fmaf(w, E - O, om1 * t[o]);
-      fout.f[(unsigned)i * N + site] = fsp;
-      fout.f[(unsigned)o * N + site] = fsm;
-      // component 1 of the pair exactly as a reader will recompute it
-      const float ap = fmaf(c1, fsp, TotalRecol::rc<i>(cf));
-      const float am = fmaf(c1, fsm, TotalRecol::rc<o>(cf));
+      float tp, tm;
+      fout.template put_pair<i, o>(site, fsp, fsm, hb, tp, tm);
+      // the components of the stored pair exactly as a reader will recompute them
+      float ap, bp, am, bm;
+      split_total<i>(tp, cf, ap, bp);
+      split_total<o>(tm, cf, am, bm);
       s1 += ap + am;
-      s2 += (fsp - ap) + (fsm - am);
+      s2 += bp + bm;
     }
   });
-  fout.f[site] = rho1 - s1;
-  fout.f[27u * N + site] = rho2 - s2;
-  fout.coef[site] = cf;
+  fout.put_rest(site, rho1 - s1, rho2 - s2, cf);
 }
 
-// The streaming collision storing the total + recolouring form, from a state in that form
-// (RD = TotalRecol::Totals, TOTALS) or in the two-population layout (RD = Plain reader:
-// the first step after a state was set). rho_1 of the site comes from the moments pass
-// (rho1m), rho from the pulled totals, rho_2 = rho - rho_1. Capped at 64 registers (four
-// blocks per SM; 24 bytes of spills): 395 us per duct step against 441 us at 80 registers
-// and three blocks, the kernel waiting on its loads.
-template <typename RD, bool TOTALS>
-__global__ void __launch_bounds__(256, 4) collide3t_kernel(RD f, TotalRecol::Writer fout,
-                                                           const float* __restrict__ rho1m,
+// The streaming collision storing a total + recolouring form (WR), from a state in that
+// form (RD its Totals, TOTALS) or in the two-population layout of the precision (RD the
+// Plain or HalfDev reader: the first step after a state was set). rho_1 of the site comes
+// from the moments pass (rho1m), rho from the pulled totals, rho_2 = rho - rho_1. Capped at
+// 64 registers (four blocks per SM; 24 bytes of spills in the FP32 build): 395 us per FP32
+// duct step against 441 us at 80 registers and three blocks, the kernel waiting on its loads.
+template <typename RD, bool TOTALS, typename WR>
+__global__ void __launch_bounds__(256, 4) collide3t_kernel(RD f, WR fout, const float* __restrict__ rho1m,
                                                            const float4* __restrict__ ng, StepT<float> p) {
   const int x = blockIdx.x * 32 + threadIdx.x, y = blockIdx.y * 8 + threadIdx.y, z = blockIdx.z;
   const unsigned site = (unsigned)x + (unsigned)p.nx * ((unsigned)y + (unsigned)p.ny * (unsigned)z);
+  if constexpr (std::is_same<WR, TotalRecolHalf::Writer>::value)
+    fout.seed = step_seed(p, p.parity, blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0 && threadIdx.x == 0 &&
+                                           threadIdx.y == 0);
   float fin[2][27];
   pull_any<1, float>(f, x, y, z, p, fin);  // the pulls' loads in flight while the ray resolves
   const float4 v = ng[site];
@@ -1049,22 +1174,7 @@ __global__ void __launch_bounds__(256, 4) collide3t_kernel(RD f, TotalRecol::Wri
 #pragma unroll
   for (int a = 0; a < 3; ++a) u[a] = M<float>::div(j[a] + 0.5f * F[a], rho);
   const float m[3] = {-v.x, -v.y, -v.z};
-  collide_totals(t, rho1, rho2, rho, u, F, v.w, m, p, fout, site);
-}
-
-// A state in the total + recolouring form written out in the two-population layout
-// (into another buffer: the form's coefficient plane overlaps other sites' populations
-// of that layout).
-__global__ void __launch_bounds__(256) totals_to_pairs_kernel(TotalRecol::Reader f, float* __restrict__ out, int N) {
-  const int idx = blockIdx.x * 256 + threadIdx.x;
-  if (idx >= N) return;
-  static_for<27>([&](auto I) {
-    constexpr int i = decltype(I)::value;
-    float a, b;
-    f.template get<i>((unsigned)idx, a, b);
-    out[(size_t)i * N + idx] = a;
-    out[(size_t)(27 + i) * N + idx] = b;
-  });
+  collide_totals<WR>(t, rho1, rho2, rho, u, F, v.w, m, p, fout, site);
 }
 
 }  // namespace lbnci

@@ -467,7 +467,7 @@ tiled_kernel(typename ST::Reader f, typename ST::Writer fout, const typename ST:
 #pragma unroll
     for (int a = 0; a < 3; ++a) u[a] = M<T>::div(j[a] + T(0.5) * F[a], rho);
 
-    if (FIELDS) {
+    if constexpr (FIELDS) {
       if (fo.rho1) fo.rho1[idx] = (double)rho1;
       if (fo.rho2) fo.rho2[idx] = (double)rho2;
       if (fo.psi) fo.psi[idx] = (double)psi_own;

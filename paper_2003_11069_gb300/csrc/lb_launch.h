@@ -51,7 +51,8 @@ struct HostParams {
   int carry3d;    // 1: D3Q27 FP32 / FP16-dev steps run the single-read carry kernels
   int c3_zseg;    // planes per z segment of their collision kernel
   int stream3d;   // 1: D3Q27 steps run moments, normals and a streaming collision
-  int totals;     // 1: FP32 streaming steps with Guo forcing store the total + recolouring form
+  int totals;     // 1: streaming steps with Guo forcing store the total + recolouring form
+  float rho_ref;  // reference density rho_0 of the FP16 totals (f*_i = w_i rho_0 + d_i)
   unsigned* seedw;  // device: two dither-seed words of the FP16-deviation stores
   int parity;       // state buffer the next step reads (0: the one the sim was created with)
   double tau, A_s, beta, A_h, h_min, h_max, g_th, G[3];
@@ -126,17 +127,22 @@ cudaError_t carry3d_init(const void* f, void* carry, void* ring, void* ghost, co
 // Streaming D3Q27 step (lb_carry3d.cu) for FP32 and FP16-dev storage on lattices of whole
 // 32 x 8 columns: moments (psi), normals3d ((n, |grad psi|) into ng, N float4), collide3d
 // (near-contact ray, pull, collision: fa -> fb). Kernels launched -> *nk.
-// With h.totals, FP32 steps under Guo forcing store the total + recolouring form
-// (TotalRecol in lb_carry3d.cuh: the total populations, the rest population of each
-// component and (rho_1/rho, beta rho_1 rho_2/rho m) per site); totals_in says that fa
-// holds that form; rho1 (N floats) carries rho_1 from the moments pass to the collision.
+// With h.totals, steps under Guo forcing store the total + recolouring form of the
+// precision (TotalRecol / TotalRecolHalf in lb_carry3d.cuh: the total populations, the rest
+// population of each component and (rho_1/rho, beta rho_1 rho_2/rho m) per site; FP16 totals
+// as deviations from w_i h.rho_ref); totals_in says that fa holds that form; rho1 (N floats)
+// carries rho_1 from the moments pass to the collision.
 bool stream3d_supported(const HostParams& h);
 bool stream3d_stores_totals(const HostParams& h);
 cudaError_t stream3d_step(const void* fa, void* fb, void* psi, void* ng, void* rho1, int totals_in,
                           const HostParams& h, cudaStream_t s, int* nk);
-// a state in the total + recolouring form written into `out` in the two-population layout
-cudaError_t stream3d_totals_to_pairs(const void* f, void* out, const HostParams& h, cudaStream_t s);
-size_t stream3d_totals_bytes(size_t N);
+// fields and population copies of a state in the total + recolouring form (the
+// Launchers::fields / decode of the other states)
+cudaError_t stream3d_form_fields(const void* f, void* psi, const HostParams& h, const FieldOut& fo, cudaStream_t s,
+                                 int* nk);
+cudaError_t stream3d_form_decode(const void* f, double* out, int s0, int count, long long pitch, const HostParams& h,
+                                 cudaStream_t s);
+size_t stream3d_totals_bytes(size_t N, int half);
 cudaError_t carry3d_step(const TmaMaps& m, int from, const void* fa, void* fb, void* carry, void* ring, void* ghost,
                          void* ng, void* hit, int* err, const HostParams& h, cudaStream_t s, int* nk);
 

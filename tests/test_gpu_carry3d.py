@@ -33,10 +33,10 @@ def _duct(nx, ny, nz, seed):
     return inputs.duct_emulsion_3d(nx, ny, nz, seed=seed, radius=5.0, volume_fraction=0.5)
 
 
-def _check_step(p, f_start, got, precision, what):
+def _check_step(p, f_start, got, precision, what, form=lbnci.LB_STATE_PAIRS):
     ref = oracle.step(p, f_start, 1)
     near, of = _near_tie_sites(p, f_start)
-    err = step_error(p, got, ref, precision)
+    err = step_error(p, got, ref, precision, form)
     ok = ~near
     assert (of["hit"][ok] > 0).sum() > 0, f"{what}: NCI must be active"
     bad = err[:, ok].max(axis=0) > 1.0

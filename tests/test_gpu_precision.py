@@ -21,18 +21,33 @@ from test_gpu_parity import FP32_TOL, _near_tie_sites
 pytestmark = pytest.mark.gpu
 
 
-def step_error(p, got, ref, precision):
+def step_error(p, got, ref, precision, form=lbnci.LB_STATE_PAIRS, rho0=None):
     """Per element ([2 Q, N]) |got - ref| in units of what one step may differ by in
     `precision`: FP32, FP32_TOL on the population scale max(|f|, w_i); FP16-deviation
-    storage, in addition one stochastically rounded FP16 store of the deviation
-    delta = f - w_i rho_k (less than one FP16 unit: 2^-10 |delta|, or 2^-24 below FP16's
-    normal range). rho_k, the site's density of component k, is the same before and
-    after the step (the collision keeps each component's mass). At most 1 passes."""
+    storage, in addition one stochastically rounded FP16 store (less than one FP16 unit:
+    2^-10 |d|, or 2^-24 below FP16's normal range) of
+      * pairs: each component's deviation d = f - w_i rho_k, rho_k the site's density of
+        component k, the same before and after the step (the collision keeps each
+        component's mass);
+      * the total + recolouring form: the total's deviation d = f*_i - w_i rho_0 (rho_0 the
+        sim's reference density, by default the mean total density of ref), which reaches
+        component k as phi_k = rho_k/rho times it; the rest population of component k is
+        rho_k minus the others, so it carries the sum of their roundings.
+    At most 1 passes."""
     Q, N = oracle.Q_of(p), oracle.N_of(p)
     _, w, _ = oracle.lattice(p.lattice)
     r3, g3 = ref.reshape(2, Q, N), got.reshape(2, Q, N)
     bound = FP32_TOL * np.maximum(np.abs(r3), w[None, :, None])
-    if precision == lbnci.LB_FP16DEV:
+    if precision == lbnci.LB_FP16DEV and form == lbnci.LB_STATE_TOTAL_RECOLOUR:
+        t = r3.sum(axis=0)
+        rho = t.sum(axis=0)
+        phi = np.abs(r3.sum(axis=1)) / rho
+        if rho0 is None:
+            rho0 = float(rho.mean())
+        q = 2.0 ** -10 * np.abs(t - w[:, None] * rho0) + 2.0 ** -24
+        q[0] = q[1:].sum(axis=0)
+        bound = bound + phi[:, None, :] * q[None, :, :]
+    elif precision == lbnci.LB_FP16DEV:
         dev = r3 - w[None, :, None] * r3.sum(axis=1)[:, None, :]
         bound = bound + 2.0 ** -10 * np.abs(dev) + 2.0 ** -24
     return (np.abs(g3 - r3) / bound).reshape(2 * Q, N)

@@ -1,16 +1,17 @@
 """The streaming D3Q27 step (LB_PATH_D3Q27_STREAM, the default for FP32 and FP16-dev storage on
 lattices of whole 32 x 8 columns): a moments kernel (psi, and rho_1 for the total form),
 normals3d_kernel (per-site n and |grad psi|) and the collision kernel (the near-contact ray
-over those normals, pull, collision and store without shared memory). FP32 steps with Guo
-forcing store the total + recolouring form (LB_STATE_TOTAL_RECOLOUR); the others, and
-FP32 with LBNCI_D3_STATE=pairs, the two components' populations.
+over those normals, pull, collision and store without shared memory). Steps under Guo
+forcing store the total + recolouring form (LB_STATE_TOTAL_RECOLOUR: FP32 totals, or FP16
+deviations of the totals from w_i rho_0); EDM steps, and steps with LBNCI_D3_STATE=pairs,
+the two components' populations.
 
-Each of four consecutive steps must lie within the storage's per-step bound of one oracle
-step from the GPU's own previous state (walls in y and z, periodic axes, a lattice of one
-column), in FP32 (both forms) and FP16-deviation storage, with Guo and EDM forcing. Reading
-the state rewrites the total form as pairs, so those steps read pairs; a step that reads
-the total form is compared through a twin sim that was not read in between. Chained steps
-equal separate ones bitwise."""
+Each of four consecutive steps must lie within the storage's per-step bound (step_error, per
+form) of one oracle step from the GPU's own previous state (walls in y and z, periodic axes,
+a lattice of one column), in FP32 and FP16-deviation storage, both forms, Guo and EDM
+forcing. Reading the state (fields, populations) goes through the form's own reader and
+leaves the state as it is, so the later steps read the form; the first reads the pairs the
+state was set as. Chained steps equal separate ones bitwise."""
 import numpy as np
 import pytest
 
@@ -28,8 +29,8 @@ def _lib():
     lbnci.load()
 
 
-def _form(precision, forcing, state):
-    if precision == lbnci.LB_FP32 and forcing == 0 and state == "default":
+def _form(forcing, state):
+    if forcing == 0 and state == "default":
         return lbnci.LB_STATE_TOTAL_RECOLOUR
     return lbnci.LB_STATE_PAIRS
 
@@ -39,8 +40,8 @@ def _form(precision, forcing, state):
 @pytest.mark.parametrize("precision", [lbnci.LB_FP32, lbnci.LB_FP16DEV])
 @pytest.mark.parametrize("name", list(CASES))
 def test_stream3d_steps_match_oracle(name, precision, forcing, state, monkeypatch):
-    if state == "pairs" and not (precision == lbnci.LB_FP32 and forcing == 0):
-        pytest.skip("LBNCI_D3_STATE=pairs changes only FP32 steps with Guo forcing")
+    if state == "pairs" and forcing != 0:
+        pytest.skip("LBNCI_D3_STATE=pairs changes only steps with Guo forcing")
     monkeypatch.delenv("LBNCI_D3_KERNEL", raising=False)
     if state == "pairs":
         monkeypatch.setenv("LBNCI_D3_STATE", "pairs")
@@ -53,13 +54,14 @@ def test_stream3d_steps_match_oracle(name, precision, forcing, state, monkeypatc
     f0 = oracle.step(p, oracle.init(p, fl.rho1, fl.rho2), 20)
     with lbnci.Sim(_cfg(p, precision)) as sim:
         assert sim.step_path() == lbnci.LB_PATH_D3Q27_STREAM
-        assert sim.state_form() == _form(precision, forcing, state)
+        form = sim.state_form()
+        assert form == _form(forcing, state)
         sim.set_populations(f0)
         start = sim.get_populations()  # the representable state
         for k in range(4):
             sim.step(1)
             got = sim.get_populations()
-            err = _check_step(p, start, got, precision, f"{name} step {k}")
+            err = _check_step(p, start, got, precision, f"{name} step {k}", form)
             print(f"{name} precision {precision} forcing {forcing} step {k}: max error {err:.3f} of the bound")
             start = got
         assert sim.observables()["n_bad"] == 0
@@ -101,15 +103,15 @@ def test_stream3d_chained_equals_separate(precision, monkeypatch):
         assert a.observables()["n_nci"] > 0
 
 
+@pytest.mark.parametrize("precision", [lbnci.LB_FP32, lbnci.LB_FP16DEV])
 @pytest.mark.parametrize("name", list(CASES))
-def test_stream3d_total_form_input_matches_oracle(name, monkeypatch):
-    """A step that reads the total + recolouring form. Sim b takes three chained steps from
-    f0 (its 2nd and 3rd read the form); sim a takes two, is read (S, its state rewritten as
-    pairs, the same populations the form stands for, since both sims are bitwise equal until
-    read), and takes the third from pairs. b's third step must lie within the FP32 per-step
-    bound of one oracle step from S, and agree with a's to rounding: the two read the same
-    populations, so psi, the normals and the NCI decisions are the same, and only the
-    pulled totals (f*_i against f_i^1 + f_i^2) differ in their last bit."""
+def test_stream3d_total_form_input_matches_oracle(name, precision, monkeypatch):
+    """A step that reads the total + recolouring form, after two steps from f0 (reading S, the
+    state after them, leaves it in the form), must lie within the form's per-step bound of one
+    oracle step from S. In FP32 it must also agree to rounding with a step from S set as
+    pairs (S is exact in FP32): the two read the same populations, so psi, the normals and
+    the NCI decisions are the same, and only the pulled totals (f*_i against
+    f_i^1 + f_i^2) differ in their last bit."""
     from test_gpu_precision import step_error
 
     monkeypatch.delenv("LBNCI_D3_KERNEL", raising=False)
@@ -119,19 +121,23 @@ def test_stream3d_total_form_input_matches_oracle(name, monkeypatch):
                            **geo)
     fl = _duct(geo["nx"], geo["ny"], geo["nz"], seed=17)
     f0 = oracle.step(p, oracle.init(p, fl.rho1, fl.rho2), 20)
-    cfg = _cfg(p, lbnci.LB_FP32)
-    with lbnci.Sim(cfg) as a, lbnci.Sim(cfg) as b:
-        assert a.state_form() == lbnci.LB_STATE_TOTAL_RECOLOUR
-        a.set_populations(f0)
+    form = lbnci.LB_STATE_TOTAL_RECOLOUR
+    cfg = _cfg(p, precision)
+    with lbnci.Sim(cfg) as b:
+        assert b.state_form() == form
         b.set_populations(f0)
-        a.step(2)
-        b.step(3)
-        s = a.get_populations()
+        b.step(2)
+        s = b.get_populations()
+        b.step(1)
+        got_b = b.get_populations()
+    err = _check_step(p, s, got_b, precision, f"{name} step from the total form", form)
+    print(f"{name} precision {precision}: step from the total form: max error {err:.3f} of the bound")
+    if precision != lbnci.LB_FP32:
+        return
+    with lbnci.Sim(cfg) as a:
+        a.set_populations(s)
         a.step(1)
         got_a = a.get_populations()
-        got_b = b.get_populations()
-    err = _check_step(p, s, got_b, lbnci.LB_FP32, f"{name} step from the total form")
-    print(f"{name}: step from the total form: max error {err:.3f} of the bound")
     rel = float(step_error(p, got_b, got_a, lbnci.LB_FP32).max())
     print(f"{name}: total-form input against pairs input: {rel:.3f} of the bound")
     assert rel < 0.5, rel
