@@ -74,7 +74,7 @@ struct lb_sim {
   void* ng;
   void* hit;
   bool carry_ok;   // the carried densities belong to the current state
-  void* rho1;      // streaming D3Q27 path: rho_1 of each site from the moments pass
+  void* rho1;      // streaming D3Q27 path: (rho_1, rho_2) of each site from the moments pass
   bool totals_state;  // fa holds the total + recolouring form (p.totals)
   double* partials;
   double* result;  // kRedSlots doubles
@@ -224,7 +224,7 @@ lb_status validate(const lb_config* c, HostParams* p, Layout* lay, long long* nb
   }
   if (p->stream3d) {
     lay->ng = off; off = align256(off + (size_t)N * 16);
-    lay->rho1 = off; off = align256(off + (size_t)N * sizeof(float));
+    lay->rho1 = off; off = align256(off + (size_t)N * 2 * sizeof(float));
   }
   lay->total = off;
   return LB_OK;

@@ -1,6 +1,7 @@
 // lb_carry3d.cu -- launchers of the D3Q27 steps of lb_carry3d.cuh for FP32 and
 // FP16-deviation storage: the single-read step (with its tensor maps) and the streaming
 // step.
+#include <cmath>
 #include <cstring>
 
 #include "lb_carry3d.cuh"
@@ -236,16 +237,23 @@ bool stream3d_supported(const HostParams& h) { return h.nx % 32 == 0 && h.ny % 8
 bool stream3d_stores_totals(const HostParams& h) { return h.totals && h.forcing != 1; }
 
 namespace {
+// rho_0/216 rounded to a multiple of 2^-24: the unit of the FP16 totals' reference (216 w_i) r
+float rho_unit(const HostParams& h) {
+  return float(std::rint(double(h.rho_ref) / 216.0 * 16777216.0) / 16777216.0);
+}
+}  // namespace
+
+namespace {
 // the collision storing the total + recolouring form of the precision
 template <typename RD, bool TOTALS, typename WR>
-cudaError_t launch_collide3t(RD rd, WR wr, const void* rho1, const void* ng, const StepT<float>& p, dim3 grid,
+cudaError_t launch_collide3t(RD rd, WR wr, const void* rho12, const void* ng, const StepT<float>& p, dim3 grid,
                              cudaStream_t s) {
-  collide3t_kernel<RD, TOTALS, WR><<<grid, dim3(32, 8), 0, s>>>(rd, wr, (const float*)rho1, (const float4*)ng, p);
+  collide3t_kernel<RD, TOTALS, WR><<<grid, dim3(32, 8), 0, s>>>(rd, wr, (const float2*)rho12, (const float4*)ng, p);
   return cudaGetLastError();
 }
 }  // namespace
 
-cudaError_t stream3d_step(const void* fa, void* fb, void* psi, void* ng, void* rho1, int totals_in,
+cudaError_t stream3d_step(const void* fa, void* fb, void* psi, void* ng, void* rho12, int totals_in,
                           const HostParams& h, cudaStream_t s, int* nk) {
   const StepT<float> p = to_step3(h);
   *nk = 0;
@@ -253,22 +261,22 @@ cudaError_t stream3d_step(const void* fa, void* fb, void* psi, void* ng, void* r
   if (totals_in && !totals_out) return cudaErrorInvalidValue;  // no step reads that form into pairs
   const dim3 grid((unsigned)(h.nx / 32), (unsigned)(h.ny / 8), (unsigned)h.nz);
   const unsigned N = (unsigned)p.N;
-  const float rho0 = h.rho_ref;
-  float* r1 = totals_out ? (float*)rho1 : nullptr;
+  const float r0 = rho_unit(h);
+  float2* r12 = totals_out ? (float2*)rho12 : nullptr;
   // 32 x 8 blocks where the sources carry per-site data that repeats within the block
   // (FP16-dev pairs: the reference densities, 0.85 ms per duct step against 0.95 ms with
   // blocks of 256 consecutive sites; the total forms: the recolouring coefficients, about
   // two thirds of whose sectors hit L1); the two-population FP32 state has none and keeps
   // the flat kernel (the same time)
   if (totals_in && h.half) {
-    moments3_kernel<TotalRecolHalf><<<grid, dim3(32, 8), 0, s>>>(TotalRecolHalf::reader(fa, N, rho0), (float*)psi,
-                                                                 r1, p);
+    moments3_kernel<TotalRecolHalf><<<grid, dim3(32, 8), 0, s>>>(TotalRecolHalf::reader(fa, N, r0), (float*)psi,
+                                                                 r12, p);
   } else if (totals_in) {
-    moments3_kernel<TotalRecol><<<grid, dim3(32, 8), 0, s>>>(TotalRecol::reader(fa, N), (float*)psi, r1, p);
+    moments3_kernel<TotalRecol><<<grid, dim3(32, 8), 0, s>>>(TotalRecol::reader(fa, N), (float*)psi, r12, p);
   } else if (h.half) {
-    moments3_kernel<HalfDev<1>><<<grid, dim3(32, 8), 0, s>>>(HalfDev<1>::reader(fa, N), (float*)psi, r1, p);
+    moments3_kernel<HalfDev<1>><<<grid, dim3(32, 8), 0, s>>>(HalfDev<1>::reader(fa, N), (float*)psi, r12, p);
   } else if (totals_out) {
-    moments3_kernel<Plain<1, float>><<<grid, dim3(32, 8), 0, s>>>(Plain<1, float>::reader(fa, N), (float*)psi, r1,
+    moments3_kernel<Plain<1, float>><<<grid, dim3(32, 8), 0, s>>>(Plain<1, float>::reader(fa, N), (float*)psi, r12,
                                                                   p);
   } else {
     const unsigned nb = (unsigned)((p.N + 255) / 256);
@@ -283,14 +291,14 @@ cudaError_t stream3d_step(const void* fa, void* fb, void* psi, void* ng, void* r
   if (e != cudaSuccess) return e;
   ++*nk;
   if (totals_out && h.half) {
-    const TotalRecolHalf::Writer wr = TotalRecolHalf::writer(fb, N, rho0);
-    e = totals_in ? launch_collide3t<TotalRecolHalf::Totals, true>(TotalRecolHalf::totals(fa, N, rho0), wr, rho1, ng,
+    const TotalRecolHalf::Writer wr = TotalRecolHalf::writer(fb, N, r0);
+    e = totals_in ? launch_collide3t<TotalRecolHalf::Totals, true>(TotalRecolHalf::totals(fa, N, r0), wr, rho12, ng,
                                                                    p, grid, s)
-                  : launch_collide3t<HalfDev<1>::Reader, false>(HalfDev<1>::reader(fa, N), wr, rho1, ng, p, grid, s);
+                  : launch_collide3t<HalfDev<1>::Reader, false>(HalfDev<1>::reader(fa, N), wr, rho12, ng, p, grid, s);
   } else if (totals_out) {
     const TotalRecol::Writer wr = TotalRecol::writer(fb, N);
-    e = totals_in ? launch_collide3t<TotalRecol::Totals, true>(TotalRecol::totals(fa, N), wr, rho1, ng, p, grid, s)
-                  : launch_collide3t<Plain<1, float>::Reader, false>(Plain<1, float>::reader(fa, N), wr, rho1, ng, p,
+    e = totals_in ? launch_collide3t<TotalRecol::Totals, true>(TotalRecol::totals(fa, N), wr, rho12, ng, p, grid, s)
+                  : launch_collide3t<Plain<1, float>::Reader, false>(Plain<1, float>::reader(fa, N), wr, rho12, ng, p,
                                                                       grid, s);
   } else {
     e = h.half ? launch_collide3d<HalfDev<1>>(fa, fb, (const float4*)ng, p, grid, s)
@@ -326,7 +334,7 @@ cudaError_t form_fields(typename FORM::Reader rd, void* psi, const HostParams& h
 
 cudaError_t stream3d_form_fields(const void* f, void* psi, const HostParams& h, const FieldOut& fo, cudaStream_t s,
                                  int* nk) {
-  if (h.half) return form_fields<TotalRecolHalf>(TotalRecolHalf::reader(f, (unsigned)h.N, h.rho_ref), psi, h, fo, s, nk);
+  if (h.half) return form_fields<TotalRecolHalf>(TotalRecolHalf::reader(f, (unsigned)h.N, rho_unit(h)), psi, h, fo, s, nk);
   return form_fields<TotalRecol>(TotalRecol::reader(f, (unsigned)h.N), psi, h, fo, s, nk);
 }
 
@@ -335,7 +343,7 @@ cudaError_t stream3d_form_decode(const void* f, double* out, int s0, int count, 
   if (count <= 0) return cudaSuccess;
   const unsigned nb = (unsigned)((count + 255) / 256);
   if (h.half)
-    decode_kernel<1, TotalRecolHalf><<<nb, 256, 0, s>>>(TotalRecolHalf::reader(f, (unsigned)h.N, h.rho_ref), out, s0,
+    decode_kernel<1, TotalRecolHalf><<<nb, 256, 0, s>>>(TotalRecolHalf::reader(f, (unsigned)h.N, rho_unit(h)), out, s0,
                                                         count, pitch);
   else
     decode_kernel<1, TotalRecol><<<nb, 256, 0, s>>>(TotalRecol::reader(f, (unsigned)h.N), out, s0, count, pitch);

@@ -827,14 +827,16 @@ __global__ void __launch_bounds__(256) normals3d_kernel(const float* __restrict_
 // block's other sites.
 template <typename ST>
 __global__ void __launch_bounds__(256) moments3_kernel(typename ST::Reader f, float* __restrict__ psi,
-                                                       float* __restrict__ rho1, StepT<float> p) {
+                                                       float2* __restrict__ rho12, StepT<float> p) {
   const int x = blockIdx.x * 32 + threadIdx.x, y = blockIdx.y * 8 + threadIdx.y, z = blockIdx.z;
   const int site = x + p.nx * (y + p.ny * z);
   float fin[2][27];
   pull_any<1, float>(f, x, y, z, p, fin);
   float r1, r2;
   psi[site] = psi_of<27, float>(fin, &r1, &r2);
-  if (rho1) rho1[site] = r1;  // the collision of a state of totals takes rho_1 from here
+  // the collision storing a total form takes (rho_1, rho_2) from here: the component sums
+  // the fields kernel also forms, so the two count each component's mass alike
+  if (rho12) rho12[site] = make_float2(r1, r2);
 }
 
 template <typename ST, bool EDM>
@@ -886,11 +888,12 @@ __global__ void __launch_bounds__(256) collide3d_kernel(typename ST::Reader f, t
 // phi_1 = rho_1/rho, s = beta (rho_1 rho_2/rho) m (the recolouring term written with the
 // vector s instead of the angle to m). A state in this form holds the 26 moving totals, the
 // rest population of each component and one float4 (phi_1, s) per site. The rest
-// populations stay per component, rho_k minus that component's moving populations as a
-// reader recomputes them from the stored totals, so each site's component masses are kept
-// to the rounding of one difference, as in the two-population collision. The
-// exact-difference forcing adds a term per component after the recolouring; its steps keep
-// the two-population form.
+// populations stay per component: rho_k minus phi_k times the sum S of the stored moving
+// totals (the moving populations of component 1 sum to phi_1 S, since the recolouring
+// terms of opposite directions cancel exactly), so each site's component masses are kept
+// to the rounding of the sums, as in the two-population collision. The exact-difference
+// forcing adds a term per component after the recolouring; its steps keep the
+// two-population form.
 //
 //   TotalRecol      FP32 totals: plane 0 f_0^1, planes 1..26 f*_i, plane 27 f_0^2 (planes
 //                   0 and 27 are also where the two-population layout keeps the rest
@@ -902,6 +905,14 @@ __global__ void __launch_bounds__(256) collide3d_kernel(typename ST::Reader f, t
 //                   two FP32 rest planes and the coefficient plane: 76 bytes per site. A
 //                   step rounds d_i stochastically (half2_stochastic, the site's dither
 //                   bits); the rest populations and the split use the rounded totals.
+//                   The reference is held as w_i rho_0 = (216 w_i) r with 216 w_i in
+//                   {64, 16, 4, 1} and r = rho_0/216 rounded to a multiple of 2^-24 (the
+//                   host's rho_unit): every decoded total is then a multiple of 2^-24 and,
+//                   below 1, exact in FP32, and so is the collision's sum of a site's
+//                   totals. With w_i rho_0 rounded instead, the totals' low bits were the
+//                   same at every site and that sum's one rounding went the same way nearly
+//                   everywhere: the rest populations made 7.5e-9 of the mass per site and
+//                   step.
 //
 // Both offer the two-population reader interface (get<I>: both components of direction I),
 // through which the moments pass, the fields kernel and population copies read them, and
@@ -909,8 +920,9 @@ __global__ void __launch_bounds__(256) collide3d_kernel(typename ST::Reader f, t
 
 // (w_i/|c_i|) c_i.s of moving direction I, s = (c.y, c.z, c.w), summed over the nonzero
 // components of c_i in x, y, z order for I < opposite(I), and exactly the negative of its
-// opposite's for the others: the collision and every reader evaluate it with these same
-// operations, so they agree bit for bit, and a pair of opposite directions costs one.
+// opposite's for the others: every reader evaluates it with these same operations, and the
+// terms of a pair of opposite directions cancel exactly (the collision's rest populations
+// rely on it).
 template <int I>
 __device__ __forceinline__ float recolour_term(const float4 c) {
   if constexpr (I > opposite(I)) return -recolour_term<opposite(I)>(c);
@@ -963,6 +975,7 @@ struct TotalRecol {
     }
   };
   struct Writer {
+    static constexpr bool kCompensate = true;  // the collision's sum of the totals
     float* __restrict__ f;
     float4* __restrict__ coef;
     unsigned N;
@@ -1003,10 +1016,13 @@ struct TotalRecolHalf {
   }
   static size_t bytes(size_t N) { return coef_offset(N) + N * sizeof(float4); }
 
-  // f*_i = w_i rho_0 + d_i, one expression for every reader and the writer
+  // 216 w_I: 64, 16, 4 or 1 (exact)
   template <int I>
-  __device__ __forceinline__ static float total(const __half* d, unsigned N, unsigned site, float rho0) {
-    return fmaf(float(Lattice<1>::w(I)), rho0, __half2float(d[(unsigned)(I - 1) * N + site]));
+  __host__ __device__ static constexpr float k216() { return float(216.0 * Lattice<1>::w(I)); }
+  // f*_i = (216 w_i) r + d_i, one expression for every reader and the writer
+  template <int I>
+  __device__ __forceinline__ static float total(const __half* d, unsigned N, unsigned site, float r) {
+    return fmaf(k216<I>(), r, __half2float(d[(unsigned)(I - 1) * N + site]));
   }
 
   struct Reader {
@@ -1014,14 +1030,14 @@ struct TotalRecolHalf {
     const float* __restrict__ r;
     const float4* __restrict__ coef;
     unsigned N;
-    float rho0;
+    float r0;  // rho_0/216 on the 2^-24 grid (the host's rho_unit)
     template <int I>
     __device__ __forceinline__ void get(unsigned site, float& a, float& b) const {
       if constexpr (I == 0) {
         a = r[site];
         b = r[N + site];
       } else {
-        split_total<I>(total<I>(d, N, site, rho0), coef[site], a, b);
+        split_total<I>(total<I>(d, N, site, r0), coef[site], a, b);
       }
     }
   };
@@ -1029,20 +1045,21 @@ struct TotalRecolHalf {
     const __half* __restrict__ d;
     const float* __restrict__ r;
     unsigned N;
-    float rho0;
+    float r0;  // rho_0/216 on the 2^-24 grid (the host's rho_unit)
     template <int I>
     __device__ __forceinline__ void get(unsigned site, float& a, float& b) const {
       if constexpr (I == 0) a = r[site] + r[N + site];
-      else a = total<I>(d, N, site, rho0);
+      else a = total<I>(d, N, site, r0);
       b = 0.f;
     }
   };
   struct Writer {
+    static constexpr bool kCompensate = false;  // the totals are multiples of 2^-24: their sum is exact
     __half* __restrict__ d;
     float* __restrict__ r;
     float4* __restrict__ coef;
     unsigned N;
-    float rho0;
+    float r0;  // rho_0/216 on the 2^-24 grid (the host's rho_unit)
     unsigned seed;  // this step's dither seed (step_seed)
     __device__ __forceinline__ unsigned site_bits(unsigned site) const { return dither_bits(site, seed); }
     // d_I and d_O rounded stochastically as one half2 (I low, O high) with the site's bits h;
@@ -1050,14 +1067,14 @@ struct TotalRecolHalf {
     template <int I, int O>
     __device__ __forceinline__ void put_pair(unsigned site, float fp, float fm, unsigned h, float& tp,
                                              float& tm) const {
-      constexpr float w = float(Lattice<1>::w(I));
-      const unsigned v = half2_stochastic<I>(fmaf(-w, rho0, fp), fmaf(-w, rho0, fm), h);
+      constexpr float w = k216<I>();
+      const unsigned v = half2_stochastic<I>(fmaf(-w, r0, fp), fmaf(-w, r0, fm), h);
       const unsigned short lo = (unsigned short)(v & 0xFFFFu), hi = (unsigned short)(v >> 16);
       unsigned short* du = reinterpret_cast<unsigned short*>(d);
       du[(unsigned)(I - 1) * N + site] = lo;
       du[(unsigned)(O - 1) * N + site] = hi;
-      tp = fmaf(w, rho0, __half2float(__ushort_as_half(lo)));
-      tm = fmaf(w, rho0, __half2float(__ushort_as_half(hi)));
+      tp = fmaf(w, r0, __half2float(__ushort_as_half(lo)));
+      tm = fmaf(w, r0, __half2float(__ushort_as_half(hi)));
     }
     __device__ __forceinline__ void put_rest(unsigned site, float r1, float r2, float4 c) const {
       r[site] = r1;
@@ -1065,17 +1082,17 @@ struct TotalRecolHalf {
       coef[site] = c;
     }
   };
-  __host__ __device__ static Reader reader(const void* base, unsigned N, float rho0) {
+  __host__ __device__ static Reader reader(const void* base, unsigned N, float r0) {
     const char* b = (const char*)base;
-    return Reader{(const __half*)b, (const float*)(b + rest_offset(N)), (const float4*)(b + coef_offset(N)), N, rho0};
+    return Reader{(const __half*)b, (const float*)(b + rest_offset(N)), (const float4*)(b + coef_offset(N)), N, r0};
   }
-  __host__ __device__ static Totals totals(const void* base, unsigned N, float rho0) {
+  __host__ __device__ static Totals totals(const void* base, unsigned N, float r0) {
     const char* b = (const char*)base;
-    return Totals{(const __half*)b, (const float*)(b + rest_offset(N)), N, rho0};
+    return Totals{(const __half*)b, (const float*)(b + rest_offset(N)), N, r0};
   }
-  __host__ __device__ static Writer writer(void* base, unsigned N, float rho0) {
+  __host__ __device__ static Writer writer(void* base, unsigned N, float r0) {
     char* b = (char*)base;
-    return Writer{(__half*)b, (float*)(b + rest_offset(N)), (float4*)(b + coef_offset(N)), N, rho0, 0u};
+    return Writer{(__half*)b, (float*)(b + rest_offset(N)), (float4*)(b + coef_offset(N)), N, r0, 0u};
   }
 };
 
@@ -1096,7 +1113,24 @@ __device__ __forceinline__ void collide_totals(const float t[27], float rho1, fl
   const float om1 = 1.f - p.omega;
   const float4 cf = make_float4(c1, seg * m[0], seg * m[1], seg * m[2]);
   const unsigned hb = fout.site_bits(site);
-  float s1 = 0.f, s2 = 0.f;
+  // S: the sum of the stored moving totals, which the rest populations below complete to
+  // rho_k. Its rounding becomes mass: a plain running sum of populations of nearly the same
+  // sizes at every site rounds the same way nearly everywhere (measured: the FP16 form lost
+  // 2.2e-8 of each component's mass per step, FP32 gained 1.9e-9). FP32 sums them with
+  // Kahan's compensation, which leaves one rounding of the exact sum; the FP16 totals are
+  // multiples of 2^-24 below 1 (TotalRecolHalf), so their plain sum is exact.
+  constexpr bool kKahan = WR::kCompensate;
+  float S = 0.f, cS = 0.f;
+  auto add = [&](float v) {
+    if constexpr (kKahan) {
+      const float y = v - cS;
+      const float t2 = S + y;
+      cS = (t2 - S) - y;
+      S = t2;
+    } else {
+      S += v;
+    }
+  };
   static_for<27>([&](auto I) {
     constexpr int i = decltype(I)::value;
     constexpr int o = opposite(i);
@@ -1117,25 +1151,25 @@ __device__ __forceinline__ void collide_totals(const float t[27], float rho1, fl
       const float fsm = fmaf(w, E - O, om1 * t[o]);
       float tp, tm;
       fout.template put_pair<i, o>(site, fsp, fsm, hb, tp, tm);
-      // the components of the stored pair exactly as a reader will recompute them
-      float ap, bp, am, bm;
-      split_total<i>(tp, cf, ap, bp);
-      split_total<o>(tm, cf, am, bm);
-      s1 += ap + am;
-      s2 += bp + bm;
+      add(tp);
+      add(tm);
     }
   });
-  fout.put_rest(site, rho1 - s1, rho2 - s2, cf);
+  // Component 1 of the moving populations sums to phi_1 S (a pair's recolouring terms are
+  // exact negatives of each other), component 2 to S - phi_1 S: the rest populations make
+  // each component's total rho_k, to the rounding of the sums.
+  const float s1 = c1 * S;
+  fout.put_rest(site, rho1 - s1, rho2 - (S - s1), cf);
 }
 
 // The streaming collision storing a total + recolouring form (WR), from a state in that
 // form (RD its Totals, TOTALS) or in the two-population layout of the precision (RD the
-// Plain or HalfDev reader: the first step after a state was set). rho_1 of the site comes
-// from the moments pass (rho1m), rho from the pulled totals, rho_2 = rho - rho_1. Capped at
+// Plain or HalfDev reader: the first step after a state was set). (rho_1, rho_2) of the
+// site come from the moments pass (rho12), rho = rho_1 + rho_2; the totals give j. Capped at
 // 64 registers (four blocks per SM; 24 bytes of spills in the FP32 build): 395 us per FP32
 // duct step against 441 us at 80 registers and three blocks, the kernel waiting on its loads.
 template <typename RD, bool TOTALS, typename WR>
-__global__ void __launch_bounds__(256, 4) collide3t_kernel(RD f, WR fout, const float* __restrict__ rho1m,
+__global__ void __launch_bounds__(256, 4) collide3t_kernel(RD f, WR fout, const float2* __restrict__ rho12,
                                                            const float4* __restrict__ ng, StepT<float> p) {
   const int x = blockIdx.x * 32 + threadIdx.x, y = blockIdx.y * 8 + threadIdx.y, z = blockIdx.z;
   const unsigned site = (unsigned)x + (unsigned)p.nx * ((unsigned)y + (unsigned)p.ny * (unsigned)z);
@@ -1151,9 +1185,6 @@ __global__ void __launch_bounds__(256, 4) collide3t_kernel(RD f, WR fout, const 
     for (int i = 0; i < 27; ++i) fin[0][i] += fin[1][i];
   }
   const float* t = fin[0];
-  float rho = 0.f;
-#pragma unroll
-  for (int i = 0; i < 27; ++i) rho += t[i];
   float j[3] = {0.f, 0.f, 0.f};
   static_for<27>([&](auto I) {
     constexpr int i = decltype(I)::value;
@@ -1161,8 +1192,9 @@ __global__ void __launch_bounds__(256, 4) collide3t_kernel(RD f, WR fout, const 
     if constexpr (cc(i, 1) != 0) j[1] += cc(i, 1) > 0 ? t[i] : -t[i];
     if constexpr (cc(i, 2) != 0) j[2] += cc(i, 2) > 0 ? t[i] : -t[i];
   });
-  const float rho1 = rho1m[site];
-  const float rho2 = rho - rho1;
+  const float2 r12 = rho12[site];
+  const float rho1 = r12.x, rho2 = r12.y;
+  const float rho = rho1 + rho2;
   float A = 0.f;  // A_h(h), indexed at compile time
   static_for<kMaxProbe>([&](auto I) {
     constexpr int s = decltype(I)::value + 1;

@@ -130,11 +130,11 @@ cudaError_t carry3d_init(const void* f, void* carry, void* ring, void* ghost, co
 // With h.totals, steps under Guo forcing store the total + recolouring form of the
 // precision (TotalRecol / TotalRecolHalf in lb_carry3d.cuh: the total populations, the rest
 // population of each component and (rho_1/rho, beta rho_1 rho_2/rho m) per site; FP16 totals
-// as deviations from w_i h.rho_ref); totals_in says that fa holds that form; rho1 (N floats)
-// carries rho_1 from the moments pass to the collision.
+// as deviations from w_i h.rho_ref); totals_in says that fa holds that form; rho12 (N float2)
+// carries (rho_1, rho_2) from the moments pass to the collision.
 bool stream3d_supported(const HostParams& h);
 bool stream3d_stores_totals(const HostParams& h);
-cudaError_t stream3d_step(const void* fa, void* fb, void* psi, void* ng, void* rho1, int totals_in,
+cudaError_t stream3d_step(const void* fa, void* fb, void* psi, void* ng, void* rho12, int totals_in,
                           const HostParams& h, cudaStream_t s, int* nk);
 // fields and population copies of a state in the total + recolouring form (the
 // Launchers::fields / decode of the other states)

@@ -97,16 +97,16 @@ def test_workspace_size_formula():
 
 def test_workspace_size_streaming_d3q27():
     """Lattices of whole 32 x 8 columns step D3Q27 FP32 / FP16-dev on the streaming step,
-    whose per-site normals (16 bytes a site) and rho_1 of the moments pass (4 bytes) are part
-    of the workspace; the state buffers keep the two-population size (the total +
+    whose per-site normals (16 bytes a site) and (rho_1, rho_2) of the moments pass (8 bytes)
+    are part of the workspace; the state buffers keep the two-population size (the total +
     recolouring form of FP32 steps fits in it)."""
     for prec, state in ((lbnci.LB_FP32, 4 * 54), (lbnci.LB_FP16DEV, 4 * 27 + 8)):
         nx, ny, nz = 64, 16, 6
         cfg = lbnci.lb_config_make(lattice=1, nx=nx, ny=ny, nz=nz, precision=prec, A_h=0.05)
         n = lbnci.lb_workspace_size(cfg)
         N = nx * ny * nz
-        assert n >= (2 * state + 4 + 16 + 4) * N
-        assert n <= (2 * state + 4 + 16 + 4) * N + 64 * 1024 + N * 10 * 8 // 64
+        assert n >= (2 * state + 4 + 16 + 8) * N
+        assert n <= (2 * state + 4 + 16 + 8) * N + 64 * 1024 + N * 10 * 8 // 64
 
 
 def test_null_arguments_are_rejected():
