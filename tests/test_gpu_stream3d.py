@@ -171,3 +171,52 @@ def test_stream3d_component_mass_drift(precision, state, monkeypatch):
           f"n_nci {o['n_nci']}")
     assert o["n_nci"] > 0
     assert np.all(drift < 2e-6), drift
+
+
+def test_duct_time_averaged_flow_rate_fp16_and_fp32_forms(monkeypatch):
+    """Equal flow-rate accuracy of the storages on the D3Q27 duct over a long horizon: a
+    64 x 24 x 24 walled duct of radius-5 droplets (volume fraction 0.5, G = 1e-5, A_h = 0.005,
+    the near-contact force acting) runs 6,000 steps in the FP64 oracle, and on the GPU in FP32
+    and FP16-deviation storage, each in the total + recolouring form and as pairs; the
+    total and the dispersed flow rate averaged over the second half of the run (13 samples,
+    every 250 steps) must agree with the oracle's within 0.2%, a fifth of the 1% asked of the
+    storage formats (measured on GB300: FP32 1.7e-6 and 2.5e-7 in the total form, 1.1e-6 and
+    1.4e-6 as pairs; FP16-dev 1.2e-4 and 6.2e-5 in the total form, 8.8e-6 and 6.0e-5 as
+    pairs)."""
+    steps, every = 6000, 250
+    p = oracle.make_params(lattice=oracle.D3Q27, nx=64, ny=24, nz=24, wall_y=1, wall_z=1, tau=1.0, A_s=0.01,
+                           beta=0.7, A_h=0.005, force=(1e-5, 0, 0))
+    fl = _duct(64, 24, 24, seed=41)
+    f = oracle.init(p, fl.rho1, fl.rho2)
+    q_ref, qd_ref = [], []
+    for k in range(steps // every):
+        oracle.step_inplace(p, f, every, 0)
+        if (k + 1) * every >= steps // 2:
+            o = oracle.observables(p, f)
+            q_ref.append(o["flow_rate"])
+            qd_ref.append(o["flow_rate_disp"])
+    assert (oracle.fields(p, f)["hit"] > 0).sum() > 0  # the near-contact force acts
+    ref_q, ref_qd = float(np.mean(q_ref)), float(np.mean(qd_ref))
+    for prec in (lbnci.LB_FP32, lbnci.LB_FP16DEV):
+        for state in ("default", "pairs"):
+            if state == "pairs":
+                monkeypatch.setenv("LBNCI_D3_STATE", "pairs")
+            else:
+                monkeypatch.delenv("LBNCI_D3_STATE", raising=False)
+            q, qd = [], []
+            with lbnci.Sim(_cfg(p, prec)) as sim:
+                assert sim.state_form() == (lbnci.LB_STATE_PAIRS if state == "pairs" else
+                                            lbnci.LB_STATE_TOTAL_RECOLOUR)
+                sim.init_fields(fl.rho1, fl.rho2)
+                for k in range(steps // every):
+                    sim.step(every)
+                    if (k + 1) * every >= steps // 2:
+                        o = sim.observables()
+                        q.append(o["flow_rate"])
+                        qd.append(o["flow_rate_disp"])
+            rq = abs(float(np.mean(q)) - ref_q) / abs(ref_q)
+            rqd = abs(float(np.mean(qd)) - ref_qd) / abs(ref_qd)
+            print(f"precision {prec} {state}: time-averaged Q {np.mean(q):.6e} (oracle {ref_q:.6e}, rel. {rq:.2e}), "
+                  f"Q_d {np.mean(qd):.6e} (oracle {ref_qd:.6e}, rel. {rqd:.2e})")
+            assert len(q) == len(q_ref) == 13
+            assert rq <= 0.002 and rqd <= 0.002, (prec, state, rq, rqd)
