@@ -278,7 +278,9 @@ void lb_ensemble_destroy(lb_ensemble* ens);
  * populations f: a device array [2][Q][N] in the storage type of cfg->precision
  * (double for LB_FP64, float for LB_FP32), laid out as lb_get_populations describes.
  * cfg->workspace is ignored; work runs on cfg->stream, and the call copies its result
- * to the host and synchronises cfg->stream before it returns.
+ * to the host and synchronises cfg->stream before it returns, so it cannot be made while
+ * cfg->stream is being captured into a CUDA graph (between captured segments it adds no
+ * allocation).
  * Scratch comes from a fixed 8 MiB static device array inside the library (held by
  * every GPU that loads it until the process exits), so lattices are limited to about
  * 2 million sites in FP32 and 1 million in FP64; larger ones return LB_EINVAL with

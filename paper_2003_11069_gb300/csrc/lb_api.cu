@@ -629,7 +629,8 @@ int lb_state_form(const lb_sim* s) {
 // the device, is not acceptable. For them this entry point computes the same
 // reductions as lb_observables from a population array they already own, using only
 // the fixed scratch array below. Like lb_observables it copies its result to the host
-// and synchronises the caller's stream before it returns.
+// and synchronises the caller's stream before it returns, so it is not a call for a
+// stream under graph capture.
 //
 // The scratch lives in this translation unit for the whole life of the process: every
 // GPU that loads the library holds kNoAllocScratchBytes of it. All calls share it and
