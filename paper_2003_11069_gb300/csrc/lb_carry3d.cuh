@@ -975,11 +975,11 @@ struct TotalRecol {
     }
   };
   struct Writer {
-    static constexpr bool kCompensate = true;  // the collision's sum of the totals
     float* __restrict__ f;
     float4* __restrict__ coef;
     unsigned N;
     unsigned seed;  // unused by this form
+    __device__ __forceinline__ bool compensate() const { return true; }  // the collision's sum of the totals
     __device__ __forceinline__ unsigned site_bits(unsigned) const { return 0u; }
     // the totals of directions I and its opposite O; (tp, tm) = the stored values
     template <int I, int O>
@@ -1054,13 +1054,15 @@ struct TotalRecolHalf {
     }
   };
   struct Writer {
-    static constexpr bool kCompensate = false;  // the totals are multiples of 2^-24: their sum is exact
     __half* __restrict__ d;
     float* __restrict__ r;
     float4* __restrict__ coef;
     unsigned N;
     float r0;  // rho_0/216 on the 2^-24 grid (the host's rho_unit)
     unsigned seed;  // this step's dither seed (step_seed)
+    // the collision's sum of the totals: exact while the totals and their sums stay below 1
+    // (multiples of 2^-24), that is for rho_0 up to about 1.25; compensated above
+    __device__ __forceinline__ bool compensate() const { return r0 > 1.25f / 216.f; }
     __device__ __forceinline__ unsigned site_bits(unsigned site) const { return dither_bits(site, seed); }
     // d_I and d_O rounded stochastically as one half2 (I low, O high) with the site's bits h;
     // (tp, tm) = the totals a reader will see
@@ -1118,11 +1120,12 @@ __device__ __forceinline__ void collide_totals(const float t[27], float rho1, fl
   // sizes at every site rounds the same way nearly everywhere (measured: the FP16 form lost
   // 2.2e-8 of each component's mass per step, FP32 gained 1.9e-9). FP32 sums them with
   // Kahan's compensation, which leaves one rounding of the exact sum; the FP16 totals are
-  // multiples of 2^-24 below 1 (TotalRecolHalf), so their plain sum is exact.
-  constexpr bool kKahan = WR::kCompensate;
+  // multiples of 2^-24 below 1 (TotalRecolHalf), so their plain sum is exact (for rho_0 up
+  // to about 1.25; compensated above).
+  const bool kahan = fout.compensate();  // the same for every thread of the launch
   float S = 0.f, cS = 0.f;
   auto add = [&](float v) {
-    if constexpr (kKahan) {
+    if (kahan) {
       const float y = v - cS;
       const float t2 = S + y;
       cS = (t2 - S) - y;
@@ -1166,8 +1169,9 @@ __device__ __forceinline__ void collide_totals(const float t[27], float rho1, fl
 // form (RD its Totals, TOTALS) or in the two-population layout of the precision (RD the
 // Plain or HalfDev reader: the first step after a state was set). (rho_1, rho_2) of the
 // site come from the moments pass (rho12), rho = rho_1 + rho_2; the totals give j. Capped at
-// 64 registers (four blocks per SM; 24 bytes of spills in the FP32 build): 395 us per FP32
-// duct step against 441 us at 80 registers and three blocks, the kernel waiting on its loads.
+// 64 registers (four blocks per SM, no spills reading the form): 395 us per FP32 duct step
+// against 441 us at 80 registers and three blocks when measured, the kernel waiting on its
+// loads.
 template <typename RD, bool TOTALS, typename WR>
 __global__ void __launch_bounds__(256, 4) collide3t_kernel(RD f, WR fout, const float2* __restrict__ rho12,
                                                            const float4* __restrict__ ng, StepT<float> p) {

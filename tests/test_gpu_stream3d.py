@@ -143,16 +143,20 @@ def test_stream3d_total_form_input_matches_oracle(name, precision, monkeypatch):
     assert rel < 0.5, rel
 
 
-@pytest.mark.parametrize("state", ["default", "pairs"])
-@pytest.mark.parametrize("precision", [lbnci.LB_FP32, lbnci.LB_FP16DEV])
-def test_stream3d_component_mass_drift(precision, state, monkeypatch):
+@pytest.mark.parametrize("precision,state,scale", [(lbnci.LB_FP32, "default", 1.0), (lbnci.LB_FP32, "pairs", 1.0),
+                                                   (lbnci.LB_FP16DEV, "default", 1.0),
+                                                   (lbnci.LB_FP16DEV, "pairs", 1.0),
+                                                   (lbnci.LB_FP16DEV, "default", 2.0)])
+def test_stream3d_component_mass_drift(precision, state, scale, monkeypatch):
     """Each component's mass over 3000 steps of a walled duct with NCI contacts, in both forms.
     The collision completes a site's stored populations to its component masses with the rest
     populations, so the rounding of the sum of the stored totals becomes mass: summed plainly
     it rounded the same way at nearly every site (the FP16 form lost 2.2e-8 of each
     component's mass per step, 6.7e-5 over these steps; FP32 gained 1.9e-9). FP32 sums with
     Kahan's compensation and the FP16 totals are multiples of 2^-24, whose sum is exact:
-    measured drifts are below 1e-7 in both forms and 2.3e-7 with pairs; the bound is 2e-6."""
+    measured drifts are below 1e-7 in both forms and 2.3e-7 with pairs; the bound is 2e-6.
+    Densities scaled by 2 (scale) take the FP16 form past the range where that sum is exact
+    (rho_0 above 1.25), where it is compensated too."""
     monkeypatch.delenv("LBNCI_D3_KERNEL", raising=False)
     if state == "pairs":
         monkeypatch.setenv("LBNCI_D3_STATE", "pairs")
@@ -162,12 +166,12 @@ def test_stream3d_component_mass_drift(precision, state, monkeypatch):
                            beta=0.7, A_h=0.03, force=(2e-6, 0, 0))
     fl = _duct(64, 24, 24, seed=31)
     with lbnci.Sim(_cfg(p, precision)) as sim:
-        sim.init_fields(fl.rho1, fl.rho2)
+        sim.init_fields(scale * fl.rho1, scale * fl.rho2)
         m0 = sim.observables()["mass"]
         sim.step(3000)
         o = sim.observables()
     drift = np.abs(o["mass"] - m0) / m0
-    print(f"precision {precision} state {state}: relative component-mass drift over 3000 steps {drift}, "
+    print(f"precision {precision} state {state} density x{scale}: relative component-mass drift over 3000 steps {drift}, "
           f"n_nci {o['n_nci']}")
     assert o["n_nci"] > 0
     assert np.all(drift < 2e-6), drift
