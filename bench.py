@@ -604,9 +604,14 @@ def main(argv=None):
         fp32_compare = {}
         for name, env in (("fp32", {}), ("fp32_pairs", {"LBNCI_D3_STATE": "pairs"})):
             ms, form_v = time_other_storage(lbnci, torch, w, lbnci.LB_FP32, rho1, rho2, args.steps, args.warmup, env)
+            b = alg_bytes_per_site(1, "fp32", form_v)
+            b2 = alg_bytes_per_site(1, "fp32", 0)
+            pk, _ = measured_hbm_peak()
             fp32_compare[name] = {"ms_per_step": round(ms, 5), "value": round(N / (ms * 1e-3) / 1e6, 2),
                                   "state_form": STATE_FORMS.get(form_v, "?").split(":")[0],
-                                  "alg_bytes_per_site": alg_bytes_per_site(1, "fp32", form_v)}
+                                  "alg_bytes_per_site": b,
+                                  "frac": round(b * N / (ms * 1e-3) / 1e9 / pk, 4),
+                                  "frac_two_population": round(b2 * N / (ms * 1e-3) / 1e9 / pk, 4)}
             fp32_compare[f"speedup_vs_{name}"] = round(ms / ms_per_step, 3)
         fp32_compare["env"] = "fp32_pairs: LBNCI_D3_STATE=pairs"
 
