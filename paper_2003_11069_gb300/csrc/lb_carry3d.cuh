@@ -758,14 +758,16 @@ carry3d_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_constant_
 
 // (n, |grad psi|) of a 32 x 8 column's sites on kN3Z consecutive planes from the psi
 // array: the block keeps psi of its 34 x 10 cells (beyond a wall the mirror cell, along
-// periodic axes the image) on three planes in a shared-memory ring; the loads of plane
-// z + 2 are issued before plane z is computed and stored after it, so their latency
-// overlaps the arithmetic. Every site sums its 26 neighbours in direction order.
+// periodic axes the image) in a shared-memory ring of four planes; the loads of plane z + 2
+// are issued before plane z is computed and stored after it, into the slot plane z - 2
+// held, so their latency overlaps the arithmetic and one barrier per plane suffices (62 us
+// per duct step against 65 us with three slots and two barriers). Every site sums its 26
+// neighbours in direction order.
 constexpr int kN3Z = 16;
 __global__ void __launch_bounds__(256) normals3d_kernel(const float* __restrict__ psi, float4* __restrict__ ng,
                                                         StepT<float> p) {
   constexpr int RX = 34, RXY = RX * 10, PER = (RXY + 255) / 256;
-  __shared__ float s_psi[3 * RXY];
+  __shared__ float s_psi[4 * RXY];
   const int x0 = blockIdx.x * 32, y0 = blockIdx.y * 8, z0 = blockIdx.z * kN3Z;
   const int nx = p.nx, ny = p.ny, nz = p.nz;
   const int tid = threadIdx.x + 32 * threadIdx.y;
@@ -783,8 +785,8 @@ __global__ void __launch_bounds__(256) normals3d_kernel(const float* __restrict_
       }
     }
   };
-  auto store = [&](int q, const float v[PER]) {  // into ring slot q mod 3
-    float* dst = s_psi + ((q + 3) % 3) * RXY;
+  auto store = [&](int q, const float v[PER]) {  // into ring slot q mod 4
+    float* dst = s_psi + ((q + 4) & 3) * RXY;
 #pragma unroll
     for (int k = 0; k < PER; ++k) {
       const int c = tid + 256 * k;
@@ -807,15 +809,16 @@ __global__ void __launch_bounds__(256) normals3d_kernel(const float* __restrict_
     float vn[PER];
     const bool more = z + 1 < z1;  // plane z + 2 is needed by the next iteration
     if (more) load(z + 2, vn);
-    const float* pm = s_psi + ((z + 2) % 3) * RXY;
-    const float* p0 = s_psi + (z % 3) * RXY;
-    const float* pp = s_psi + ((z + 1) % 3) * RXY;
+    const float* pm = s_psi + ((z + 3) & 3) * RXY;
+    const float* p0 = s_psi + (z & 3) * RXY;
+    const float* pp = s_psi + ((z + 1) & 3) * RXY;
     float g[3];
     grad_ring<float>(pm, p0, pp, RX, cxy, g);
     float n[3];
     const float gn = M<float>::unit(g, n);
     ng[(unsigned)x + (unsigned)nx * ((unsigned)y + (unsigned)ny * (unsigned)z)] = make_float4(n[0], n[1], n[2], gn);
-    __syncthreads();  // plane z - 1's slot is free
+    // plane z + 2 goes to the fourth slot, the one plane z - 2 held: every thread finished
+    // reading it before the barrier that ended the previous plane
     if (more) store(z + 2, vn);
     __syncthreads();
   }
