@@ -216,8 +216,9 @@ int lb_step_path(const lb_sim* sim);
  *                           FP32 keeps f*_i in FP32 (128 instead of 216 bytes per site);
  *                           FP16-dev keeps f*_i - w_i rho_0 in FP16, rho_0 the mean total
  *                           density of the state as lb_init_fields or lb_set_populations set
- *                           it (76 instead of 116 bytes per site; those two calls then run
- *                           one fields pass for rho_0 and synchronise the sim's stream).
+ *                           it (76 instead of 116 bytes per site; lb_init_fields then sums
+ *                           the given fields, lb_set_populations runs one fields pass, and
+ *                           both synchronise the sim's stream).
  *                           The first step after a state is set reads it as pairs.
  * Returns -1 for a NULL sim. */
 enum { LB_STATE_PAIRS = 0, LB_STATE_TOTAL_RECOLOUR = 1 };

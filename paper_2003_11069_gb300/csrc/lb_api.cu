@@ -40,6 +40,24 @@ cudaError_t reduce_partials(const double* partials, long long nblocks, double* o
   return cudaGetLastError();
 }
 
+// Sum of rho1 + rho2 over the sites, per block (a grid-stride range, then a fixed tree) into
+// slot 0 of the block's partials (the other slots zeroed), for reduce_partials to add in a
+// fixed order: the mean density of the initial fields in a few microseconds.
+__global__ void __launch_bounds__(256) density_sum_kernel(const double* __restrict__ rho1,
+                                                          const double* __restrict__ rho2, long long N,
+                                                          double* __restrict__ partials) {
+  __shared__ double s[256];
+  double v = 0.0;
+  for (long long i = blockIdx.x * 256LL + threadIdx.x; i < N; i += (long long)gridDim.x * 256) v += rho1[i] + rho2[i];
+  s[threadIdx.x] = v;
+  __syncthreads();
+  for (int w = 128; w > 0; w >>= 1) {
+    if ((int)threadIdx.x < w) s[threadIdx.x] += s[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x < kRedSlots) partials[blockIdx.x * (long long)kRedSlots + threadIdx.x] = threadIdx.x == 0 ? s[0] : 0.0;
+}
+
 long long tiled_blocks(int lattice, const HostParams& p) {
   if (lattice == 0) {
     return (long long)((p.nx + Tile<0>::X - 1) / Tile<0>::X) * ((p.ny + Tile<0>::Y - 1) / Tile<0>::Y) *
@@ -272,12 +290,26 @@ lb_status run_fields(lb_sim* s, const FieldOut& outs) {
 }
 
 // The reference density rho_0 of the FP16 total + recolouring form: the mean total
-// density of a state just set (a fields pass and its reduction; synchronises the stream).
-lb_status refresh_rho_ref(lb_sim* s) {
+// density of a state just set; from the density fields given to lb_init_fields (d1, d2 on
+// the device) or, after lb_set_populations, from a fields pass. Synchronises the stream.
+lb_status refresh_rho_ref(lb_sim* s, const double* d1 = nullptr, const double* d2 = nullptr) {
   if (!(s->p.stream3d && s->p.totals && s->p.half)) return LB_OK;
-  lb_status st = run_fields(s, FieldOut{});
-  if (st != LB_OK) return st;
-  const double r = (s->host_result[0] + s->host_result[1]) / (double)s->p.N;
+  double total = 0.0;
+  if (d1 && d2) {
+    const long long nb = s->nblocks < 1024 ? s->nblocks : 1024;
+    density_sum_kernel<<<(unsigned)nb, 256, 0, s->stream>>>(d1, d2, s->p.N, s->partials);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = reduce_partials(s->partials, nb, s->result, s->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&total, s->result, sizeof(double), cudaMemcpyDeviceToHost, s->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+    s->launches += 2;
+    if (e != cudaSuccess) return cuda_fail(s, e, "reference density");
+  } else {
+    lb_status st = run_fields(s, FieldOut{});
+    if (st != LB_OK) return st;
+    total = s->host_result[0] + s->host_result[1];
+  }
+  const double r = total / (double)s->p.N;
   s->p.rho_ref = std::isfinite(r) && r > 0.0 ? (float)r : 1.0f;
   return LB_OK;
 }
@@ -424,7 +456,7 @@ lb_status lb_init_fields(lb_sim* s, const double* rho1, const double* rho2, cons
     if (e != cudaSuccess) return cuda_fail(s, e, "stream synchronize");
   }
   s->step = 0;
-  return refresh_rho_ref(s);
+  return refresh_rho_ref(s, d1, d2);
 }
 
 lb_status lb_step(lb_sim* s, long long nsteps) {
