@@ -751,9 +751,11 @@ carry3d_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_constant_
 
 // ---------------------------------------------------------------------------------
 // The streaming D3Q27 step (FP32 and FP16-dev storage; lattices of whole 32 x 8 columns):
-// moments_kernel writes psi; normals3d_kernel the per-site (n, |grad psi|);
-// collide3d_kernel then runs the near-contact ray of its site over those normals (probes
-// through L2), pulls, collides and stores, with no shared memory and no barrier, its
+// a moments pass writes psi (and, for a step that stores the total + recolouring form,
+// (rho_1, rho_2)); normals3d_kernel the per-site (n, |grad psi|); the collision
+// (collide3d_kernel for two populations per direction, collide3t_kernel for the total form,
+// at the end of the file) then runs the near-contact ray of its site over those normals
+// (probes through L2), pulls, collides and stores, with no shared memory and no barrier, its
 // block's neighbours reading the same planes at the same time from L2.
 
 // (n, |grad psi|) of a 32 x 8 column's sites on kN3Z consecutive planes from the psi
