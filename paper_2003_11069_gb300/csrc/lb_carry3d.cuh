@@ -902,14 +902,15 @@ __global__ void __launch_bounds__(256) collide3d_kernel(typename ST::Reader f, t
 //
 //   TotalRecol      FP32 totals: plane 0 f_0^1, planes 1..26 f*_i, plane 27 f_0^2 (planes
 //                   0 and 27 are also where the two-population layout keeps the rest
-//                   populations), then the coefficient plane: 128 bytes per site.
+//                   populations), then the coefficient plane: 128 bytes per site. The
+//                   collision sums S with Kahan's compensation (collide_totals).
 //   TotalRecolHalf  FP16 totals, as deviations from the lattice-weight equilibrium of one
 //                   reference density rho_0 of the sim (f*_i = w_i rho_0 + d_i; the total
 //                   density of the model's two fluids stays close to its mean, so d_i is of
 //                   the order of w_i (|rho - rho_0| + 3 |c_i.u|)): 26 half planes, then the
 //                   two FP32 rest planes and the coefficient plane: 76 bytes per site. A
 //                   step rounds d_i stochastically (half2_stochastic, the site's dither
-//                   bits); the rest populations and the split use the rounded totals.
+//                   bits); the rest populations use the rounded totals.
 //                   The reference is held as w_i rho_0 = (216 w_i) r with 216 w_i in
 //                   {64, 16, 4, 1} and r = rho_0/216 rounded to a multiple of 2^-24 (the
 //                   host's rho_unit): every decoded total is then a multiple of 2^-24 and,
