@@ -89,3 +89,17 @@ def test_recorded_traffic_follows_the_kernel_code(tmp_path, monkeypatch):
     assert bench.kernel_source_hash("k.cu") != h0
     assert bench.recorded_traffic("w", "fp32") is None
     assert bench.recorded_traffic("w", "fp64") is None
+
+
+def test_algorithmic_bytes_per_site():
+    """B_alg per site update (one read and one write of the stored state), which the bench's
+    roofline fractions divide by: two populations per direction in FP64/FP32 (2 Q values),
+    FP16-dev deviations (Q half2 and a float2 of reference densities), and the D3Q27 total +
+    recolouring form (26 totals in FP32 or FP16, two FP32 rest populations, a float4)."""
+    assert bench.alg_bytes_per_site(0, "fp32") == 2 * 2 * 9 * 4 == 144
+    assert bench.alg_bytes_per_site(0, "fp16dev") == 2 * (9 * 4 + 8) == 88
+    assert bench.alg_bytes_per_site(1, "fp64") == 2 * 2 * 27 * 8 == 864
+    assert bench.alg_bytes_per_site(1, "fp32") == 432
+    assert bench.alg_bytes_per_site(1, "fp16dev") == 232
+    assert bench.alg_bytes_per_site(1, "fp32", 1) == 2 * (26 * 4 + 2 * 4 + 16) == 256
+    assert bench.alg_bytes_per_site(1, "fp16dev", 1) == 2 * (26 * 2 + 2 * 4 + 16) == 152
