@@ -96,6 +96,8 @@ def test_algorithmic_bytes_per_site():
     roofline fractions divide by: two populations per direction in FP64/FP32 (2 Q values),
     FP16-dev deviations (Q half2 and a float2 of reference densities), and the D3Q27 total +
     recolouring form (26 totals in FP32 or FP16, two FP32 rest populations, a float4)."""
+    import bench
+
     assert bench.alg_bytes_per_site(0, "fp32") == 2 * 2 * 9 * 4 == 144
     assert bench.alg_bytes_per_site(0, "fp16dev") == 2 * (9 * 4 + 8) == 88
     assert bench.alg_bytes_per_site(1, "fp64") == 2 * 2 * 27 * 8 == 864
