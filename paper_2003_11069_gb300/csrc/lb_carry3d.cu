@@ -292,8 +292,8 @@ cudaError_t stream3d_step(const void* fa, void* fb, void* psi, void* ng, void* r
   ++*nk;
   if (totals_out && h.half) {
     const TotalRecolHalf::Writer wr = TotalRecolHalf::writer(fb, N, r0);
-    e = totals_in ? launch_collide3t<TotalRecolHalf::Totals, true>(TotalRecolHalf::totals(fa, N, r0), wr, rho12, ng,
-                                                                   p, grid, s)
+    e = totals_in ? launch_collide3t<TotalRecolHalf::Devs, true>(TotalRecolHalf::devs(fa, N), wr, rho12, ng, p,
+                                                                 grid, s)
                   : launch_collide3t<HalfDev<1>::Reader, false>(HalfDev<1>::reader(fa, N), wr, rho12, ng, p, grid, s);
   } else if (totals_out) {
     const TotalRecol::Writer wr = TotalRecol::writer(fb, N);

@@ -921,8 +921,9 @@ __global__ void __launch_bounds__(256) collide3d_kernel(typename ST::Reader f, t
 //                   step.
 //
 // Both offer the two-population reader interface (get<I>: both components of direction I),
-// through which the moments pass, the fields kernel and population copies read them, and
-// Totals (get<I>: the total alone) for the collision, which needs no split.
+// through which the moments pass, the fields kernel and population copies read them; the
+// collision, which needs no split, reads TotalRecol's Totals (get<I>: the total alone) or
+// TotalRecolHalf's Devs (the deviations d_i: it works on them, collide_totals_dev).
 
 // (w_i/|c_i|) c_i.s of moving direction I, s = (c.y, c.z, c.w), summed over the nonzero
 // components of c_i in x, y, z order for I < opposite(I), and exactly the negative of its
@@ -1047,15 +1048,15 @@ struct TotalRecolHalf {
       }
     }
   };
-  struct Totals {
+  // The deviations d_i alone, as pairs (d_i, 0) (0 for the rest direction, which the
+  // collision does not pull): the collision of a step that reads this form works on them.
+  struct Devs {
     const __half* __restrict__ d;
-    const float* __restrict__ r;
     unsigned N;
-    float r0;  // rho_0/216 on the 2^-24 grid (the host's rho_unit)
     template <int I>
     __device__ __forceinline__ void get(unsigned site, float& a, float& b) const {
-      if constexpr (I == 0) a = r[site] + r[N + site];
-      else a = total<I>(d, N, site, r0);
+      if constexpr (I == 0) a = 0.f;
+      else a = __half2float(d[(unsigned)(I - 1) * N + site]);
       b = 0.f;
     }
   };
@@ -1084,19 +1085,29 @@ struct TotalRecolHalf {
       tp = fmaf(w, r0, __half2float(__ushort_as_half(lo)));
       tm = fmaf(w, r0, __half2float(__ushort_as_half(hi)));
     }
+    // deviations already relative to the reference, rounded stochastically; (qp, qm) = the
+    // stored values
+    template <int I, int O>
+    __device__ __forceinline__ void put_pair_dev(unsigned site, float dp, float dm, unsigned h, float& qp,
+                                                 float& qm) const {
+      const unsigned v = half2_stochastic<I>(dp, dm, h);
+      const unsigned short lo = (unsigned short)(v & 0xFFFFu), hi = (unsigned short)(v >> 16);
+      unsigned short* du = reinterpret_cast<unsigned short*>(d);
+      du[(unsigned)(I - 1) * N + site] = lo;
+      du[(unsigned)(O - 1) * N + site] = hi;
+      qp = __half2float(__ushort_as_half(lo));
+      qm = __half2float(__ushort_as_half(hi));
+    }
     __device__ __forceinline__ void put_rest(unsigned site, float r1, float r2, float4 c) const {
       r[site] = r1;
       r[N + site] = r2;
       coef[site] = c;
     }
   };
+  __host__ __device__ static Devs devs(const void* base, unsigned N) { return Devs{(const __half*)base, N}; }
   __host__ __device__ static Reader reader(const void* base, unsigned N, float r0) {
     const char* b = (const char*)base;
     return Reader{(const __half*)b, (const float*)(b + rest_offset(N)), (const float4*)(b + coef_offset(N)), N, r0};
-  }
-  __host__ __device__ static Totals totals(const void* base, unsigned N, float r0) {
-    const char* b = (const char*)base;
-    return Totals{(const __half*)b, (const float*)(b + rest_offset(N)), N, r0};
   }
   __host__ __device__ static Writer writer(void* base, unsigned N, float r0) {
     char* b = (char*)base;
@@ -1171,8 +1182,71 @@ __device__ __forceinline__ void collide_totals(const float t[27], float rho1, fl
   fout.put_rest(site, rho1 - s1, rho2 - (S - s1), cf);
 }
 
+// collide_totals for a step that reads and stores the FP16 form, on the deviations
+// d_i = f*_i - (216 w_i) r0 themselves: the references carry no momentum (sum_i c_i w_i = 0),
+// so j is the deviations' momentum, and the collision's output deviation is
+//   (1 - omega) d_i + w_i (E_i +/- O_i - 216 omega r0),
+// formed without the totals: the offset enters K0 through rho - 216 r0, exact for rho within
+// a factor of two of the reference, so the deviations keep their own precision. The sum of
+// the stored totals is S = 152 r0 + sum of the stored deviations (152 = 216 (1 - w_0)).
+__device__ __forceinline__ void collide_totals_dev(const float d[27], float rho1, float rho2, float rho,
+                                                   const float u[3], const float F[3], float g, const float m[3],
+                                                   const StepT<float>& p, const TotalRecolHalf::Writer& fout,
+                                                   unsigned site) {
+  const float uF = u[0] * F[0] + u[1] * F[1] + u[2] * F[2];
+  const float uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+  const float seg = M<float>::div(p.beta * rho1 * rho2, rho);
+  const float pamp = p.pamp * g;
+  const float c1 = M<float>::div(rho1, rho);
+  const float r0 = fout.r0;
+  const float K0d = p.omega * ((rho - 216.f * r0) - 1.5f * rho * uu) - 3.f * p.guo * uF - pamp * (1.0f / 3.0f);
+  const float orho = p.omega * rho;
+  const float a3 = 3.f * orho, a45 = 4.5f * orho, g3 = 3.f * p.guo, g9 = 9.f * p.guo;
+  const float om1 = 1.f - p.omega;
+  const float4 cf = make_float4(c1, seg * m[0], seg * m[1], seg * m[2]);
+  const unsigned hb = fout.site_bits(site);
+  const bool kahan = fout.compensate();  // the same for every thread of the launch
+  float S = 0.f, cS = 0.f;               // the stored deviations (see collide_totals)
+  auto add = [&](float v) {
+    if (kahan) {
+      const float y = v - cS;
+      const float t2 = S + y;
+      cS = (t2 - S) - y;
+      S = t2;
+    } else {
+      S += v;
+    }
+  };
+  static_for<27>([&](auto I) {
+    constexpr int i = decltype(I)::value;
+    constexpr int o = opposite(i);
+    if constexpr (i > 0 && i < o) {
+      constexpr float w = float(Lattice<1>::w(i));
+      constexpr int ix = cc(i, 0), iy = cc(i, 1), iz = cc(i, 2);
+      auto dotc = [&](const float v[3]) {
+        float r = 0.f;
+        if constexpr (ix == 1) r += v[0]; else if constexpr (ix == -1) r -= v[0];
+        if constexpr (iy == 1) r += v[1]; else if constexpr (iy == -1) r -= v[1];
+        if constexpr (iz == 1) r += v[2]; else if constexpr (iz == -1) r -= v[2];
+        return r;
+      };
+      const float cu = dotc(u), cF = dotc(F), cm = dotc(m);
+      const float E = fmaf(pamp, cm * cm, fmaf(g9, cu * cF, fmaf(a45, cu * cu, K0d)));
+      const float O = fmaf(g3, cF, a3 * cu);
+      float qp, qm;
+      fout.template put_pair_dev<i, o>(site, fmaf(w, E + O, om1 * d[i]), fmaf(w, E - O, om1 * d[o]), hb, qp, qm);
+      add(qp);
+      add(qm);
+    }
+  });
+  const float St = fmaf(152.f, r0, S);
+  const float s1 = c1 * St;
+  fout.put_rest(site, rho1 - s1, rho2 - (St - s1), cf);
+}
+
 // The streaming collision storing a total + recolouring form (WR), from a state in that
-// form (RD its Totals, TOTALS) or in the two-population layout of the precision (RD the
+// form (RD TotalRecol::Totals or TotalRecolHalf::Devs, TOTALS) or in the two-population
+// layout of the precision (RD the
 // Plain or HalfDev reader: the first step after a state was set). (rho_1, rho_2) of the
 // site come from the moments pass (rho12), rho = rho_1 + rho_2; the totals give j. Capped at
 // 64 registers (four blocks per SM, no spills reading the form): 395 us per FP32 duct step
@@ -1216,7 +1290,10 @@ __global__ void __launch_bounds__(256, 4) collide3t_kernel(RD f, WR fout, const 
 #pragma unroll
   for (int a = 0; a < 3; ++a) u[a] = M<float>::div(j[a] + 0.5f * F[a], rho);
   const float m[3] = {-v.x, -v.y, -v.z};
-  collide_totals<WR>(t, rho1, rho2, rho, u, F, v.w, m, p, fout, site);
+  if constexpr (std::is_same<RD, TotalRecolHalf::Devs>::value)
+    collide_totals_dev(t, rho1, rho2, rho, u, F, v.w, m, p, fout, site);  // t: the deviations
+  else
+    collide_totals<WR>(t, rho1, rho2, rho, u, F, v.w, m, p, fout, site);
 }
 
 }  // namespace lbnci
