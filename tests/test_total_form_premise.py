@@ -98,3 +98,37 @@ def test_exact_difference_forcing_is_not_a_recolouring_of_totals():
         _, _, a, _ = _split(c, w, fin, grad, p.beta, out)
         worst = max(worst, float(np.max(np.abs(out[0][1:] - a[1:]) / np.maximum(np.abs(out[0][1:]), w[1:]))))
     assert worst > 1e-8
+
+
+@pytest.mark.parametrize("rho0", [0.97, 1.0, 1.013, 1.2])
+def test_fp16_totals_on_the_2_24_grid_sum_exactly(rho0):
+    """The FP16 form holds its reference as (216 w_i) r with r = rho_0/216 rounded to a
+    multiple of 2^-24, so a decoded total (216 w_i) r + d_i (d_i an FP16 value, itself a
+    multiple of 2^-24) is a multiple of 2^-24 below 1: exact in FP32. A running FP32 sum of
+    a site's 26 totals is then exact too, and equals 152 r + the sum of the deviations
+    (152 = 216 (1 - w_0)), which is how the collision forms it: the rest populations complete
+    the stored mass with no rounding (measured: no drift; with the reference rounded to
+    nearest instead, a plain sum rounded the same way at every site)."""
+    from fractions import Fraction
+
+    _, w, _ = oracle.lattice(oracle.D3Q27)
+    k = np.rint(216.0 * w).astype(np.int64)
+    assert np.all(np.abs(216.0 * w - k) < 1e-12) and sorted(set(k.tolist())) == [1, 4, 16, 64]
+    assert int(k[1:].sum()) == 152
+    r = np.float32(np.rint(rho0 / 216.0 * 2.0 ** 24) / 2.0 ** 24)
+    rng = np.random.default_rng(int(rho0 * 1000))
+    for _ in range(100):
+        d = (rng.normal(0.0, 3e-3, 26) * w[1:]).astype(np.float16).astype(np.float32)
+        base = np.float32(k[1:].astype(np.float32) * r)  # exact: (216 w_i) r on the grid
+        t = base + d
+        for ti, ki, di in zip(t, k[1:], d):
+            assert Fraction(float(ti)) == int(ki) * Fraction(float(r)) + Fraction(float(di))
+        S = np.float32(0.0)
+        Sd = np.float32(0.0)
+        for ti, di in zip(t, d):
+            S = np.float32(S + ti)
+            Sd = np.float32(Sd + di)
+        exact = sum(Fraction(float(x)) for x in t)
+        assert Fraction(float(S)) == exact
+        St = np.float32(np.float32(152.0) * r) + Sd
+        assert Fraction(float(np.float32(St))) == exact
