@@ -132,3 +132,39 @@ def test_fp16_totals_on_the_2_24_grid_sum_exactly(rho0):
         assert Fraction(float(S)) == exact
         St = np.float32(np.float32(152.0) * r) + Sd
         assert Fraction(float(np.float32(St))) == exact
+
+
+def test_collision_on_deviations_equals_collision_on_totals():
+    """A step that reads the FP16 form collides on the deviations d_i = f*_i - (216 w_i) r: the
+    references carry no momentum (sum_i c_i w_i = 0), so j is the deviations' momentum, and
+    BGK with the Guo source and the perturbation, f*_i' = (1 - omega) f*_i + w_i (E_i +/- O_i),
+    with E_i containing K0 = omega rho (1 - 1.5 u.u) - 3 (1 - omega/2) u.F - pamp/3, gives
+    f*_i' - (216 w_i) r = (1 - omega) d_i + w_i (E_i +/- O_i - 216 omega r): the formula of the
+    deviations' collision, checked here in FP64 against the collision on the totals."""
+    rng = np.random.default_rng(77)
+    c, w, _ = oracle.lattice(oracle.D3Q27)
+    k = 216.0 * w
+    for _ in range(50):
+        omega = rng.uniform(0.6, 1.8)
+        guo = 1.0 - 0.5 * omega
+        r = np.rint(rng.uniform(0.97, 1.03) / 216.0 * 2.0 ** 24) / 2.0 ** 24
+        d = rng.normal(0.0, 3e-3, 27) * w
+        t = k * r + d
+        rho = rng.uniform(0.97, 1.03)
+        F = rng.normal(0.0, 1e-4, 3)
+        m = rng.normal(0.0, 1.0, 3)
+        m /= np.linalg.norm(m)
+        pamp = 0.01 * rng.uniform(0.0, 0.2)
+        j_t = c[1:].T @ t[1:]
+        j_d = c[1:].T @ d[1:]
+        assert np.allclose(j_t, j_d, rtol=0, atol=1e-15)  # the references' momentum is zero
+        u = (j_d + 0.5 * F) / rho
+        uu, uF = u @ u, u @ F
+        cu, cF, cm = c @ u, c @ F, c @ m
+        E_core = 4.5 * omega * rho * cu ** 2 + 9 * guo * cu * cF + pamp * cm ** 2
+        O = 3 * omega * rho * cu + 3 * guo * cF
+        K0 = omega * rho * (1 - 1.5 * uu) - 3 * guo * uF - pamp / 3
+        K0d = omega * ((rho - 216 * r) - 1.5 * rho * uu) - 3 * guo * uF - pamp / 3
+        fs = (1 - omega) * t + w * (K0 + E_core + O)  # the collision on the totals
+        dout = (1 - omega) * d + w * (K0d + E_core + O)  # on the deviations
+        assert np.allclose(fs[1:] - k[1:] * r, dout[1:], rtol=0, atol=1e-15)
